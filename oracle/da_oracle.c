@@ -1,0 +1,716 @@
+/*
+ * da_oracle.c -- plain serial CPU reference of the Digital Annealer method
+ * (arXiv:1806.08815).  TEST INFRASTRUCTURE: only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg load this library; it shares nothing
+ * with the CUDA path.  Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp
+ * -shared -fPIC (no fast-math: every fp32 operation below is one IEEE
+ * rounding, which is what makes the fp32 trajectories reproducible).
+ *
+ * Readings of the paper used here (the paper gives no formulas for them):
+ *  - Delta E of flipping x_i: (1 - 2 x_i)(Q_ii + h_i), h_i = sum_j W_ij x_j.
+ *  - Metropolis with the dynamic offset (Algorithm 2): a trial with
+ *    delta = Delta E - E_off is accepted when delta <= 0 (the clipped
+ *    min(1, .)), otherwise when u < exp(-beta * delta) (Sec. III).
+ *  - E_off = m * inc after m consecutive steps without an accepted flip; it
+ *    returns to 0 after a flip (Algorithm 2).
+ *  - "choose one flip uniformly at random" (Algorithm 2): j = floor(u32 * cnt
+ *    / 2^32) and the j-th accepted index in increasing index order.
+ *  - All runs start from x = 0, so h = 0 and E = 0 (Sec. II, DA parameters).
+ *  - Random numbers: Philox4x32-10 keyed by the seed; the paper's hardware
+ *    generator (Sec. II) is replaced by this counter-based one.
+ * parity unpinned: none (every function here is pinned by tests/test_oracle*.py).
+ */
+#include "da_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11.  Ten rounds of the 4x32 Philox S-box; the key is
+ * bumped by the Weyl constants between rounds. */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int lane)
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[lane];
+}
+
+/* The acceptance draw of trial i at step t: counter word 0 is
+ * 32 * (i / 128) + i % 32 and the output lane is (i % 128) / 32, so the four
+ * lanes of one Philox block serve variables i, i+32, i+64, i+96. */
+static uint32_t draw_accept(uint64_t seed, int64_t i, uint32_t t, uint32_t rep)
+{
+    uint32_t c0 = (uint32_t)(32 * (i / 128) + (i % 32));
+    return philox_word(seed, c0, t, rep, 0u, (int)((i % 128) / 32));
+}
+
+static uint32_t draw_choice(uint64_t seed, uint32_t t, uint32_t rep)
+{
+    return philox_word(seed, 0u, t, rep, 1u, 0);
+}
+
+float orc_uniform(uint32_t r)
+{
+    return (float)((r >> 8) + 1u) * 5.9604644775390625e-08f; /* 2^-24 */
+}
+
+/* ------------------------------------------------------------------------ */
+/* exp in fp32.  x = n ln2 + r with n = rint(x / ln2) and ln2 split into a
+ * short head and a tail (Cody & Waite); e^r by its Taylor series to r^7 in
+ * Horner form with fused multiply-adds; then the exponent is set directly. */
+float orc_expf(float x)
+{
+    if (!(x >= -86.0f))
+        return 0.0f;
+    const float log2e = 1.44269504088896341f;
+    const float ln2_head = 0.693145751953125f;      /* ln 2 to 16 bits */
+    const float ln2_tail = 1.428606765330187e-06f;  /* ln 2 - head     */
+    float n = rintf(x * log2e);
+    float r = fmaf(-n, ln2_head, x);
+    r = fmaf(-n, ln2_tail, r);
+    float p = 1.0f / 5040.0f;
+    p = fmaf(p, r, 1.0f / 720.0f);
+    p = fmaf(p, r, 1.0f / 120.0f);
+    p = fmaf(p, r, 1.0f / 24.0f);
+    p = fmaf(p, r, 1.0f / 6.0f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    int e = (int)n + 127;
+    union { uint32_t u; float f; } s;
+    s.u = (uint32_t)e << 23;
+    return p * s.f;
+}
+
+void orc_expf_batch(const float* x, float* y, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        y[i] = orc_expf(x[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+static inline int getbit(const uint32_t* x, int64_t i) { return (int)((x[i >> 5] >> (i & 31)) & 1u); }
+
+int64_t orc_energy_int(int64_t N, const int32_t* Q, const uint32_t* x)
+{
+    int64_t E = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!getbit(x, i)) continue;
+        E += Q[i * N + i];
+        for (int64_t j = i + 1; j < N; ++j)
+            if (getbit(x, j)) E += Q[i * N + j];
+    }
+    return E;
+}
+
+double orc_energy_f64(int64_t N, const float* Q, const uint32_t* x)
+{
+    double E = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (!getbit(x, i)) continue;
+        E += (double)Q[i * N + i];
+        for (int64_t j = i + 1; j < N; ++j)
+            if (getbit(x, j)) E += (double)Q[i * N + j];
+    }
+    return E;
+}
+
+/* H = -sum_{i<j} J_ij s_i s_j - sum_i hb_i s_i (Eq. 4).  With s = 2x - 1,
+ * s_i s_j = 4 x_i x_j - 2 x_i - 2 x_j + 1, which gives the coefficients
+ * below. */
+int orc_ising_to_qubo(int64_t N, const double* J, const double* hb, double* Q, double* C)
+{
+    if (N < 1) return -1;
+    double c = 0.0;
+    for (int64_t i = 0; i < N * N; ++i) Q[i] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        Q[i * N + i] = -2.0 * hb[i];
+        c += hb[i];
+    }
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i + 1; j < N; ++j) {
+            double Jij = J[i * N + j];
+            Q[i * N + j] = -4.0 * Jij;
+            Q[i * N + i] += 2.0 * Jij;
+            Q[j * N + j] += 2.0 * Jij;
+            c -= Jij;
+        }
+    *C = c;
+    return 0;
+}
+
+double orc_ising_energy(int64_t N, const double* J, const double* hb, const int8_t* s)
+{
+    double H = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        H -= hb[i] * s[i];
+        for (int64_t j = i + 1; j < N; ++j)
+            H -= J[i * N + j] * s[i] * s[j];
+    }
+    return H;
+}
+
+int orc_brute_force_f64(int64_t N, const double* Q, double* Emin, int64_t* count, uint32_t* argmin)
+{
+    if (N < 1 || N > 30) return -1;
+    double* h = (double*)calloc((size_t)N, sizeof(double));
+    if (!h) return -2;
+    uint32_t x = 0;
+    double E = 0.0, best = 0.0;
+    int64_t nbest = 1;
+    uint32_t arg = 0;
+    const uint64_t total = 1ull << N;
+    for (uint64_t k = 1; k < total; ++k) {
+        int i = __builtin_ctzll(k);               /* Gray code: flip bit i */
+        int xi = (int)((x >> i) & 1u);
+        double dE = (xi ? -1.0 : 1.0) * (Q[i * N + i] + h[i]);
+        E += dE;
+        x ^= 1u << i;
+        double s = xi ? -1.0 : 1.0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            double w = (j < i) ? Q[j * N + i] : Q[i * N + j];
+            h[j] += s * w;
+        }
+        double tol = 1e-9 * (fabs(best) + 1.0);
+        if (E < best - tol) { best = E; nbest = 1; arg = x; }
+        else if (fabs(E - best) <= tol) nbest++;
+    }
+    free(h);
+    *Emin = best;
+    *count = nbest;
+    argmin[0] = arg;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Instance in the form the annealer reads: symmetric W and diagonal d. */
+typedef struct {
+    int64_t N;
+    int mode;
+    int64_t* Wi; int64_t* di;   /* ORC_MODE_INT */
+    float* Wf; float* df;       /* ORC_MODE_F32 / ORC_MODE_F64 */
+} inst_t;
+
+static void inst_free(inst_t* I)
+{
+    free(I->Wi); free(I->di); free(I->Wf); free(I->df);
+}
+
+static int inst_make(inst_t* I, int64_t N, int mode, const void* Q)
+{
+    memset(I, 0, sizeof(*I));
+    I->N = N; I->mode = mode;
+    if (mode == ORC_MODE_INT) {
+        const int32_t* Qi = (const int32_t*)Q;
+        I->Wi = (int64_t*)calloc((size_t)(N * N), sizeof(int64_t));
+        I->di = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+        if (!I->Wi || !I->di) { inst_free(I); return -2; }
+        for (int64_t i = 0; i < N; ++i) {
+            I->di[i] = Qi[i * N + i];
+            for (int64_t j = i + 1; j < N; ++j) {
+                I->Wi[i * N + j] = Qi[i * N + j];
+                I->Wi[j * N + i] = Qi[i * N + j];
+            }
+        }
+    } else {
+        const float* Qf = (const float*)Q;
+        I->Wf = (float*)calloc((size_t)(N * N), sizeof(float));
+        I->df = (float*)calloc((size_t)N, sizeof(float));
+        if (!I->Wf || !I->df) { inst_free(I); return -2; }
+        for (int64_t i = 0; i < N; ++i) {
+            I->df[i] = Qf[i * N + i];
+            for (int64_t j = i + 1; j < N; ++j) {
+                I->Wf[i * N + j] = Qf[i * N + j];
+                I->Wf[j * N + i] = Qf[i * N + j];
+            }
+        }
+    }
+    return 0;
+}
+
+int orc_fields_int(int64_t N, const int32_t* Q, const uint32_t* x, int64_t* h)
+{
+    if (N < 1) return -1;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t s = 0;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i || !getbit(x, j)) continue;
+            s += (j < i) ? Q[j * N + i] : Q[i * N + j];
+        }
+        h[i] = s;
+    }
+    return 0;
+}
+
+/* Fixed-point scale of the recompute: with max|W| < 2^e and 2^L >= N,
+ * S = 62 - L - e puts every |W_ij| 2^S below 2^(62-L), so a sum of N of them
+ * cannot overflow int64. */
+static int32_t fix_scale(int64_t N, const float* Wf)
+{
+    float amax = 0.0f;
+    for (int64_t i = 0; i < N * N; ++i) {
+        float a = fabsf(Wf[i]);
+        if (a > amax) amax = a;
+    }
+    if (amax == 0.0f) return 0;
+    int e;
+    frexpf(amax, &e);
+    int L = 0;
+    while ((1ll << L) < N) L++;
+    return 62 - L - e;
+}
+
+static void recompute_sums(const inst_t* I, int32_t S, const uint8_t* x, int64_t* sums)
+{
+    const int64_t N = I->N;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t s = 0;
+        for (int64_t j = 0; j < N; ++j)
+            if (x[j]) s += (int64_t)llrintf(ldexpf(I->Wf[i * N + j], S));
+        sums[i] = s;
+    }
+}
+
+static double recompute_energy(const inst_t* I, int32_t S, const uint8_t* x, const int64_t* sums)
+{
+    double E = 0.0;
+    for (int64_t i = 0; i < I->N; ++i) {
+        if (!x[i]) continue;
+        double hd = ldexp((double)sums[i], -S);
+        E += (double)I->df[i] + 0.5 * hd;
+    }
+    return E;
+}
+
+int orc_recompute_f32(int64_t N, const float* Q, const uint32_t* x, float* h, int64_t* sums, int32_t* S_out)
+{
+    if (N < 1) return -1;
+    inst_t I;
+    if (inst_make(&I, N, ORC_MODE_F32, Q)) return -2;
+    int32_t S = fix_scale(N, I.Wf);
+    uint8_t* xb = (uint8_t*)malloc((size_t)N);
+    int64_t* s = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    for (int64_t i = 0; i < N; ++i) xb[i] = (uint8_t)getbit(x, i);
+    recompute_sums(&I, S, xb, s);
+    for (int64_t i = 0; i < N; ++i) {
+        if (h) h[i] = ldexpf((float)s[i], -S);
+        if (sums) sums[i] = s[i];
+    }
+    if (S_out) *S_out = S;
+    free(xb); free(s); inst_free(&I);
+    return 0;
+}
+
+double orc_recompute_energy_f32(int64_t N, const float* Q, const uint32_t* x)
+{
+    inst_t I;
+    if (N < 1 || inst_make(&I, N, ORC_MODE_F32, Q)) return NAN;
+    int32_t S = fix_scale(N, I.Wf);
+    uint8_t* xb = (uint8_t*)malloc((size_t)N);
+    int64_t* s = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+    for (int64_t i = 0; i < N; ++i) xb[i] = (uint8_t)getbit(x, i);
+    recompute_sums(&I, S, xb, s);
+    double E = recompute_energy(&I, S, xb, s);
+    free(xb); free(s); inst_free(&I);
+    return E;
+}
+
+/* ------------------------------------------------------------------------ */
+/* State of one replica of the annealer. */
+typedef struct {
+    uint8_t* x;
+    int64_t* hi;   /* ORC_MODE_INT */
+    float* hf;     /* ORC_MODE_F32 */
+    double* hd;    /* ORC_MODE_F64 */
+    int64_t Ei;    /* tracked energy, ORC_MODE_INT */
+    double Ed;     /* tracked energy, real modes   */
+    uint32_t m;    /* steps since the last accepted flip (dynamic offset) */
+    int32_t* acc;  /* accepted indices of the current step */
+} rep_t;
+
+static int rep_init(rep_t* s, const inst_t* I)
+{
+    memset(s, 0, sizeof(*s));
+    const int64_t N = I->N;
+    s->x = (uint8_t*)calloc((size_t)N, 1);
+    s->acc = (int32_t*)malloc((size_t)N * sizeof(int32_t));
+    if (I->mode == ORC_MODE_INT) s->hi = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    else if (I->mode == ORC_MODE_F32) s->hf = (float*)calloc((size_t)N, sizeof(float));
+    else s->hd = (double*)calloc((size_t)N, sizeof(double));
+    if (!s->x || !s->acc || (!s->hi && !s->hf && !s->hd)) return -2;
+    return 0;
+}
+
+static void rep_free(rep_t* s)
+{
+    free(s->x); free(s->hi); free(s->hf); free(s->hd); free(s->acc);
+}
+
+static double tracked_energy(const inst_t* I, const rep_t* s)
+{
+    return I->mode == ORC_MODE_INT ? (double)s->Ei : s->Ed;
+}
+
+/* Steps (a)-(b) of the DA step: every trial against E_off; fills s->acc and
+ * returns how many were accepted. */
+static int32_t da_trials(const inst_t* I, rep_t* s, float beta, float inc,
+                         uint64_t seed, uint32_t t, uint32_t rep)
+{
+    const int64_t N = I->N;
+    const float E_off = (float)s->m * inc;
+    int32_t cnt = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        float delta;
+        if (I->mode == ORC_MODE_INT) {
+            int64_t v = I->di[i] + s->hi[i];
+            int64_t dE = s->x[i] ? -v : v;
+            delta = (float)dE - E_off;
+        } else if (I->mode == ORC_MODE_F32) {
+            float v = I->df[i] + s->hf[i];
+            float dE = s->x[i] ? -v : v;
+            delta = dE - E_off;
+        } else {
+            double v = (double)I->df[i] + s->hd[i];
+            double dE = s->x[i] ? -v : v;
+            double d64 = dE - (double)E_off;
+            if (d64 <= 0.0) { s->acc[cnt++] = (int32_t)i; continue; }
+            float a = (float)(-(double)beta * d64);
+            float p = orc_expf(a);
+            if (orc_uniform(draw_accept(seed, i, t, rep)) < p) s->acc[cnt++] = (int32_t)i;
+            continue;
+        }
+        if (delta <= 0.0f) { s->acc[cnt++] = (int32_t)i; continue; }
+        float a = -(beta * delta);
+        float p = orc_expf(a);
+        if (orc_uniform(draw_accept(seed, i, t, rep)) < p) s->acc[cnt++] = (int32_t)i;
+    }
+    return cnt;
+}
+
+/* Step (c): flip x_k and update every field with the column W[:, k]. */
+static void da_flip(const inst_t* I, rep_t* s, int64_t k)
+{
+    const int64_t N = I->N;
+    const int old = s->x[k];
+    if (I->mode == ORC_MODE_INT) {
+        int64_t v = I->di[k] + s->hi[k];
+        s->Ei += old ? -v : v;
+        const int64_t sg = old ? -1 : 1;
+        for (int64_t j = 0; j < N; ++j) s->hi[j] += sg * I->Wi[k * N + j];
+    } else if (I->mode == ORC_MODE_F32) {
+        float v = I->df[k] + s->hf[k];
+        float dE = old ? -v : v;
+        s->Ed += (double)dE;
+        const float sg = old ? -1.0f : 1.0f;
+        for (int64_t j = 0; j < N; ++j) s->hf[j] = s->hf[j] + sg * I->Wf[k * N + j];
+    } else {
+        double v = (double)I->df[k] + s->hd[k];
+        s->Ed += old ? -v : v;
+        const double sg = old ? -1.0 : 1.0;
+        for (int64_t j = 0; j < N; ++j) s->hd[j] += sg * (double)I->Wf[k * N + j];
+    }
+    s->x[k] = (uint8_t)(old ^ 1);
+}
+
+/* One complete step of Algorithm 2.  Returns the flipped index or -1. */
+static int64_t da_step(const inst_t* I, rep_t* s, float beta, float inc,
+                       uint64_t seed, uint32_t t, uint32_t rep, int32_t* n_acc)
+{
+    int32_t cnt = da_trials(I, s, beta, inc, seed, t, rep);
+    if (n_acc) *n_acc = cnt;
+    if (cnt == 0) {
+        s->m += 1;
+        return -1;
+    }
+    uint32_t u = draw_choice(seed, t, rep);
+    uint32_t j = (uint32_t)(((uint64_t)u * (uint64_t)cnt) >> 32);
+    int64_t k = s->acc[j];
+    da_flip(I, s, k);
+    s->m = 0;
+    return k;
+}
+
+static void pack_bits(const uint8_t* x, int64_t N, uint32_t* out)
+{
+    int64_t words = (N + 31) / 32;
+    for (int64_t w = 0; w < words; ++w) out[w] = 0;
+    for (int64_t i = 0; i < N; ++i)
+        if (x[i]) out[i >> 5] |= 1u << (i & 31);
+}
+
+static void periodic_recompute(const inst_t* I, rep_t* s, int32_t S, int64_t* sums)
+{
+    recompute_sums(I, S, s->x, sums);
+    for (int64_t i = 0; i < I->N; ++i) s->hf[i] = ldexpf((float)sums[i], -S);
+    s->Ed = recompute_energy(I, S, s->x, sums);
+}
+
+int orc_da_anneal(int64_t N, int mode, const void* Q,
+                  const float* beta, int64_t T, float inc, int32_t R,
+                  uint64_t seed, uint32_t replica_base, int64_t recompute_every,
+                  double* E_final, double* E_best, uint32_t* x_final, uint32_t* x_best,
+                  int64_t* flips, int32_t* trace, int32_t* accepted, int nthreads)
+{
+    if (N < 1 || T < 0 || R < 0 || !Q || (T > 0 && !beta)) return -1;
+    if (mode < ORC_MODE_INT || mode > ORC_MODE_F64) return -1;
+    inst_t I;
+    if (inst_make(&I, N, mode, Q)) return -2;
+    const int32_t S = (mode == ORC_MODE_F32) ? fix_scale(N, I.Wf) : 0;
+    const int64_t words = (N + 31) / 32;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int32_t r = 0; r < R; ++r) {
+        rep_t s;
+        uint8_t* best = (uint8_t*)calloc((size_t)N, 1);
+        int64_t* sums = (int64_t*)malloc((size_t)N * sizeof(int64_t));
+        if (rep_init(&s, &I) || !best || !sums) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = -2;
+            rep_free(&s); free(best); free(sums);
+            continue;
+        }
+        const uint32_t rep = replica_base + (uint32_t)r;
+        double Ebest = 0.0;
+        int64_t nflip = 0;
+        for (int64_t t = 0; t < T; ++t) {
+            int32_t na = 0;
+            int64_t k = da_step(&I, &s, beta[t], inc, seed, (uint32_t)t, rep, &na);
+            if (trace) trace[(int64_t)r * T + t] = (int32_t)k;
+            if (accepted) accepted[(int64_t)r * T + t] = na;
+            if (k >= 0) nflip++;
+            if (mode == ORC_MODE_F32 && recompute_every > 0 && (t + 1) % recompute_every == 0)
+                periodic_recompute(&I, &s, S, sums);
+            double E = tracked_energy(&I, &s);
+            if (E < Ebest) {
+                Ebest = E;
+                memcpy(best, s.x, (size_t)N);
+            }
+        }
+        if (E_final) E_final[r] = tracked_energy(&I, &s);
+        if (E_best) E_best[r] = Ebest;
+        if (x_final) pack_bits(s.x, N, x_final + (int64_t)r * words);
+        if (x_best) pack_bits(best, N, x_best + (int64_t)r * words);
+        if (flips) flips[r] = nflip;
+        rep_free(&s); free(best); free(sums);
+    }
+    inst_free(&I);
+    return err;
+}
+
+int orc_da_one_step(int64_t N, int mode, const void* Q, const uint32_t* x, uint32_t m,
+                    float beta, float inc, uint64_t seed, uint32_t t, uint32_t replica,
+                    int32_t* n_accepted)
+{
+    if (N < 1 || !Q || !x) return -2;
+    inst_t I;
+    if (inst_make(&I, N, mode, Q)) return -2;
+    rep_t s;
+    if (rep_init(&s, &I)) { rep_free(&s); inst_free(&I); return -2; }
+    for (int64_t i = 0; i < N; ++i) s.x[i] = (uint8_t)getbit(x, i);
+    /* fields of the given state, summed in index order */
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j) {
+            if (!s.x[j]) continue;
+            if (mode == ORC_MODE_INT) s.hi[i] += I.Wi[i * N + j];
+            else if (mode == ORC_MODE_F32) s.hf[i] = s.hf[i] + I.Wf[i * N + j];
+            else s.hd[i] += (double)I.Wf[i * N + j];
+        }
+    s.m = m;
+    int64_t k = da_step(&I, &s, beta, inc, seed, t, replica, n_accepted);
+    rep_free(&s); inst_free(&I);
+    return (int)k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: R runs, each from a random state; temperature t is one sweep
+ * over the variables in index order, proposing single flips. */
+int orc_sa_anneal(int64_t N, const float* Q, const float* beta, int64_t T, int32_t R,
+                  uint64_t seed, double* E_best, uint32_t* x_best, int nthreads)
+{
+    if (N < 1 || T < 0 || R < 0 || !Q) return -1;
+    inst_t I;
+    if (inst_make(&I, N, ORC_MODE_F64, Q)) return -2;
+    const int64_t words = (N + 31) / 32;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int32_t r = 0; r < R; ++r) {
+        uint8_t* x = (uint8_t*)calloc((size_t)N, 1);
+        uint8_t* best = (uint8_t*)calloc((size_t)N, 1);
+        double* h = (double*)calloc((size_t)N, sizeof(double));
+        if (!x || !best || !h) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = -2;
+            free(x); free(best); free(h);
+            continue;
+        }
+        for (int64_t i = 0; i < N; ++i)
+            x[i] = (uint8_t)(philox_word(seed, (uint32_t)(i / 4), 0u, (uint32_t)r, 4u, (int)(i % 4)) >> 31);
+        double E = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (!x[i]) continue;
+            E += (double)I.df[i];
+            for (int64_t j = 0; j < N; ++j) {
+                if (!x[j]) continue;
+                h[i] += (double)I.Wf[i * N + j];
+                if (j > i) E += (double)I.Wf[i * N + j];
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            if (x[i]) continue;
+            for (int64_t j = 0; j < N; ++j)
+                if (x[j]) h[i] += (double)I.Wf[i * N + j];
+        }
+        double Ebest = E;
+        memcpy(best, x, (size_t)N);
+        for (int64_t t = 0; t < T; ++t) {
+            for (int64_t i = 0; i < N; ++i) {
+                double v = (double)I.df[i] + h[i];
+                double dE = x[i] ? -v : v;
+                int acc = dE <= 0.0;
+                if (!acc) {
+                    float a = (float)(-(double)beta[t] * dE);
+                    uint32_t rw = philox_word(seed, (uint32_t)(i / 4), (uint32_t)t, (uint32_t)r, 5u, (int)(i % 4));
+                    acc = orc_uniform(rw) < orc_expf(a);
+                }
+                if (!acc) continue;
+                const double sg = x[i] ? -1.0 : 1.0;
+                for (int64_t j = 0; j < N; ++j) h[j] += sg * (double)I.Wf[i * N + j];
+                x[i] ^= 1;
+                E += dE;
+                if (E < Ebest) { Ebest = E; memcpy(best, x, (size_t)N); }
+            }
+        }
+        if (x_best) pack_bits(best, N, x_best + (int64_t)r * words);
+        if (E_best) {
+            uint32_t* packed = (uint32_t*)calloc((size_t)words, sizeof(uint32_t));
+            pack_bits(best, N, packed);
+            E_best[r] = orc_energy_f64(N, Q, packed);
+            free(packed);
+        }
+        free(x); free(best); free(h);
+    }
+    inst_free(&I);
+    return err;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PTDA: the DA step inside every replica, replica exchange between
+ * neighbouring temperatures after every sweep of N steps (Sec. II, PTDA;
+ * the exchange rule is the Metropolis swap of Algorithm 4). */
+int orc_ptda(int64_t N, int mode, const void* Q, const float* betas, int32_t K,
+             int64_t sweeps, float inc, int32_t L, uint64_t seed,
+             double* E_final, double* E_best, uint32_t* x_best, int32_t* temp_of,
+             int64_t* swaps, uint8_t* swap_trace, int nthreads)
+{
+    if (N < 1 || K < 1 || sweeps < 0 || L < 0 || !Q || !betas) return -1;
+    if (mode != ORC_MODE_INT && mode != ORC_MODE_F32) return -1;
+    inst_t I;
+    if (inst_make(&I, N, mode, Q)) return -2;
+    const int64_t words = (N + 31) / 32;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int32_t l = 0; l < L; ++l) {
+        rep_t* reps = (rep_t*)calloc((size_t)K, sizeof(rep_t));
+        uint8_t* best = (uint8_t*)calloc((size_t)(K * N), 1);
+        double* Ebest = (double*)calloc((size_t)K, sizeof(double));
+        int32_t* tof = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+        int32_t* at = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+        int bad = !reps || !best || !Ebest || !tof || !at;
+        for (int32_t k = 0; k < K && !bad; ++k) bad = rep_init(&reps[k], &I) != 0;
+        if (bad) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            err = -2;
+        } else {
+            for (int32_t k = 0; k < K; ++k) { tof[k] = k; at[k] = k; }
+            if (swaps) for (int32_t p = 0; p + 1 < K; ++p) swaps[(int64_t)l * (K - 1) + p] = 0;
+            for (int64_t sw = 0; sw < sweeps; ++sw) {
+                for (int32_t k = 0; k < K; ++k) {
+                    const float b = betas[tof[k]];
+                    const uint32_t rep = (uint32_t)(l * K + k);
+                    for (int64_t q = 0; q < N; ++q) {
+                        const uint32_t t = (uint32_t)(sw * N + q);
+                        da_step(&I, &reps[k], b, inc, seed, t, rep, NULL);
+                        double E = tracked_energy(&I, &reps[k]);
+                        if (E < Ebest[k]) { Ebest[k] = E; memcpy(best + (int64_t)k * N, reps[k].x, (size_t)N); }
+                    }
+                }
+                for (int32_t p = 0; p + 1 < K; ++p) {
+                    const int32_t a = at[p], c = at[p + 1];
+                    const double arg = ((double)betas[p] - (double)betas[p + 1]) *
+                                       (tracked_energy(&I, &reps[a]) - tracked_energy(&I, &reps[c]));
+                    int acc = arg >= 0.0;
+                    if (!acc) {
+                        uint32_t rw = philox_word(seed, (uint32_t)p, (uint32_t)sw, (uint32_t)l, 2u, 0);
+                        acc = orc_uniform(rw) < orc_expf((float)arg);
+                    }
+                    if (swap_trace) swap_trace[((int64_t)l * sweeps + sw) * (K - 1) + p] = (uint8_t)acc;
+                    if (acc) {
+                        at[p] = c; at[p + 1] = a;
+                        tof[a] = p + 1; tof[c] = p;
+                        if (swaps) swaps[(int64_t)l * (K - 1) + p]++;
+                    }
+                }
+            }
+            for (int32_t k = 0; k < K; ++k) {
+                const int64_t o = (int64_t)l * K + k;
+                if (E_final) E_final[o] = tracked_energy(&I, &reps[k]);
+                if (E_best) E_best[o] = Ebest[k];
+                if (x_best) pack_bits(best + (int64_t)k * N, N, x_best + o * words);
+                if (temp_of) temp_of[o] = tof[k];
+            }
+        }
+        if (reps) for (int32_t k = 0; k < K; ++k) rep_free(&reps[k]);
+        free(reps); free(best); free(Ebest); free(tof); free(at);
+    }
+    inst_free(&I);
+    return err;
+}

@@ -1,0 +1,221 @@
+"""Pins of the oracle's Digital Annealer step (Algorithm 2), SA (Algorithm 1) and PTDA.
+
+The DA step is pinned to its exact transition law: with acceptance
+probabilities A_i, a step flips k with probability
+sum_{S containing k} prod_{i in S} A_i prod_{i not in S} (1 - A_i) / |S| and
+flips nothing with probability prod_i (1 - A_i) (Eq. 2).  The A_i are built
+here from energy differences taken by brute force, not from the oracle's
+Delta E formula.  The dynamic offset is pinned by its zero-temperature closed
+form, the optimisation by brute-force ground states.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_1806_08815_gb300 import instances
+
+
+def _E(Q, x):
+    Qu = np.triu(Q.astype(np.float64))
+    x = x.astype(np.float64)
+    return float(x @ Qu @ x)
+
+
+def _accept_prob(orc, delta32, beta):
+    """P(u < p) for u uniform on {1..2^24} 2^-24 and p = exp(-beta delta) (fp32)."""
+    if delta32 <= 0:
+        return 1.0
+    a = np.float32(-(np.float32(beta) * np.float32(delta32)))
+    p = float(orc.expf(np.array([a]))[0])
+    return (math.ceil(p * 2 ** 24) - 1) / 2 ** 24
+
+
+def _exact_step_law(A):
+    N = len(A)
+    P = np.zeros(N + 1)     # P[N] = no flip
+    for S in itertools.product([0, 1], repeat=N):
+        pr = np.prod([A[i] if S[i] else 1 - A[i] for i in range(N)])
+        n = sum(S)
+        if n == 0:
+            P[N] += pr
+        else:
+            for i in range(N):
+                if S[i]:
+                    P[i] += pr / n
+    return P
+
+
+@pytest.mark.parametrize("integer,m,inc", [(True, 0, 0.0), (True, 2, 1.0), (False, 1, 0.5), (False, 0, 0.0)])
+def test_one_step_transition_law(orc, integer, m, inc):
+    N = 6
+    inst = instances.random_qubo(N, 21 + m, integer, -3, 3)
+    x = np.array([1, 0, 1, 1, 0, 0], np.uint8)
+    beta = 0.45
+    E0 = _E(inst.Q, x)
+    E_off = np.float32(np.float32(m) * np.float32(inc))
+    A = []
+    for i in range(N):
+        y = x.copy()
+        y[i] ^= 1
+        dE = np.float32(_E(inst.Q, y) - E0)        # Delta E by brute force
+        A.append(_accept_prob(orc, np.float32(dE - E_off), beta))
+    law = _exact_step_law(A)
+    n = 40_000
+    counts = np.zeros(N + 1)
+    xp = orc.pack(x)[0]
+    for rep in range(n):
+        k, _ = orc.da_one_step(inst.Q, xp, m, beta, inc, seed=12345, t=7, replica=rep)
+        counts[k if k >= 0 else N] += 1
+    keep = law * n > 5
+    chi2 = ((counts[keep] - n * law[keep]) ** 2 / (n * law[keep])).sum()
+    dof = keep.sum() - 1
+    assert stats.chi2.sf(chi2, dof) > 1e-3, (counts, n * law)
+    assert counts[~keep].sum() <= 10
+
+
+def test_infinite_temperature_choice_is_uniform(orc):
+    """At beta = 0 every trial is accepted (p = 1 > u except u = 1), so the flip is uniform."""
+    N = 24
+    inst = instances.random_qubo(N, 2, True)
+    xp = orc.pack(np.zeros(N, np.uint8))[0]
+    n = 48_000
+    counts = np.zeros(N)
+    for rep in range(n):
+        k, na = orc.da_one_step(inst.Q, xp, 0, 0.0, 0.0, seed=99, t=0, replica=rep)
+        assert na >= N - 1
+        counts[k] += 1
+    assert stats.chisquare(counts).pvalue > 1e-3
+
+
+def test_dynamic_offset_zero_temperature_closed_form(orc):
+    """x = 0 is a local minimum when every Q_ii > 0.  At beta -> infinity nothing is
+    accepted until E_off = m * inc reaches min_i Q_ii; the first flip then comes at
+    step m* = ceil(min Q_ii / inc) and picks one of the variables with Q_ii <= m* inc."""
+    N = 16
+    rng = np.random.default_rng(4)
+    Q = np.triu(rng.integers(-3, 4, (N, N)), 1).astype(np.int32)
+    diag = rng.integers(5, 30, N)
+    Q[np.arange(N), np.arange(N)] = diag
+    inc = 2.0
+    T = 40
+    beta = np.full(T, 1e6, np.float32)
+    out = orc.da_anneal(Q, beta, R=8, seed=3, inc=inc, trace=True)
+    mstar = math.ceil(diag.min() / inc)
+    for tr in out["trace"]:
+        assert np.all(tr[:mstar] == -1)
+        k = tr[mstar]
+        assert k >= 0 and diag[k] <= mstar * inc
+    # with the offset off nothing ever flips
+    out0 = orc.da_anneal(Q, beta, R=4, seed=3, inc=0.0, trace=True)
+    assert np.all(out0["trace"] == -1)
+
+
+def test_tracked_energy_is_exact_integer(orc):
+    inst = instances.sk_bimodal(48, 1)
+    beta = instances.beta_linear(0.05, 3.0, 3000)
+    out = orc.da_anneal(inst.Q, beta, R=6, seed=5, inc=1.0)
+    assert np.array_equal(out["E_final"].astype(np.int64), orc.energy(inst.Q, out["x_final"]))
+    assert np.array_equal(out["E_best"].astype(np.int64), orc.energy(inst.Q, out["x_best"]))
+    assert np.all(out["E_best"] <= out["E_final"])
+    assert np.all(out["flips"] > 0)
+
+
+def test_fp32_tracked_energy_and_recompute(orc):
+    inst = instances.sk_gaussian(64, 2)
+    beta = instances.beta_linear(0.5, 8.0, 4000)
+    for every in (0, 256):
+        out = orc.da_anneal(inst.Q, beta, R=4, seed=8, inc=0.0, recompute_every=every)
+        Eex = orc.energy(inst.Q, out["x_final"])
+        assert np.allclose(out["E_final"], Eex, rtol=1e-5, atol=1e-5)
+    # right after a recompute the tracked energy is the recompute energy
+    beta = instances.beta_linear(0.5, 8.0, 512)
+    out = orc.da_anneal(inst.Q, beta, R=3, seed=8, inc=0.0, recompute_every=256)
+    for r in range(3):
+        assert out["E_final"][r] == orc.recompute_energy_f32(inst.Q, out["x_final"][r])
+
+
+def test_modes_agree_statistically(orc):
+    """fp32 and fp64 fields take the same decisions except in rare near-ties."""
+    inst = instances.sk_gaussian(32, 5)
+    beta = instances.beta_linear(0.2, 6.0, 2000)
+    a = orc.da_anneal(inst.Q, beta, R=16, seed=1, mode=orc.MODE_F32, trace=True)
+    b = orc.da_anneal(inst.Q, beta, R=16, seed=1, mode=orc.MODE_F64, trace=True)
+    same = np.mean([np.array_equal(x, y) for x, y in zip(a["trace"], b["trace"])])
+    assert same >= 0.75
+
+
+def test_threads_do_not_change_results(orc):
+    inst = instances.sk_bimodal(40, 3)
+    beta = instances.beta_linear(0.05, 3.0, 800)
+    a = orc.da_anneal(inst.Q, beta, R=8, seed=2, inc=1.0, trace=True, nthreads=1)
+    b = orc.da_anneal(inst.Q, beta, R=8, seed=2, inc=1.0, trace=True, nthreads=4)
+    assert np.array_equal(a["trace"], b["trace"])
+    # replica r of a run equals replica 0 of a run with replica_base = r
+    c = orc.da_anneal(inst.Q, beta, R=1, seed=2, inc=1.0, trace=True, replica_base=5)
+    assert np.array_equal(a["trace"][5], c["trace"][0])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_da_finds_brute_force_ground_state(orc, seed):
+    N = 16
+    inst = instances.sk_bimodal(N, seed)
+    Emin, _, _ = orc.brute_force(inst.Q.astype(np.float64))
+    beta = instances.beta_linear(0.05, 3.0, 2000)
+    out = orc.da_anneal(inst.Q, beta, R=32, seed=seed, inc=1.0)
+    assert out["E_best"].min() == Emin
+    assert np.mean(out["E_best"] == Emin) >= 0.5
+    assert np.all(out["E_best"] >= Emin)
+
+
+def test_sa_finds_ground_state(orc):
+    N = 14
+    inst = instances.sk_gaussian(N, 4)
+    Emin, _, _ = orc.brute_force(inst.Q.astype(np.float64))
+    beta = instances.beta_linear(0.2, 12.0, 300)
+    out = orc.sa_anneal(inst.Q, beta, R=16, seed=2)
+    assert np.all(out["E_best"] >= Emin - 1e-9)
+    assert np.mean(np.abs(out["E_best"] - Emin) < 1e-9) >= 0.5
+    assert np.allclose(out["E_best"], orc.energy(inst.Q, out["x_best"]))
+
+
+def test_ptda_single_temperature_is_plain_da(orc):
+    """With K = 1 there is no exchange: ladder l is replica l of a plain DA run at fixed beta."""
+    inst = instances.sk_bimodal(24, 6)
+    sweeps = 30
+    pt = orc.ptda(inst.Q, np.array([1.3], np.float32), sweeps, L=5, seed=4)
+    da = orc.da_anneal(inst.Q, np.full(sweeps * inst.N, 1.3, np.float32), R=5, seed=4)
+    assert np.array_equal(pt["E_final"][:, 0], da["E_final"])
+    assert np.array_equal(pt["E_best"][:, 0], da["E_best"])
+
+
+def test_ptda_exchange_rate_matches_metropolis(orc):
+    """After one sweep, pair (0, 1) is swapped with probability
+    min(1, exp((b0 - b1)(E_0 - E_1))) given the two energies (Algorithm 4)."""
+    inst = instances.sk_bimodal(10, 7)
+    b = np.array([0.3, 0.9], np.float32)
+    L = 6000
+    pt = orc.ptda(inst.Q, b, 1, L=L, seed=11)
+    dE = pt["E_final"][:, 0] - pt["E_final"][:, 1]
+    arg = (np.float64(b[0]) - np.float64(b[1])) * dE
+    p = np.where(arg >= 0, 1.0, np.exp(np.minimum(arg, 0)))
+    acc = pt["swap_trace"][:, 0, 0].astype(float)
+    z = (acc.sum() - p.sum()) / math.sqrt((p * (1 - p)).sum())
+    assert abs(z) < 4.0
+    assert np.array_equal(pt["swaps"][:, 0], acc.astype(np.int64))
+    # swapped ladders exchange their temperature labels
+    assert np.all(np.sort(pt["temp_of"], axis=1) == np.arange(2))
+    assert np.array_equal(pt["temp_of"][:, 0] == 1, acc == 1)
+
+
+def test_ptda_finds_ground_state(orc):
+    N = 16
+    inst = instances.sk_bimodal(N, 9)
+    Emin, _, _ = orc.brute_force(inst.Q.astype(np.float64))
+    betas = instances.beta_geometric(0.2, 5.0, 8)
+    pt = orc.ptda(inst.Q, betas, 60, L=4, seed=3)
+    assert np.all(pt["E_best"].min(axis=1) == Emin)
+    assert np.array_equal(pt["E_best"].astype(np.int64).ravel(),
+                          orc.energy(inst.Q, pt["x_best"].reshape(-1, 1)).astype(np.int64))
