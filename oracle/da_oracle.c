@@ -77,9 +77,11 @@ static uint32_t draw_accept(uint64_t seed, int64_t i, uint32_t t, uint32_t rep)
     return philox_word(seed, c0, t, rep, 0u, (int)((i % 128) / 32));
 }
 
+/* The choice draw of step t: one Philox block serves four consecutive steps,
+ * counter (0, t - t % 4, replica, 1), output lane t % 4. */
 static uint32_t draw_choice(uint64_t seed, uint32_t t, uint32_t rep)
 {
-    return philox_word(seed, 0u, t, rep, 1u, 0);
+    return philox_word(seed, 0u, t & ~3u, rep, 1u, (int)(t & 3u));
 }
 
 float orc_uniform(uint32_t r)
