@@ -1,0 +1,301 @@
+"""Benchmark of the Digital Annealer hot path on one GB300 (or N, one process each).
+
+Workload (one "step" = one complete anneal): fully connected SK spin glass,
+N = 1024, Gaussian couplings J_ij ~ N(0, 1)/sqrt(N) in an fp32 QUBO (4 MB),
+1024 replicas, 2e5 DA steps, beta linear 0.1 -> 10, fp32 fields with the exact
+field recompute every 1024 steps.  Metric: single-flip trials per second,
+R * T * N / time, plus TTS99 from the hit rate of the best energy over all
+runs.  The instance is synthetic (seeded), standing in for the paper's SK
+instances.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1, beta1=10.0, inc=0.0,
+          instance_seed=0, seed=0)
+METRIC = "single-flip trials/s (DA step, SK-Gaussian N=1024, 1024 replicas, 2e5 steps)"
+UNIT = "trials/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def hbm_peak(peaks):
+    for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "hbm"):
+        v = peaks.get(k)
+        if isinstance(v, (int, float)):
+            return float(v)
+        if isinstance(v, dict):
+            for kk in ("gbs", "value", "GB/s"):
+                if isinstance(v.get(kk), (int, float)):
+                    return float(v[kk])
+    return 6800.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def tts99(best_E, tau_run):
+    """TTS99 = tau * R99 with theta from the Jeffreys posterior mean (Scaling Analysis section)."""
+    Eref = float(np.min(best_E))
+    tol = 1e-6 * max(1.0, abs(Eref))
+    y = int(np.sum(best_E <= Eref + tol))
+    r = len(best_E)
+    theta = (y + 0.5) / (r + 1.0)
+    R99 = math.log(1 - 0.99) / math.log(1 - theta) if theta < 1 else 1.0
+    return dict(E_ref=Eref, hits=y, runs=r, theta=theta, R99=R99, tts99_s=tau_run * R99)
+
+
+def cpu_baseline(sample_R=None, sample_T=16384):
+    """The oracle, as it stands, on the host cores over a bounded sample of the workload."""
+    import oracle
+    from paper_1806_08815_gb300 import instances
+    cores = os.cpu_count() or 1
+    R = sample_R or 2 * cores
+    q = instances.sk_gaussian(C3["N"], C3["instance_seed"])
+    beta = instances.beta_linear(C3["beta0"], C3["beta1"], C3["steps"])[:sample_T]
+    t0 = time.perf_counter()
+    oracle.da_anneal(q.Q, beta, R=R, seed=C3["seed"], inc=C3["inc"], recompute_every=C3["recompute_every"],
+                     nthreads=cores)
+    dt = time.perf_counter() - t0
+    trials = R * sample_T * C3["N"]
+    return {"value": trials / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{R} replicas x first {sample_T} of the 2e5 steps (N=1024 fp32, recompute every 1024), "
+                      f"{dt:.1f} s wall"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    res = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sample_T=1024 if i < args.warmup else 4096)
+        if i >= args.warmup:
+            res.append(cb)
+    v = statistics.median(r["value"] for r in res)
+    cb = res[-1]
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sk_gaussian_N1024_R1024_T2e5 (bounded sample on host cores)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steps-per-anneal", type=int, default=C3["steps"])
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1806_08815_gb300 import binding as da
+    from paper_1806_08815_gb300 import instances
+    da.lib()
+
+    dev = torch.device("cuda", local)
+    N, R, T, P = C3["N"], C3["replicas"], args.steps_per_anneal, C3["recompute_every"]
+    q = instances.sk_gaussian(N, C3["instance_seed"])
+    beta = instances.beta_linear(C3["beta0"], C3["beta1"], T)
+    seed = C3["seed"] + rank            # weak scaling: each rank anneals its own 1024 replicas
+    ctx = da.da_create(q.Q)
+    beta_dev = torch.from_numpy(beta).to(dev)
+    Wd = da.da_words(N)
+    out = dict(final_E=torch.zeros(R, dtype=torch.float64, device=dev),
+               best_E=torch.zeros(R, dtype=torch.float64, device=dev),
+               best_x=torch.zeros((R, Wd), dtype=torch.int32, device=dev),
+               max_drift=torch.zeros(R, dtype=torch.float64, device=dev),
+               flips=torch.zeros(R, dtype=torch.int64, device=dev))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+
+    def one_step():
+        da.da_anneal_async(ctx, beta_dev, T, C3["inc"], R, seed, P, out, stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    stream.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    da.da_profile_enable(ctx, True)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches, step_ms = da.da_profile_read(ctx)
+    da.da_profile_enable(ctx, False)
+    clk = clocks.stop()
+    t_step = float(np.mean(times))
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    trials = R * T * N
+    value = world * trials / t_step
+
+    best_E = out["best_E"].cpu().numpy()
+    drift = out["max_drift"].cpu().numpy()
+    tts = tts99(best_E, t_step / R)
+
+    # end to end through the blocking host API: Q and beta uploaded, results read back
+    e2e_times = []
+    res_bytes = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = da.da_create(q.Q)
+        r2 = da.da_anneal(c2, beta, C3["inc"], R, seed, recompute_every=P)
+        da.da_destroy(c2)
+        e2e_times.append(time.perf_counter() - t0)
+        res_bytes = sum(r2[k].nbytes for k in ("final_E", "best_E", "final_x", "best_x", "max_drift", "flips"))
+    e2e_v = world * trials / float(np.mean(e2e_times))
+
+    # roofline of the step kernel: nominal bytes per replica-step = one fp32 column of W
+    # (4N) plus the replica state (fields 4N + state bits N/8)
+    peaks, peak_src = load_peaks()
+    hbm = hbm_peak(peaks)
+    per_launch_steps = min(P, T)
+    bytes_per_launch = R * per_launch_steps * (4 * N + 4 * N + N // 8)
+    avg_launch_s = (step_ms / 1e3) / max(launches, 1)
+    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9
+    n_step_launches = math.ceil(T / P)
+    n_recompute = T // P
+    gpu_launches = n_step_launches + 2 * n_recompute + 2 + 1     # steps, recompute+energy, final eval, finalize
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sk_gaussian_N1024_R1024_T2e5", "N": N, "replicas": R, "steps_per_anneal": T,
+                   "recompute_every": P, "beta": f"linear {C3['beta0']} -> {C3['beta1']}",
+                   "offset_inc": C3["inc"], "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) before every timed step"},
+        "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(q.Q.nbytes + beta.nbytes),
+                "d2h_bytes_per_step": int(res_bytes)},
+        "gpu_launches": gpu_launches * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm, "traffic": None,
+                     "kernel": "step_kernel<float,V=32,G=1>", "peak_source": peak_src,
+                     "basis": "nominal bytes per replica-step: fp32 column of W + fields + state bits"},
+        "step_kernel": {"launches": launches, "avg_launch_ms": avg_launch_s * 1e3,
+                        "share_of_step": (step_ms / 1e3) / (t_step * args.steps)},
+        "tts99": tts,
+        "max_fp32_drift": float(drift.max()),
+    }
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * da.h -- C ABI of a GB300 (sm_103a) library for the Digital Annealer's
+ * method: the parallel-trial Monte Carlo step on a dense QUBO with a dynamic
+ * offset, run over many replicas, and its parallel-tempering variant (PTDA).
+ *
+ * Paper: M. Aramon, G. Rosenberg, E. Valiante, T. Miyazawa, H. Tamura,
+ * H. G. Katzgraber, "Physics-Inspired Optimization for Quadratic
+ * Unconstrained Problems Using a Digital Annealer", arXiv:1806.08815.
+ *
+ * General conventions
+ *  - Every entry point returns a da_status and never aborts.  On failure a
+ *    description is available from da_last_error() (per calling thread).
+ *  - "host" pointers are ordinary CPU memory owned by the caller; the library
+ *    copies what it needs before returning (or, for the *_async calls, before
+ *    the queued work reads it).  "device" pointers are CUDA global memory of
+ *    the current device, owned by the caller.  The library owns all other
+ *    device memory it uses (its context's copies of the instance and its
+ *    workspace) and frees it in da_destroy.
+ *  - A QUBO is an N x N row-major matrix Q of which only the upper triangle
+ *    (i <= j) is read: Q_ii are the linear terms and Q_ij (i < j) the
+ *    couplings of E(x) = sum_i Q_ii x_i + sum_{i<j} Q_ij x_i x_j over
+ *    x in {0,1}^N ("Benchmarking Problems": the QUBO form the DA optimises,
+ *    obtained from Eq. 4 with s = 2x - 1).
+ *  - A state is bit-packed in 32-bit words: x_i is bit (i % 32) of word
+ *    (i / 32); a state of N variables takes da_words(N) = ceil(N / 32) words.
+ *  - Calls on one da_ctx are serialised by the context (thread-safe); the
+ *    *_async calls only order work on the caller's stream, so concurrent
+ *    async calls on one context must use one stream.
+ *  - No CPU fallback: without a usable CUDA device every call that computes
+ *    returns DA_ECUDA.
+ */
+#ifndef DA_H
+#define DA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct da_ctx da_ctx;
+
+typedef enum da_dtype {
+    DA_INT8 = 0, /* integer couplings (e.g. bimodal +-1 -> +-4): int8 W, int32 fields, exact */
+    DA_FP32 = 1  /* real couplings (e.g. Gaussian): fp32 W and fields, fp64 energies */
+} da_dtype;
+
+typedef enum da_status {
+    DA_OK = 0,
+    DA_EINVAL = 1,    /* an argument is out of range; nothing was done */
+    DA_ENOMEM = 2,    /* a device or host allocation failed */
+    DA_EBUDGET = 3,   /* the request can never fit the device-memory budget */
+    DA_EBUSY = 4,     /* the context is in use by an incompatible call */
+    DA_ETIMEOUT = 5,  /* a bounded wait ran out */
+    DA_ECUDA = 6,     /* a CUDA call failed (no device, launch error, ...) */
+    DA_ENOTREADY = 7  /* asynchronous work has not finished yet */
+} da_status;
+
+/* Results of da_anneal, one entry per replica r (host arrays, caller-allocated;
+ * every pointer may be NULL to skip that output). */
+typedef struct da_result {
+    double* final_E;    /* [R] exact energy of the final state (int64 sum for DA_INT8;
+                           exact fixed-point fields then fp64 for DA_FP32) */
+    double* best_E;     /* [R] exact energy of the lowest-energy state the run visited */
+    uint32_t* final_x;  /* [R * da_words(N)] final state */
+    uint32_t* best_x;   /* [R * da_words(N)] best state */
+    double* max_drift;  /* [R] |tracked energy - exact energy| of the final state
+                           (the fp32 accumulation error; 0 for DA_INT8) */
+    int64_t* flips;     /* [R] number of accepted (applied) flips */
+    int32_t* trace;     /* [R * steps] index flipped at every step, -1 if none was
+                           accepted (debug output; slows the run) */
+    double elapsed_s;   /* written by the call: device time of the anneal */
+} da_result;
+
+/* Device-side results of da_anneal_async (device arrays, caller-allocated,
+ * each may be NULL).  Same meaning as in da_result. */
+typedef struct da_dev_result {
+    double* final_E;
+    double* best_E;
+    uint32_t* final_x;
+    uint32_t* best_x;
+    double* max_drift;
+    int64_t* flips;
+    int32_t* trace;
+} da_dev_result;
+
+/* Results of da_pt: L ladders of K replicas; replica k of ladder l is entry
+ * l*K + k.  Host arrays, caller-allocated, each may be NULL. */
+typedef struct da_pt_result {
+    double* final_E;     /* [L*K] exact energy of each replica's final state */
+    double* best_E;      /* [L*K] exact energy of each replica's best state */
+    uint32_t* best_x;    /* [L*K*da_words(N)] */
+    int32_t* temp_of;    /* [L*K] final temperature index of each replica */
+    int64_t* swaps;      /* [L*(K-1)] accepted exchanges of each neighbouring pair */
+    uint8_t* swap_trace; /* [L*sweeps*(K-1)] 1 where the exchange of pair p after a
+                            sweep was accepted (debug output) */
+    double elapsed_s;    /* written by the call: device time */
+} da_pt_result;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int da_version(void);
+
+/* Words of a bit-packed state of N variables: ceil(N / 32). */
+int64_t da_words(int64_t N);
+
+/* Description of the last failure on the calling thread ("" if none).  The
+ * string stays valid until the next call on this thread. */
+const char* da_last_error(void);
+
+/* Create a context holding one QUBO instance on the current CUDA device.
+ *   Q      host, N x N row-major (int32_t for DA_INT8, float for DA_FP32);
+ *          the upper triangle is read and copied, the caller keeps Q.
+ *   N      1 <= N <= 8192 (the next-generation DA size named in Sec. II).
+ *   dtype  DA_INT8 requires every coupling in [-128, 127] and every
+ *          |Q_ii| + sum_j |Q_ij| < 2^24 (so that every Delta E is exact in
+ *          fp32); DA_FP32 requires finite values.
+ * The library stores W (symmetric, zero diagonal) and diag(Q) in device
+ * memory.  Errors: DA_EINVAL (bad N, dtype, range), DA_ENOMEM, DA_ECUDA. */
+da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out);
+
+/* Release a context and its device memory (NULL is ignored). */
+void da_destroy(da_ctx* ctx);
+
+/* N and dtype of a context. */
+da_status da_ctx_info(const da_ctx* ctx, int64_t* N, da_dtype* dtype);
+
+/* Fix the launch shape of the step kernel for this context instead of the
+ * automatic choice: a group of G warps per replica, V variables per lane
+ * (32 * V * G >= N), rpb replicas per thread block.  Supported: G = 1 with
+ * V in {2, 4, 8, 16, 32}; G in {2, 4, 8} with V in {4, 8, 16, 32}; at most
+ * 1024 threads per block.  V = 0 restores the automatic choice.  Results do
+ * not depend on the shape (the random numbers are keyed by variable index,
+ * step and replica).  Errors: DA_EINVAL. */
+da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);
+
+/* Run the Digital Annealer (Algorithm 2) R times from x = 0 (all runs start
+ * from one state, Sec. II) for `steps` iterations, blocking until done.
+ *   beta_schedule  host, [steps] inverse temperature of every step (the
+ *                  temperature is updated every iteration, "DA parameters").
+ *   offset_inc     dynamic-offset increase rate: after m steps without an
+ *                  accepted flip the trials use Delta E - m * offset_inc;
+ *                  0 switches the offset off (as in the paper's runs).
+ *   replicas       R >= 1 independent runs.
+ *   seed           Philox key; run r draws its numbers with replica id r, so
+ *                  results do not depend on R, on the launch shape or on the
+ *                  device.
+ *   recompute_every  DA_FP32 only: recompute the fields exactly every this many
+ *                  steps to bound the fp32 drift (0 = never).  Ignored for
+ *                  DA_INT8, whose fields are exact.
+ * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+da_status da_anneal(da_ctx* ctx, const float* beta_schedule, int64_t steps, float offset_inc,
+                    int32_t replicas, uint64_t seed, int64_t recompute_every, da_result* out);
+
+/* As da_anneal, with the schedule and every output in device memory, queued
+ * on `stream` (a cudaStream_t; NULL = the legacy default stream) and
+ * returning without waiting.  The context's workspace is reused: calls on one
+ * context must be ordered on one stream. */
+da_status da_anneal_async(da_ctx* ctx, const float* beta_schedule_dev, int64_t steps, float offset_inc,
+                          int32_t replicas, uint64_t seed, int64_t recompute_every,
+                          const da_dev_result* out, void* stream);
+
+/* Parallel tempering with the DA step (PTDA, Sec. II and Algorithm 4): L
+ * independent ladders of K replicas at inverse temperatures betas[0..K-1]
+ * (host, ascending), replica k starting at index k from x = 0.  A sweep is N DA
+ * steps of every replica; after each sweep the pairs (0,1), (1,2), ...,
+ * (K-2,K-1) propose, in order, to swap their temperatures with probability
+ * min(1, exp((beta_p - beta_{p+1})(E_p - E_{p+1}))).  Blocking.
+ * Errors: DA_EINVAL (K < 1, betas not ascending, ...), DA_ENOMEM, DA_ECUDA. */
+da_status da_pt(da_ctx* ctx, const float* betas, int32_t K, int64_t sweeps, int32_t ladders,
+                float offset_inc, uint64_t seed, da_pt_result* out);
+
+/* Exact energies of R bit-packed host states x[R * da_words(N)] into E[R]
+ * (host).  Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+da_status da_energy(da_ctx* ctx, const uint32_t* x, int32_t R, double* E);
+
+/* The field recompute of R host states: h[R * N] (host; int32_t for DA_INT8,
+ * float for DA_FP32), exactly as used between steps.  Errors as da_energy. */
+da_status da_field_recompute(da_ctx* ctx, const uint32_t* x, int32_t R, void* h);
+
+/* Per-launch timing of the step kernel: while enabled, every step-kernel
+ * launch of this context is bracketed by CUDA events on the stream it runs
+ * on.  da_profile_read waits for the recorded launches, returns their count
+ * and summed device time, and starts a new count.  Enabling resets the
+ * count.  Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_profile_enable(da_ctx* ctx, int32_t on);
+da_status da_profile_read(da_ctx* ctx, int64_t* launches, double* total_ms);
+
+/* Diagnostics: run the device's own fp32 exponential (used for every
+ * Metropolis decision) on n host values x[n] -> y[n], and its Philox4x32-10
+ * (Salmon et al., SC'11) on n host records ctr_key[6n] = (c0, c1, c2, c3, k0,
+ * k1) -> out[4n].  For testing the device arithmetic against independent
+ * implementations.  Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_diag_expf(const float* x, float* y, int64_t n);
+da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DA_H */

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of the C ABI in include/da.h (argument marshalling only).
+
+Every function here calls the CUDA library libda.so; there is no CPU path.
+If the library has not been built, importing raises at the first call with
+instructions, and on a machine without a CUDA device the library returns
+DA_ECUDA, which is raised as DAError.
+
+Names follow the C ABI: da_create, da_anneal, da_anneal_async, da_pt,
+da_energy, da_field_recompute, da_set_launch_shape, da_destroy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libda.so")
+
+DA_INT8, DA_FP32 = 0, 1
+STATUS = {0: "DA_OK", 1: "DA_EINVAL", 2: "DA_ENOMEM", 3: "DA_EBUDGET", 4: "DA_EBUSY",
+          5: "DA_ETIMEOUT", 6: "DA_ECUDA", 7: "DA_ENOTREADY"}
+
+
+class DAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+
+
+class da_result(ctypes.Structure):
+    _fields_ = [("final_E", _P), ("best_E", _P), ("final_x", _P), ("best_x", _P),
+                ("max_drift", _P), ("flips", _P), ("trace", _P), ("elapsed_s", ctypes.c_double)]
+
+
+class da_dev_result(ctypes.Structure):
+    _fields_ = [("final_E", _P), ("best_E", _P), ("final_x", _P), ("best_x", _P),
+                ("max_drift", _P), ("flips", _P), ("trace", _P)]
+
+
+class da_pt_result(ctypes.Structure):
+    _fields_ = [("final_E", _P), ("best_E", _P), ("best_x", _P), ("temp_of", _P),
+                ("swaps", _P), ("swap_trace", _P), ("elapsed_s", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libda.so (built by __graft_entry__.build() / paper_1806_08815_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, u64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+    L.da_version.restype = ctypes.c_int
+    L.da_words.argtypes = [i64]
+    L.da_words.restype = i64
+    L.da_last_error.restype = ctypes.c_char_p
+    L.da_create.argtypes = [_P, i64, ctypes.c_int, ctypes.POINTER(_P)]
+    L.da_destroy.argtypes = [_P]
+    L.da_destroy.restype = None
+    L.da_ctx_info.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
+    L.da_set_launch_shape.argtypes = [_P, i32, i32, i32]
+    L.da_anneal.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_result)]
+    L.da_anneal_async.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_dev_result), _P]
+    L.da_pt.argtypes = [_P, _P, i32, i64, i32, f32, u64, ctypes.POINTER(da_pt_result)]
+    L.da_energy.argtypes = [_P, _P, i32, _P]
+    L.da_field_recompute.argtypes = [_P, _P, i32, _P]
+    L.da_profile_enable.argtypes = [_P, i32]
+    L.da_profile_read.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+    L.da_profile_enable.restype = ctypes.c_int
+    L.da_profile_read.restype = ctypes.c_int
+    L.da_diag_expf.argtypes = [_P, _P, i64]
+    L.da_diag_philox.argtypes = [_P, _P, i64]
+    for name in ("da_diag_expf", "da_diag_philox", "da_create", "da_ctx_info", "da_set_launch_shape", "da_anneal", "da_anneal_async", "da_pt",
+                 "da_energy", "da_field_recompute"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise DAError(status, lib().da_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(_P)
+    return _P(int(a.data_ptr()))      # torch tensor (device or host)
+
+
+def da_words(N: int) -> int:
+    return int(lib().da_words(int(N)))
+
+
+class Context:
+    """One QUBO instance resident on the device (wraps da_ctx*)."""
+
+    def __init__(self, handle, N: int, dtype: int):
+        self.handle = handle
+        self.N = N
+        self.dtype = dtype
+
+    def __del__(self):
+        try:
+            da_destroy(self)
+        except Exception:
+            pass
+
+
+def da_create(Q: np.ndarray) -> Context:
+    """Q: N x N upper-triangular QUBO, int32 (-> DA_INT8) or float32 (-> DA_FP32)."""
+    Q = np.asarray(Q)
+    N = Q.shape[0]
+    if Q.ndim != 2 or Q.shape[1] != N:
+        raise ValueError("Q must be N x N")
+    dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
+    Qc = np.ascontiguousarray(Q, dtype=np.int32 if dtype == DA_INT8 else np.float32)
+    h = _P()
+    _check(lib().da_create(_ptr(Qc), N, dtype, ctypes.byref(h)))
+    return Context(h, N, dtype)
+
+
+def da_destroy(ctx: Context):
+    if ctx.handle:
+        lib().da_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def da_set_launch_shape(ctx: Context, V: int = 0, G: int = 0, rpb: int = 0):
+    _check(lib().da_set_launch_shape(ctx.handle, V, G, rpb))
+
+
+def da_anneal(ctx: Context, beta: np.ndarray, offset_inc: float, replicas: int, seed: int,
+              recompute_every: int = 0, trace: bool = False) -> dict:
+    """Blocking anneal; returns numpy arrays (see da_result in include/da.h)."""
+    b = np.ascontiguousarray(beta, dtype=np.float32)
+    R, T, W = int(replicas), b.size, da_words(ctx.N)
+    out = dict(final_E=np.zeros(R), best_E=np.zeros(R), final_x=np.zeros((R, W), np.uint32),
+               best_x=np.zeros((R, W), np.uint32), max_drift=np.zeros(R), flips=np.zeros(R, np.int64))
+    if trace:
+        out["trace"] = np.zeros((R, T), np.int32)
+    res = da_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                  "flips", "trace")), 0.0)
+    _check(lib().da_anneal(ctx.handle, _ptr(b), T, float(offset_inc), R, int(seed) & (2 ** 64 - 1),
+                           int(recompute_every), ctypes.byref(res)))
+    out["elapsed_s"] = res.elapsed_s
+    return out
+
+
+def da_anneal_async(ctx: Context, beta_dev, steps: int, offset_inc: float, replicas: int, seed: int,
+                    recompute_every: int, out: dict, stream) -> None:
+    """Queue an anneal on `stream` (torch.cuda.Stream or raw handle); `beta_dev` and the
+    tensors in `out` (keys as da_dev_result) are device tensors owned by the caller."""
+    res = da_dev_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                      "flips", "trace")))
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().da_anneal_async(ctx.handle, _ptr(beta_dev), int(steps), float(offset_inc), int(replicas),
+                                 int(seed) & (2 ** 64 - 1), int(recompute_every), ctypes.byref(res),
+                                 _P(int(handle) if handle else 0)))
+
+
+def da_pt(ctx: Context, betas: np.ndarray, sweeps: int, ladders: int, seed: int, offset_inc: float = 0.0,
+          swap_trace: bool = False) -> dict:
+    b = np.ascontiguousarray(betas, dtype=np.float32)
+    K, L, W = b.size, int(ladders), da_words(ctx.N)
+    out = dict(final_E=np.zeros((L, K)), best_E=np.zeros((L, K)), best_x=np.zeros((L, K, W), np.uint32),
+               temp_of=np.zeros((L, K), np.int32), swaps=np.zeros((L, max(K - 1, 0)), np.int64))
+    if swap_trace:
+        out["swap_trace"] = np.zeros((L, sweeps, max(K - 1, 0)), np.uint8)
+    res = da_pt_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "best_x", "temp_of", "swaps",
+                                                     "swap_trace")), 0.0)
+    _check(lib().da_pt(ctx.handle, _ptr(b), K, int(sweeps), L, float(offset_inc), int(seed) & (2 ** 64 - 1),
+                       ctypes.byref(res)))
+    out["elapsed_s"] = res.elapsed_s
+    return out
+
+
+def da_energy(ctx: Context, x: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.uint32)
+    E = np.zeros(xs.shape[0])
+    _check(lib().da_energy(ctx.handle, _ptr(xs), xs.shape[0], _ptr(E)))
+    return E
+
+
+def da_field_recompute(ctx: Context, x: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.uint32)
+    h = np.zeros((xs.shape[0], ctx.N), np.int32 if ctx.dtype == DA_INT8 else np.float32)
+    _check(lib().da_field_recompute(ctx.handle, _ptr(xs), xs.shape[0], _ptr(h)))
+    return h
+
+
+def da_diag_expf(x: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    y = np.empty_like(xs)
+    _check(lib().da_diag_expf(_ptr(xs), _ptr(y), xs.size))
+    return y
+
+
+def da_diag_philox(ctr_key: np.ndarray) -> np.ndarray:
+    """ctr_key: [n, 6] uint32 (c0..c3, k0, k1) -> [n, 4] uint32."""
+    ck = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.empty((ck.shape[0], 4), np.uint32)
+    _check(lib().da_diag_philox(_ptr(ck), _ptr(out), ck.shape[0]))
+    return out
+
+
+def da_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().da_profile_enable(ctx.handle, 1 if on else 0))
+
+
+def da_profile_read(ctx: Context):
+    """(launches, summed device ms) of the step-kernel launches since the last read."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(lib().da_profile_read(ctx.handle, ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value

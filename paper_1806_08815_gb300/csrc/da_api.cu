@@ -1,0 +1,651 @@
+// da_api.cu -- the C ABI of include/da.h: instance contexts, the blocking and
+// asynchronous anneal, PTDA, exact energies and the field recompute.
+//
+// Runtime layout in HBM (per call, in the context's workspace):
+//   h      [R][npad]   int32 / fp32 fields between step launches
+//   xs     [2R][nw]    current states, then best states (adjacent, so the
+//                      final exact evaluation treats them as 2R states)
+//   sc     [R]         ReplicaScalars (tracked E, best E, flips, offset count)
+//   sums_t [N][2R]     int64 scratch of the exact recompute
+//   E_ex   [2R]        exact energies of the final and best states
+// The instance itself (symmetric W with row pitch ldw, and diag) lives in the
+// context for its whole life.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "da.h"
+#include "da_internal.h"
+
+using da::ReplicaScalars;
+using da::StepParams;
+using da::StepShape;
+
+namespace {
+
+thread_local std::string g_err;
+
+da_status fail(da_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define DA_CU(call)                                                                                    \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(DA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct da_ctx {
+    int N = 0;
+    da_dtype dtype = DA_INT8;
+    int ldw = 0;
+    int S = 0;  // fixed-point scale of the fp32 recompute
+    int device = 0;
+    void* W = nullptr;
+    void* diag = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    StepShape forced;  // V = 0: automatic
+    // optional per-launch timing of the step kernel (da_profile_*)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;  // pairs around step launches
+    size_t prof_used = 0;
+    std::mutex mu;
+};
+
+namespace {
+
+bool is_int8(const da_ctx* c) { return c->dtype == DA_INT8; }
+
+StepShape auto_shape(int N)
+{
+    StepShape s;
+    if (N <= 1024) {
+        int V = 2;
+        while (32 * V < N) V *= 2;
+        s.V = V;
+        s.G = 1;
+        s.rpb = 4;
+    } else {
+        int G = 2;
+        while (32 * 32 * G < N) G *= 2;
+        s.V = 32;
+        s.G = G;
+        s.rpb = G == 2 ? 2 : 1;
+    }
+    return s;
+}
+
+StepShape shape_for(const da_ctx* c)
+{
+    if (c->forced.V > 0) return c->forced;
+    return auto_shape(c->N);
+}
+
+da_status ensure_ws(da_ctx* c, size_t bytes)
+{
+    if (bytes <= c->ws_bytes) return DA_OK;
+    if (c->ws) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DA_ENOMEM, std::string("workspace of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+    }
+    c->ws_bytes = bytes;
+    return DA_OK;
+}
+
+// Workspace carve-up for one anneal-like call.
+struct Layout {
+    size_t h, xs, sc, sums, eex, beta, res, trace, pt, total;
+};
+
+Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_beta, bool with_trace, size_t pt_bytes)
+{
+    Layout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    L.h = take((size_t)R * s.npad() * 4);
+    L.xs = take((size_t)2 * R * s.nwords() * 4);
+    L.sc = take((size_t)R * sizeof(ReplicaScalars));
+    L.sums = take((size_t)c->N * 2 * R * 8);
+    L.eex = take((size_t)2 * R * 8);
+    L.beta = take(with_beta ? (size_t)T * 4 : 0);
+    L.res = take((size_t)4 * R * 8);
+    L.trace = take(with_trace ? (size_t)R * T * 4 : 0);
+    L.pt = take(pt_bytes);
+    L.total = o;
+    return L;
+}
+
+__global__ void finalize_kernel(bool int8, int R, const ReplicaScalars* sc, const long long* eex, double* final_E,
+                                double* best_E, double* drift, int64_t* flips)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double ef, eb, tracked;
+    if (int8) {
+        ef = (double)eex[r];
+        eb = (double)eex[R + r];
+        tracked = (double)sc[r].E;
+    } else {
+        ef = __longlong_as_double(eex[r]);
+        eb = __longlong_as_double(eex[R + r]);
+        tracked = __longlong_as_double(sc[r].E);
+    }
+    if (final_E) final_E[r] = ef;
+    if (best_E) best_E[r] = eb;
+    if (drift) drift[r] = fabs(tracked - ef);
+    if (flips) flips[r] = sc[r].flips;
+}
+
+struct RunBuffers {
+    char* base;
+    Layout L;
+    StepShape s;
+    int R;
+    void* h() const { return base + L.h; }
+    uint32_t* x() const { return reinterpret_cast<uint32_t*>(base + L.xs); }
+    uint32_t* bestx() const { return x() + (size_t)R * s.nwords(); }
+    ReplicaScalars* sc() const { return reinterpret_cast<ReplicaScalars*>(base + L.sc); }
+    long long* sums() const { return reinterpret_cast<long long*>(base + L.sums); }
+    long long* eex() const { return reinterpret_cast<long long*>(base + L.eex); }
+};
+
+StepParams base_params(const da_ctx* c, const RunBuffers& b)
+{
+    StepParams p;
+    p.W = c->W;
+    p.diag = c->diag;
+    p.N = c->N;
+    p.ldw = c->ldw;
+    p.R = b.R;
+    p.npad = b.s.npad();
+    p.nw = b.s.nwords();
+    p.h = b.h();
+    p.x = b.x();
+    p.bestx = b.bestx();
+    p.sc = b.sc();
+    return p;
+}
+
+// Zero the replica state: x = 0, h = 0, E = 0 (all runs start from the same
+// state, Sec. II).
+da_status reset_state(const RunBuffers& b, cudaStream_t st)
+{
+    DA_CU(cudaMemsetAsync(b.h(), 0, (size_t)b.R * b.s.npad() * 4, st));
+    DA_CU(cudaMemsetAsync(b.x(), 0, (size_t)2 * b.R * b.s.nwords() * 4, st));
+    DA_CU(cudaMemsetAsync(b.sc(), 0, (size_t)b.R * sizeof(ReplicaScalars), st));
+    return DA_OK;
+}
+
+// Exact energies of the final and best states into eex[0..2R).
+da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
+{
+    DA_CU(da::launch_recompute(is_int8(c), c->W, c->diag, c->N, c->ldw, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
+                               b.s.npad(), b.eex(), 1, st, b.sums()));
+    return DA_OK;
+}
+
+// Next free pair of profiling events (created on first use).
+da_status prof_pair(da_ctx* c, cudaEvent_t* a, cudaEvent_t* b)
+{
+    while (c->prof_used + 2 > c->prof_ev.size()) {
+        cudaEvent_t e;
+        DA_CU(cudaEventCreate(&e));
+        c->prof_ev.push_back(e);
+    }
+    *a = c->prof_ev[c->prof_used];
+    *b = c->prof_ev[c->prof_used + 1];
+    c->prof_used += 2;
+    return DA_OK;
+}
+
+// The anneal loop proper: steps [0, T) in launches that end at every
+// recompute point (fp32) or every 2^14 steps.
+da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long long T, float inc, uint64_t seed,
+                     long long recompute_every, int* trace_dev, cudaStream_t st)
+{
+    StepParams p = base_params(c, b);
+    p.beta = beta_dev;
+    p.inc = inc;
+    p.seed = seed;
+    p.rep_base = 0;
+    p.trace = trace_dev;
+    p.trace_T = T;
+    const bool rec = !is_int8(c) && recompute_every > 0;
+    for (long long t0 = 0; t0 < T; t0 = p.t1) {
+        p.t0 = t0;
+        p.t1 = std::min(T, t0 + (1ll << 14));
+        if (rec) p.t1 = std::min(p.t1, (t0 / recompute_every + 1) * recompute_every);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->prof) {
+            if (da_status e = prof_pair(c, &e0, &e1)) return e;
+            DA_CU(cudaEventRecord(e0, st));
+        }
+        DA_CU(da::launch_step(is_int8(c), b.s, p, trace_dev != nullptr, st));
+        if (e1) DA_CU(cudaEventRecord(e1, st));
+        if (rec && p.t1 % recompute_every == 0) {
+            DA_CU(da::launch_recompute(false, c->W, c->diag, c->N, c->ldw, c->S, b.x(), b.s.nwords(), b.R, b.h(),
+                                       b.s.npad(), reinterpret_cast<long long*>(b.sc()),
+                                       (int)(sizeof(ReplicaScalars) / 8), st, b.sums()));
+        }
+    }
+    return DA_OK;
+}
+
+da_status check_ctx(const da_ctx* c)
+{
+    if (!c) return fail(DA_EINVAL, "null context");
+    return DA_OK;
+}
+
+struct CtxLock {
+    da_ctx* c;
+    explicit CtxLock(da_ctx* cc) : c(cc)
+    {
+        c->mu.lock();
+        cudaSetDevice(c->device);
+    }
+    ~CtxLock() { c->mu.unlock(); }
+};
+
+}  // namespace
+
+extern "C" {
+
+int da_version(void) { return 100; }
+
+int64_t da_words(int64_t N) { return N <= 0 ? 0 : (N + 31) / 32; }
+
+const char* da_last_error(void) { return g_err.c_str(); }
+
+da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
+{
+    g_err.clear();
+    if (!out) return fail(DA_EINVAL, "out is null");
+    *out = nullptr;
+    if (!Q) return fail(DA_EINVAL, "Q is null");
+    if (N < 1 || N > 8192) return fail(DA_EINVAL, "N must be in [1, 8192]");
+    if (dtype != DA_INT8 && dtype != DA_FP32) return fail(DA_EINVAL, "unknown dtype");
+    const int n = (int)N;
+    const int ldw = (int)align_up((size_t)n, 128);
+    const size_t esz = dtype == DA_INT8 ? 1 : 4;
+    std::vector<char> Wh((size_t)n * ldw * esz, 0);
+    std::vector<char> dh((size_t)n * 4, 0);
+    float amax = 0.f;
+    if (dtype == DA_INT8) {
+        const int32_t* q = static_cast<const int32_t*>(Q);
+        int8_t* w = reinterpret_cast<int8_t*>(Wh.data());
+        int32_t* d = reinterpret_cast<int32_t*>(dh.data());
+        std::vector<long long> rowabs(n, 0);
+        for (int i = 0; i < n; ++i) {
+            d[i] = q[(size_t)i * n + i];
+            rowabs[i] += std::llabs((long long)d[i]);
+            for (int j = i + 1; j < n; ++j) {
+                const int32_t v = q[(size_t)i * n + j];
+                if (v < -128 || v > 127)
+                    return fail(DA_EINVAL, "DA_INT8 coupling Q[" + std::to_string(i) + "][" + std::to_string(j) +
+                                               "] = " + std::to_string(v) + " outside [-128, 127]");
+                w[(size_t)i * ldw + j] = (int8_t)v;
+                w[(size_t)j * ldw + i] = (int8_t)v;
+                rowabs[i] += std::abs(v);
+                rowabs[j] += std::abs(v);
+            }
+        }
+        for (int i = 0; i < n; ++i)
+            if (rowabs[i] >= (1ll << 24))
+                return fail(DA_EINVAL, "DA_INT8 row " + std::to_string(i) + ": |Q_ii| + sum |Q_ij| >= 2^24");
+    } else {
+        const float* q = static_cast<const float*>(Q);
+        float* w = reinterpret_cast<float*>(Wh.data());
+        float* d = reinterpret_cast<float*>(dh.data());
+        for (int i = 0; i < n; ++i) {
+            d[i] = q[(size_t)i * n + i];
+            if (!std::isfinite(d[i])) return fail(DA_EINVAL, "non-finite Q entry");
+            for (int j = i + 1; j < n; ++j) {
+                const float v = q[(size_t)i * n + j];
+                if (!std::isfinite(v)) return fail(DA_EINVAL, "non-finite Q entry");
+                w[(size_t)i * ldw + j] = v;
+                w[(size_t)j * ldw + i] = v;
+                amax = std::max(amax, std::fabs(v));
+            }
+        }
+    }
+    int dev = 0;
+    DA_CU(cudaGetDevice(&dev));
+    da_ctx* c = new (std::nothrow) da_ctx;
+    if (!c) return fail(DA_ENOMEM, "host allocation");
+    c->N = n;
+    c->dtype = dtype;
+    c->ldw = ldw;
+    c->device = dev;
+    c->S = dtype == DA_FP32 ? da::fix_scale(amax, n) : 0;
+    auto bail = [&](da_status s, const std::string& m) {
+        da_destroy(c);
+        return fail(s, m);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) return bail(DA_ECUDA, std::string("stream/event: ") + cudaGetErrorString(e));
+    e = cudaMalloc(&c->W, Wh.size());
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag, dh.size());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(DA_ENOMEM, std::string("instance: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
+    *out = c;
+    return DA_OK;
+}
+
+void da_destroy(da_ctx* c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->W) cudaFree(c->W);
+    if (c->diag) cudaFree(c->diag);
+    if (c->ws) cudaFree(c->ws);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+da_status da_ctx_info(const da_ctx* c, int64_t* N, da_dtype* dtype)
+{
+    if (da_status s = check_ctx(c)) return s;
+    if (N) *N = c->N;
+    if (dtype) *dtype = c->dtype;
+    return DA_OK;
+}
+
+da_status da_set_launch_shape(da_ctx* c, int32_t V, int32_t G, int32_t rpb)
+{
+    if (da_status s = check_ctx(c)) return s;
+    if (V == 0) {
+        c->forced = StepShape{};
+        return DA_OK;
+    }
+    StepShape s;
+    s.V = V;
+    s.G = G;
+    s.rpb = rpb;
+    if (!da::step_shape_supported(s)) return fail(DA_EINVAL, "unsupported launch shape");
+    if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape covers fewer than N variables");
+    c->forced = s;
+    return DA_OK;
+}
+
+static da_status anneal_common(da_ctx* c, const float* beta, bool beta_on_host, int64_t steps, float inc,
+                               int32_t R, uint64_t seed, int64_t recompute_every, bool want_trace,
+                               cudaStream_t st, RunBuffers* out_b)
+{
+    if (steps < 0) return fail(DA_EINVAL, "steps < 0");
+    if (steps > 0 && !beta) return fail(DA_EINVAL, "beta schedule is null");
+    if (R < 1) return fail(DA_EINVAL, "replicas < 1");
+    if (steps >= (1ll << 32)) return fail(DA_EINVAL, "steps >= 2^32");
+    if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
+    if (recompute_every < 0) return fail(DA_EINVAL, "recompute_every < 0");
+    const StepShape s = shape_for(c);
+    if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
+    const Layout L = plan(c, s, R, steps, beta_on_host, want_trace, 0);
+    if (da_status e = ensure_ws(c, L.total)) return e;
+    RunBuffers b{static_cast<char*>(c->ws), L, s, R};
+    const float* beta_dev = beta;
+    if (beta_on_host && steps > 0) {
+        DA_CU(cudaMemcpyAsync(b.base + L.beta, beta, (size_t)steps * 4, cudaMemcpyHostToDevice, st));
+        beta_dev = reinterpret_cast<const float*>(b.base + L.beta);
+    }
+    if (da_status e = reset_state(b, st)) return e;
+    int* trace_dev = want_trace ? reinterpret_cast<int*>(b.base + L.trace) : nullptr;
+    if (da_status e = run_anneal(c, b, beta_dev, steps, inc, seed, recompute_every, trace_dev, st)) return e;
+    if (da_status e = evaluate(c, b, st)) return e;
+    *out_b = b;
+    return DA_OK;
+}
+
+da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int32_t R, uint64_t seed,
+                    int64_t recompute_every, da_result* out)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    CtxLock lock(c);
+    const bool want_trace = out && out->trace;
+    cudaStream_t st = c->stream;
+    DA_CU(cudaEventRecord(c->ev0, st));
+    RunBuffers b{};
+    if (da_status e = anneal_common(c, beta, true, steps, inc, R, seed, recompute_every, want_trace, st, &b)) return e;
+    double* res = reinterpret_cast<double*>(b.base + b.L.res);
+    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int8(c), R, b.sc(), b.eex(), res, res + R, res + 2 * R,
+                                                     reinterpret_cast<int64_t*>(res + 3 * R));
+    DA_CU(cudaGetLastError());
+    DA_CU(cudaEventRecord(c->ev1, st));
+    if (!out) {
+        DA_CU(cudaStreamSynchronize(st));
+        return DA_OK;
+    }
+    const size_t words = (size_t)da_words(c->N);
+    std::vector<double> hres((size_t)4 * R);
+    DA_CU(cudaMemcpyAsync(hres.data(), res, hres.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (out->final_x)
+        DA_CU(cudaMemcpy2DAsync(out->final_x, words * 4, b.x(), (size_t)b.s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (out->best_x)
+        DA_CU(cudaMemcpy2DAsync(out->best_x, words * 4, b.bestx(), (size_t)b.s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (want_trace && steps > 0)
+        DA_CU(cudaMemcpyAsync(out->trace, b.base + b.L.trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
+    DA_CU(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    out->elapsed_s = ms * 1e-3;
+    for (int r = 0; r < R; ++r) {
+        if (out->final_E) out->final_E[r] = hres[r];
+        if (out->best_E) out->best_E[r] = hres[R + r];
+        if (out->max_drift) out->max_drift[r] = hres[2 * R + r];
+        if (out->flips) out->flips[r] = reinterpret_cast<const int64_t*>(hres.data() + 3 * R)[r];
+    }
+    return DA_OK;
+}
+
+da_status da_anneal_async(da_ctx* c, const float* beta_dev, int64_t steps, float inc, int32_t R, uint64_t seed,
+                          int64_t recompute_every, const da_dev_result* out, void* stream)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    CtxLock lock(c);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool want_trace = out && out->trace;
+    RunBuffers b{};
+    if (da_status e = anneal_common(c, beta_dev, false, steps, inc, R, seed, recompute_every, want_trace, st, &b))
+        return e;
+    if (!out) return DA_OK;
+    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int8(c), R, b.sc(), b.eex(), out->final_E, out->best_E,
+                                                     out->max_drift, out->flips);
+    DA_CU(cudaGetLastError());
+    const size_t words = (size_t)da_words(c->N);
+    if (out->final_x)
+        DA_CU(cudaMemcpy2DAsync(out->final_x, words * 4, b.x(), (size_t)b.s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToDevice, st));
+    if (out->best_x)
+        DA_CU(cudaMemcpy2DAsync(out->best_x, words * 4, b.bestx(), (size_t)b.s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToDevice, st));
+    if (want_trace && steps > 0)
+        DA_CU(cudaMemcpyAsync(out->trace, b.base + b.L.trace, (size_t)R * steps * 4, cudaMemcpyDeviceToDevice, st));
+    return DA_OK;
+}
+
+da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_t L, float inc, uint64_t seed,
+                da_pt_result* out)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    if (!betas || K < 1 || K > 4096) return fail(DA_EINVAL, "need 1 <= K <= 4096 and betas");
+    if (L < 1 || sweeps < 0) return fail(DA_EINVAL, "need ladders >= 1 and sweeps >= 0");
+    if ((long long)L * K > (1 << 24)) return fail(DA_EINVAL, "too many replicas");
+    if ((double)sweeps * c->N >= 4294967296.0) return fail(DA_EINVAL, "sweeps * N >= 2^32");
+    if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
+    for (int k = 0; k < K; ++k) {
+        if (!std::isfinite(betas[k]) || betas[k] < 0.f) return fail(DA_EINVAL, "betas must be finite and >= 0");
+        if (k > 0 && betas[k] < betas[k - 1]) return fail(DA_EINVAL, "betas must be ascending");
+    }
+    CtxLock lock(c);
+    cudaStream_t st = c->stream;
+    const int R = L * K;
+    const StepShape s = shape_for(c);
+    if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
+    const bool want_trace = out && out->swap_trace && K > 1;
+    const size_t n_sw = (size_t)L * std::max(K - 1, 0);
+    const size_t pt_bytes = align_up((size_t)K * 4, 256) + align_up((size_t)R * 4, 256) * 2 +
+                            align_up(n_sw * 8, 256) + (want_trace ? n_sw * (size_t)sweeps : 0);
+    const Layout Ly = plan(c, s, R, 0, false, false, pt_bytes);
+    if (da_status e = ensure_ws(c, Ly.total)) return e;
+    RunBuffers b{static_cast<char*>(c->ws), Ly, s, R};
+    char* pb = b.base + Ly.pt;
+    float* betas_dev = reinterpret_cast<float*>(pb);
+    int* temp_of = reinterpret_cast<int*>(pb + align_up((size_t)K * 4, 256));
+    int* rep_at = temp_of + align_up((size_t)R * 4, 256) / 4;
+    long long* swaps = reinterpret_cast<long long*>(reinterpret_cast<char*>(rep_at) + align_up((size_t)R * 4, 256));
+    uint8_t* strace = want_trace ? reinterpret_cast<uint8_t*>(swaps) + align_up(n_sw * 8, 256) : nullptr;
+    std::vector<int> init((size_t)R);
+    for (int l = 0; l < L; ++l)
+        for (int k = 0; k < K; ++k) init[(size_t)l * K + k] = k;
+    DA_CU(cudaEventRecord(c->ev0, st));
+    DA_CU(cudaMemcpyAsync(betas_dev, betas, (size_t)K * 4, cudaMemcpyHostToDevice, st));
+    DA_CU(cudaMemcpyAsync(temp_of, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
+    DA_CU(cudaMemcpyAsync(rep_at, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
+    if (n_sw) DA_CU(cudaMemsetAsync(swaps, 0, n_sw * 8, st));
+    if (da_status e = reset_state(b, st)) return e;
+    StepParams p = base_params(c, b);
+    p.betas = betas_dev;
+    p.temp_of = temp_of;
+    p.inc = inc;
+    p.seed = seed;
+    for (long long sw = 0; sw < sweeps; ++sw) {
+        p.t0 = sw * c->N;
+        p.t1 = p.t0 + c->N;
+        DA_CU(da::launch_step(is_int8(c), s, p, false, st));
+        DA_CU(da::launch_pt_exchange(is_int8(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
+                                     seed, st));
+    }
+    if (da_status e = evaluate(c, b, st)) return e;
+    DA_CU(cudaEventRecord(c->ev1, st));
+    std::vector<long long> eex((size_t)2 * R);
+    DA_CU(cudaMemcpyAsync(eex.data(), b.eex(), eex.size() * 8, cudaMemcpyDeviceToHost, st));
+    const size_t words = (size_t)da_words(c->N);
+    if (out && out->best_x)
+        DA_CU(cudaMemcpy2DAsync(out->best_x, words * 4, b.bestx(), (size_t)s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (out && out->temp_of) DA_CU(cudaMemcpyAsync(out->temp_of, temp_of, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
+    if (out && out->swaps && n_sw)
+        DA_CU(cudaMemcpyAsync(out->swaps, swaps, n_sw * 8, cudaMemcpyDeviceToHost, st));
+    if (want_trace && sweeps > 0)
+        DA_CU(cudaMemcpyAsync(out->swap_trace, strace, n_sw * (size_t)sweeps, cudaMemcpyDeviceToHost, st));
+    DA_CU(cudaStreamSynchronize(st));
+    if (!out) return DA_OK;
+    float ms = 0.f;
+    DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    out->elapsed_s = ms * 1e-3;
+    for (int r = 0; r < R; ++r) {
+        const double ef = is_int8(c) ? (double)eex[r] : reinterpret_cast<const double*>(eex.data())[r];
+        const double eb = is_int8(c) ? (double)eex[R + r] : reinterpret_cast<const double*>(eex.data())[R + r];
+        if (out->final_E) out->final_E[r] = ef;
+        if (out->best_E) out->best_E[r] = eb;
+    }
+    return DA_OK;
+}
+
+static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h, double* E)
+{
+    if (da_status s = check_ctx(c)) return s;
+    if (!x || R < 1) return fail(DA_EINVAL, "need states and R >= 1");
+    CtxLock lock(c);
+    cudaStream_t st = c->stream;
+    const size_t words = (size_t)da_words(c->N);
+    const size_t xb = align_up((size_t)R * words * 4, 256);
+    const size_t hb = align_up((size_t)R * c->N * 4, 256);
+    const size_t sb = align_up((size_t)R * c->N * 8, 256);
+    const size_t eb = align_up((size_t)R * 8, 256);
+    if (da_status e = ensure_ws(c, xb + hb + sb + eb)) return e;
+    char* base = static_cast<char*>(c->ws);
+    uint32_t* xd = reinterpret_cast<uint32_t*>(base);
+    void* hd = base + xb;
+    long long* sums = reinterpret_cast<long long*>(base + xb + hb);
+    long long* ed = reinterpret_cast<long long*>(base + xb + hb + sb);
+    DA_CU(cudaMemcpyAsync(xd, x, (size_t)R * words * 4, cudaMemcpyHostToDevice, st));
+    DA_CU(da::launch_recompute(is_int8(c), c->W, c->diag, c->N, c->ldw, c->S, xd, (int)words, R, h ? hd : nullptr,
+                               c->N, E ? ed : nullptr, 1, st, sums));
+    std::vector<long long> eh(E ? (size_t)R : 0);
+    if (h) DA_CU(cudaMemcpyAsync(h, hd, (size_t)R * c->N * 4, cudaMemcpyDeviceToHost, st));
+    if (E) DA_CU(cudaMemcpyAsync(eh.data(), ed, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
+    DA_CU(cudaStreamSynchronize(st));
+    if (E)
+        for (int r = 0; r < R; ++r)
+            E[r] = is_int8(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
+    return DA_OK;
+}
+
+da_status da_profile_enable(da_ctx* c, int32_t on)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    CtxLock lock(c);
+    c->prof = on != 0;
+    c->prof_used = 0;
+    return DA_OK;
+}
+
+da_status da_profile_read(da_ctx* c, int64_t* launches, double* total_ms)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    CtxLock lock(c);
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+        DA_CU(cudaEventSynchronize(c->prof_ev[i + 1]));
+        float t = 0.f;
+        DA_CU(cudaEventElapsedTime(&t, c->prof_ev[i], c->prof_ev[i + 1]));
+        ms += t;
+    }
+    if (launches) *launches = (int64_t)(c->prof_used / 2);
+    if (total_ms) *total_ms = ms;
+    c->prof_used = 0;
+    return DA_OK;
+}
+
+da_status da_energy(da_ctx* c, const uint32_t* x, int32_t R, double* E)
+{
+    g_err.clear();
+    if (!E) return fail(DA_EINVAL, "E is null");
+    return states_common(c, x, R, nullptr, E);
+}
+
+da_status da_field_recompute(da_ctx* c, const uint32_t* x, int32_t R, void* h)
+{
+    g_err.clear();
+    if (!h) return fail(DA_EINVAL, "h is null");
+    return states_common(c, x, R, h, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// da_device.cuh -- device-side random numbers and the fp32 exponential used
+// by every annealer kernel.
+//
+// Random numbers (the DA's hardware generator of Sec. II is replaced by a
+// counter-based one, so that any trial's draw can be computed, or skipped,
+// independently):
+//   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed_lo, seed_hi).
+//   acceptance draw of trial i at step t of replica r:
+//       counter (32*(i/128) + i%32, t, r, 0), output lane (i%128)/32
+//   uniform choice of step t:   counter (0, t & ~3, r, 1), output lane t%4
+//   replica exchange after sweep s, pair p, ladder l:  counter (p, s, l, 2), lane 0
+//   u = ((word >> 8) + 1) * 2^-24, uniform on (0, 1] with 24-bit resolution.
+//
+// Every fp32 operation that feeds an accept decision is written with an _rn
+// intrinsic so that the compiler cannot contract it into an FMA: the
+// decisions are then a function of IEEE single-precision arithmetic alone.
+#pragma once
+#include <cstdint>
+
+namespace da {
+
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo_a = kMulA * c0, hi_a = __umulhi(kMulA, c0);
+        const uint32_t lo_b = kMulB * c2, hi_b = __umulhi(kMulB, c2);
+        const uint32_t n0 = hi_b ^ c1 ^ k0;
+        const uint32_t n2 = hi_a ^ c3 ^ k1;
+        c0 = n0; c1 = lo_b; c2 = n2; c3 = lo_a;
+        k0 += kWeylA; k1 += kWeylB;
+    }
+    return {c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t pick(const u32x4& r, int lane)
+{
+    return lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+}
+
+// u in (0, 1]: ((w >> 8) + 1) * 2^-24 (exact in fp32).
+__device__ __forceinline__ float uniform01(uint32_t w)
+{
+    return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-08f);
+}
+
+// exp(x) for x <= 0 in fp32: n = rint(x log2 e); r = x - n ln2 with ln2 split
+// into a 16-bit head and a tail (Cody & Waite reduction); e^r from its Taylor
+// series through r^7 by Horner's rule with fused multiply-adds; the result is
+// scaled by 2^n through its exponent field.  0 for x < -86.
+__device__ __forceinline__ float exp_neg(float x)
+{
+    if (!(x >= -86.0f)) return 0.0f;
+    const float n = rintf(__fmul_rn(x, 1.44269504088896341f));
+    float r = __fmaf_rn(-n, 0.693145751953125f, x);
+    r = __fmaf_rn(-n, 1.428606765330187e-06f, r);
+    float p = 1.0f / 5040.0f;
+    p = __fmaf_rn(p, r, 1.0f / 720.0f);
+    p = __fmaf_rn(p, r, 1.0f / 120.0f);
+    p = __fmaf_rn(p, r, 1.0f / 24.0f);
+    p = __fmaf_rn(p, r, 1.0f / 6.0f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const float scale = __int_as_float(((int)n + 127) << 23);
+    return __fmul_rn(p, scale);
+}
+
+// Arguments at or below this give exp_neg(x) <= 2^-24, which no u in (0, 1]
+// is below: such trials are rejected without drawing u (checked
+// exhaustively over all fp32 values in [-104, -16.7] by the tests).
+constexpr float kExpCut = -16.7f;
+
+}  // namespace da

@@ -1,0 +1,70 @@
+// da_diag.cu -- diagnostic entry points that run the device's own Philox and
+// exponential (the exact functions every annealer kernel uses) on host
+// arrays, so that tests can compare them with independent implementations.
+#include <string>
+
+#include "da.h"
+#include "da_device.cuh"
+
+namespace {
+
+__global__ void expf_kernel(const float* x, float* y, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = da::exp_neg(x[i]);
+}
+
+__global__ void philox_kernel(const uint32_t* in, uint32_t* out, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t* c = in + 6 * i;
+    const da::u32x4 r = da::philox4x32_10(c[0], c[1], c[2], c[3], c[4], c[5]);
+    out[4 * i + 0] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+thread_local std::string g_diag_err;
+
+template <typename Fn>
+da_status run(size_t in_bytes, size_t out_bytes, const void* in_h, void* out_h, Fn launch)
+{
+    void *din = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&din, in_bytes ? in_bytes : 1);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, out_bytes ? out_bytes : 1);
+    if (e == cudaSuccess) e = cudaMemcpy(din, in_h, in_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch(din, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out_h, dout, out_bytes, cudaMemcpyDeviceToHost);
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DA_ECUDA;
+    }
+    return DA_OK;
+}
+
+}  // namespace
+
+extern "C" da_status da_diag_expf(const float* x, float* y, int64_t n)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    return run((size_t)n * 4, (size_t)n * 4, x, y, [&](void* a, void* b) {
+        expf_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<const float*>(a), static_cast<float*>(b), n);
+    });
+}
+
+extern "C" da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n)
+{
+    if (n < 0 || (n > 0 && (!ctr_key || !out))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    return run((size_t)n * 24, (size_t)n * 16, ctr_key, out, [&](void* a, void* b) {
+        philox_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<const uint32_t*>(a), static_cast<uint32_t*>(b), n);
+    });
+}

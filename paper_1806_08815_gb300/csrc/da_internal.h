@@ -1,0 +1,76 @@
+// da_internal.h -- structures shared by the library's kernels and its runtime
+// (not part of the public ABI in include/da.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace da {
+
+// Per-replica scalars kept in global memory between kernel launches.
+// E and best hold int64 energies (int8 instances) or fp64 bit patterns (fp32).
+struct alignas(32) ReplicaScalars {
+    long long E;       // tracked energy after the last completed step
+    long long best;    // lowest tracked energy seen
+    long long flips;   // accepted flips
+    uint32_t m;        // consecutive steps without an accepted flip (E_off = m * inc)
+    uint32_t pad;
+};
+
+// Launch shape of the parallel-trial step: a group of G warps per replica,
+// V variables per lane, so one replica spans Npad = 32 * V * G variables;
+// lane l of warp w owns i = w*32V + 32v + l (v < V).
+struct StepShape {
+    int V = 0;
+    int G = 0;
+    int rpb = 0;  // replicas (groups) per block
+    int npad() const { return 32 * V * G; }
+    int nwords() const { return V * G; }
+};
+
+struct StepParams {
+    const void* W = nullptr;      // [N][ldw] symmetric, zero diagonal (int8 or fp32)
+    const void* diag = nullptr;   // [N] int32 or fp32
+    int N = 0;
+    int ldw = 0;
+    int R = 0;                    // replicas handled by this launch
+    int npad = 0, nw = 0;
+    void* h = nullptr;            // [R][npad] int32 / fp32 fields
+    uint32_t* x = nullptr;        // [R][nw] state words
+    uint32_t* bestx = nullptr;    // [R][nw] best-state words
+    ReplicaScalars* sc = nullptr; // [R]
+    const float* beta = nullptr;  // schedule, indexed by the global step t
+    const float* betas = nullptr; // PT: beta of replica r is betas[temp_of[r]]
+    const int* temp_of = nullptr;
+    float inc = 0.f;
+    uint64_t seed = 0;
+    uint32_t rep_base = 0;        // Philox replica id of replica r is rep_base + r
+    long long t0 = 0, t1 = 0;     // steps [t0, t1)
+    int* trace = nullptr;         // optional [R][trace_T]
+    long long trace_T = 0;
+};
+
+// Step kernel launcher (da_step.cu).  is_int8 selects int8 W / int32 fields.
+cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
+bool step_shape_supported(const StepShape& s);
+
+// Field recompute and energies (da_fields.cu).
+// Exact fields of R bit-packed states xs[R][nw] (words of 32 variables):
+// int8: h = W x in int32.  fp32: every W_ij is put on the grid 2^-S, summed
+// exactly in int64, and rounded once to fp32.  hout[R][npad] (npad >= N)
+// receives the fields (0 beyond N).  If E != nullptr, also writes the
+// energy sum_i x_i (d_i + h_i / 2) (int64 or fp64 bit pattern) to E[r*Estride].
+// sums_t is scratch of N * R int64 (layout [i][R]), required when E != nullptr.
+cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
+                             const uint32_t* xs, int nw, int R, void* hout, int npad,
+                             long long* E, int Estride, cudaStream_t st, long long* sums_t);
+
+// PT exchange (da_pt.cu).
+cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
+                               const ReplicaScalars* sc, int* temp_of, int* rep_at,
+                               long long* swaps, uint8_t* swap_trace, long long sweep, long long sweeps,
+                               uint64_t seed, cudaStream_t st);
+
+// Fixed-point scale of the fp32 recompute for max|W| = amax and N variables.
+int fix_scale(float amax, int N);
+
+}  // namespace da

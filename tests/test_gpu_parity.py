@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Integer (bimodal) runs must reproduce the oracle's flip trajectory bit for bit;
+so must fp32 runs, whose every decision and field update is one IEEE fp32
+operation on both sides and whose periodic recompute is an exact fixed-point
+sum.  Energies of identical states agree to fp64 rounding (1e-12 relative).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+NT = 8   # oracle threads
+
+
+@pytest.fixture(scope="module")
+def da():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1806_08815_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def inst():
+    from paper_1806_08815_gb300 import instances
+    return instances
+
+
+def _compare_anneal(got, ref, Q, exact_int):
+    import oracle
+    assert np.array_equal(got["trace"], ref["trace"])
+    assert np.array_equal(got["final_x"], ref["x_final"])
+    assert np.array_equal(got["best_x"], ref["x_best"])
+    assert np.array_equal(got["flips"], ref["flips"])
+    Ef = oracle.energy(Q, got["final_x"])
+    Eb = oracle.energy(Q, got["best_x"])
+    if exact_int:
+        assert np.array_equal(got["final_E"], Ef.astype(float))
+        assert np.array_equal(got["best_E"], Eb.astype(float))
+        assert np.array_equal(got["final_E"], ref["E_final"])
+        assert np.all(got["max_drift"] == 0)
+    else:
+        assert np.allclose(got["final_E"], Ef, rtol=1e-12, atol=1e-12)
+        assert np.allclose(got["best_E"], Eb, rtol=1e-12, atol=1e-12)
+        # the tracked fp32 energy stays within 1e-5 relative of the exact one
+        assert np.all(got["max_drift"] <= 1e-5 * np.maximum(1.0, np.abs(Ef)))
+
+
+def test_device_exp_matches_oracle_exhaustively(da):
+    """Every fp32 x with 2^-30 <= -x <= 16.7 (all arguments the kernels evaluate
+    beyond the round-to-1 region), and a sample of the rest, bit for bit."""
+    import oracle
+    lo = np.float32(-(2.0 ** -30)).view(np.uint32)
+    hi = np.float32(-16.7).view(np.uint32)
+    step = 1 << 25
+    for start in range(int(lo), int(hi) + 1, step):
+        bits = np.arange(start, min(start + step, int(hi) + 1), dtype=np.uint32)
+        x = bits.view(np.float32)
+        assert np.array_equal(da.binding.da_diag_expf(x).view(np.uint32), oracle.expf(x).view(np.uint32))
+    rng = np.random.default_rng(0)
+    x = np.concatenate([-rng.random(1 << 20).astype(np.float32) * 200, -rng.random(1 << 16).astype(np.float32) * 1e-9,
+                        np.array([0.0, -0.0, -86.0, -86.00001, -np.inf], np.float32)])
+    assert np.array_equal(da.binding.da_diag_expf(x).view(np.uint32), oracle.expf(x).view(np.uint32))
+
+
+def test_device_philox_matches_oracle(da):
+    import oracle
+    rng = np.random.default_rng(1)
+    ck = rng.integers(0, 2 ** 32, size=(4096, 6), dtype=np.uint64).astype(np.uint32)
+    ck[:3] = [[0] * 6, [0xFFFFFFFF] * 6, [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344, 0xa4093822, 0x299f31d0]]
+    got = da.binding.da_diag_philox(ck)
+    for row, g in zip(ck[:512], got[:512]):
+        assert np.array_equal(g, oracle.philox(row[:4], row[4:]))
+    assert [hex(v) for v in got[0]] == ["0x6627e8d5", "0xe169c58d", "0xbc57ac4c", "0x9b00dbd8"]
+
+
+def test_sk_bimodal_n64_full_config(da, inst):
+    """Fully connected +-1 spin glass, N = 64, 64 replicas, 10^4 steps, beta linear
+    0.05 -> 3.0, offset increment 1, seed 0: bit-exact trajectories."""
+    import oracle
+    q = inst.sk_bimodal(64, 0)
+    beta = inst.beta_linear(0.05, 3.0, 10_000)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, 1.0, 64, 0, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=64, seed=0, inc=1.0, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, True)
+
+
+SHAPES = [(0, 0, 0), (4, 1, 8), (8, 1, 3), (4, 2, 4), (4, 4, 1), (4, 8, 1), (8, 2, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("N", [1, 33, 100])
+def test_int8_ragged_sizes_all_shapes(da, inst, N, shape):
+    import oracle
+    q = inst.random_qubo(N, N + 1, True, -5, 5)
+    if N > 1:
+        q = inst.Instance(q.name, N, np.triu(q.Q).astype(np.int32), 0.0, q.J)
+    beta = inst.beta_linear(0.1, 2.5, 700)
+    ctx = da.da_create(q.Q)
+    if shape[0]:
+        if 32 * shape[0] * shape[1] < N:
+            pytest.skip("shape smaller than N")
+        da.da_set_launch_shape(ctx, *shape)
+    got = da.da_anneal(ctx, beta, 0.5, 13, 7, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=13, seed=7, inc=0.5, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, True)
+
+
+@pytest.mark.parametrize("N,shape", [(300, (0, 0, 0)), (300, (16, 1, 2)), (1000, (0, 0, 0)), (1000, (8, 4, 1)),
+                                     (1500, (0, 0, 0)), (2100, (0, 0, 0)), (2100, (16, 8, 1))])
+def test_int8_larger_sizes(da, inst, N, shape):
+    import oracle
+    q = inst.sk_bimodal(N, 3)
+    beta = inst.beta_linear(0.02, 1.5, 300)
+    ctx = da.da_create(q.Q)
+    if shape[0]:
+        da.da_set_launch_shape(ctx, *shape)
+    got = da.da_anneal(ctx, beta, 1.0, 6, 11, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=6, seed=11, inc=1.0, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, True)
+
+
+@pytest.mark.parametrize("shape", [(0, 0, 0), (4, 2, 2), (8, 1, 4)])
+def test_fp32_sk_gaussian_with_recompute(da, inst, shape):
+    import oracle
+    q = inst.sk_gaussian(256, 5)
+    beta = inst.beta_linear(0.2, 8.0, 3000)
+    ctx = da.da_create(q.Q)
+    if shape[0]:
+        da.da_set_launch_shape(ctx, *shape)
+    got = da.da_anneal(ctx, beta, 0.25, 16, 5, recompute_every=256, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=16, seed=5, inc=0.25, recompute_every=256, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, False)
+
+
+def test_fp32_lattice_l32_geometric(da, inst):
+    """2D Gaussian torus L = 32 (N = 1024) kept dense, geometric beta 0.1 -> 5.0, offset 0.5."""
+    import oracle
+    q = inst.lattice2d(32, 0, True)
+    beta = inst.beta_geometric(0.1, 5.0, 2000)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, 0.5, 8, 2, recompute_every=1024, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=8, seed=2, inc=0.5, recompute_every=1024, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, False)
+
+
+def test_fp32_sk_n1024_recompute_1024(da, inst):
+    import oracle
+    q = inst.sk_gaussian(1024, 0)
+    beta = inst.beta_linear(0.5, 10.0, 2100)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, 0.0, 4, 0, recompute_every=1024, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=4, seed=0, inc=0.0, recompute_every=1024, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, False)
+
+
+def test_full_size_sk_n1024_sampled_replicas(da, inst):
+    """The benchmark's launch (SK Gaussian N = 1024, 1024 replicas, 2e5 steps, recompute
+    every 1024) checked on two sampled replicas that the oracle reruns alone."""
+    import oracle
+    from bench import C3
+    q = inst.sk_gaussian(C3["N"], C3["instance_seed"])
+    beta = inst.beta_linear(C3["beta0"], C3["beta1"], C3["steps"])
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, C3["inc"], C3["replicas"], C3["seed"], recompute_every=C3["recompute_every"])
+    for r in (0, 777):
+        ref = oracle.da_anneal(q.Q, beta, R=1, seed=C3["seed"], inc=C3["inc"], replica_base=r,
+                               recompute_every=C3["recompute_every"])
+        assert np.array_equal(got["final_x"][r], ref["x_final"][0])
+        assert np.array_equal(got["best_x"][r], ref["x_best"][0])
+        assert got["flips"][r] == ref["flips"][0]
+        assert abs(got["best_E"][r] - oracle.energy(q.Q, ref["x_best"])[0]) <= 1e-12 * abs(got["best_E"][r])
+
+
+def test_edge_cases(da, inst):
+    import oracle
+    q = inst.sk_bimodal(40, 9)
+    ctx = da.da_create(q.Q)
+    # zero steps: everything stays at x = 0
+    got = da.da_anneal(ctx, np.zeros(0, np.float32), 1.0, 3, 1)
+    assert np.all(got["final_x"] == 0) and np.all(got["final_E"] == 0) and np.all(got["flips"] == 0)
+    # beta = 0: every trial accepted, a flip at every step
+    got = da.da_anneal(ctx, np.zeros(50, np.float32), 0.0, 2, 1, trace=True)
+    ref = oracle.da_anneal(q.Q, np.zeros(50, np.float32), R=2, seed=1, trace=True)
+    assert np.array_equal(got["trace"], ref["trace"]) and np.all(got["trace"] >= 0)
+    # zero temperature, offset off, from a local minimum: nothing is ever accepted
+    Q = np.triu(np.random.default_rng(0).integers(-3, 4, (20, 20)), 1).astype(np.int32)
+    Q[np.arange(20), np.arange(20)] = 50
+    ctx2 = da.da_create(Q)
+    got = da.da_anneal(ctx2, np.full(30, 1e6, np.float32), 0.0, 2, 1, trace=True)
+    assert np.all(got["trace"] == -1)
+    # and with the offset on, the first flip comes at the closed-form step
+    got = da.da_anneal(ctx2, np.full(40, 1e6, np.float32), 2.0, 2, 1, trace=True)
+    assert np.all(got["trace"][:, :25] == -1) and np.all(got["trace"][:, 25] >= 0)
+
+
+def test_results_do_not_depend_on_replica_count(da, inst):
+    q = inst.sk_bimodal(64, 4)
+    beta = inst.beta_linear(0.05, 3.0, 500)
+    ctx = da.da_create(q.Q)
+    a = da.da_anneal(ctx, beta, 1.0, 40, 9, trace=True)
+    b = da.da_anneal(ctx, beta, 1.0, 7, 9, trace=True)
+    assert np.array_equal(a["trace"][:7], b["trace"])
+
+
+def test_energy_and_recompute_entry_points(da, inst):
+    import oracle
+    rng = np.random.default_rng(3)
+    for q in (inst.sk_bimodal(77, 1), inst.sk_gaussian(130, 2)):
+        ctx = da.da_create(q.Q)
+        X = rng.integers(0, 2, (9, q.N))
+        xp = oracle.pack(X)
+        E = da.da_energy(ctx, xp)
+        ref = oracle.energy(q.Q, xp)
+        h = da.da_field_recompute(ctx, xp)
+        if q.bimodal:
+            assert np.array_equal(E, ref.astype(float))
+            for r in range(9):
+                assert np.array_equal(h[r], oracle.fields_int(q.Q, xp[r]))
+        else:
+            assert np.allclose(E, ref, rtol=1e-12, atol=1e-12)
+            for r in range(9):
+                hr, _, _ = oracle.recompute_f32(q.Q, xp[r])
+                assert np.array_equal(h[r].view(np.uint32), hr.view(np.uint32))
+                assert E[r] == oracle.recompute_energy_f32(q.Q, xp[r])
+
+
+def test_async_device_resident_matches_blocking(da, inst):
+    import torch
+    q = inst.sk_gaussian(200, 8)
+    beta = inst.beta_linear(0.3, 6.0, 1500)
+    ctx = da.da_create(q.Q)
+    ref = da.da_anneal(ctx, beta, 0.5, 10, 4, recompute_every=500)
+    dev = torch.device("cuda", 0)
+    W = da.da_words(q.N)
+    out = dict(final_E=torch.zeros(10, dtype=torch.float64, device=dev),
+               best_E=torch.zeros(10, dtype=torch.float64, device=dev),
+               final_x=torch.zeros((10, W), dtype=torch.int32, device=dev),
+               flips=torch.zeros(10, dtype=torch.int64, device=dev))
+    s = torch.cuda.Stream()
+    bd = torch.from_numpy(beta).to(dev)
+    torch.cuda.synchronize()
+    da.da_anneal_async(ctx, bd, beta.size, 0.5, 10, 4, 500, out, s)
+    s.synchronize()
+    assert np.array_equal(out["final_E"].cpu().numpy(), ref["final_E"])
+    assert np.array_equal(out["best_E"].cpu().numpy(), ref["best_E"])
+    assert np.array_equal(out["final_x"].cpu().numpy().view(np.uint32), ref["final_x"])
+    assert np.array_equal(out["flips"].cpu().numpy(), ref["flips"])
+
+
+@pytest.mark.parametrize("dtype", ["int8", "fp32"])
+def test_ptda_matches_oracle(da, inst, dtype):
+    import oracle
+    q = inst.sk_bimodal(128, 2) if dtype == "int8" else inst.sk_gaussian(96, 2)
+    betas = inst.beta_geometric(0.2, 5.0, 8)
+    ctx = da.da_create(q.Q)
+    got = da.da_pt(ctx, betas, 12, 5, 6, swap_trace=True)
+    ref = oracle.ptda(q.Q, betas, 12, L=5, seed=6, nthreads=NT)
+    assert np.array_equal(got["swap_trace"], ref["swap_trace"])
+    assert np.array_equal(got["temp_of"], ref["temp_of"])
+    assert np.array_equal(got["swaps"], ref["swaps"])
+    assert np.array_equal(got["best_x"], ref["x_best"])
+    Eb = oracle.energy(q.Q, got["best_x"].reshape(-1, da.da_words(q.N))).reshape(5, 8)
+    if dtype == "int8":
+        assert np.array_equal(got["best_E"], ref["E_best"])
+        assert np.array_equal(got["final_E"], ref["E_final"])
+    else:
+        assert np.allclose(got["best_E"], Eb, rtol=1e-12, atol=1e-12)
+
+
+def test_ptda_c4b_shape(da, inst):
+    """SK bimodal N = 512, 32 geometric betas in 0.2-5.0, exchange every sweep."""
+    import oracle
+    q = inst.sk_bimodal(512, 0)
+    betas = inst.beta_geometric(0.2, 5.0, 32)
+    ctx = da.da_create(q.Q)
+    got = da.da_pt(ctx, betas, 3, 2, 1, swap_trace=True)
+    ref = oracle.ptda(q.Q, betas, 3, L=2, seed=1, nthreads=NT)
+    assert np.array_equal(got["swap_trace"], ref["swap_trace"])
+    assert np.array_equal(got["best_E"], ref["E_best"])
+    assert np.array_equal(got["temp_of"], ref["temp_of"])
