@@ -278,41 +278,49 @@ int orc_fields_int(int64_t N, const int32_t* Q, const uint32_t* x, int64_t* h)
     return 0;
 }
 
-/* Fixed-point scale of the recompute: with max|W| < 2^e and 2^L >= N,
- * S = 62 - L - e puts every |W_ij| 2^S below 2^(62-L), so a sum of N of them
- * cannot overflow int64. */
-static int32_t fix_scale(int64_t N, const float* Wf)
+/* Fixed-point scale of the recompute: with max(|W_ij|, |Q_ii|) < 2^e and
+ * 2^L >= N + 1, S = 62 - L - e puts every |W_ij| 2^S and |Q_ii| 2^S below
+ * 2^(62-L), so the sum of a linear term and N couplings cannot overflow int64. */
+static int32_t fix_scale(int64_t N, const float* Wf, const float* df)
 {
     float amax = 0.0f;
     for (int64_t i = 0; i < N * N; ++i) {
         float a = fabsf(Wf[i]);
         if (a > amax) amax = a;
     }
+    for (int64_t i = 0; i < N; ++i) {
+        float a = fabsf(df[i]);
+        if (a > amax) amax = a;
+    }
     if (amax == 0.0f) return 0;
     int e;
     frexpf(amax, &e);
     int L = 0;
-    while ((1ll << L) < N) L++;
+    while ((1ll << L) < N + 1) L++;
     return 62 - L - e;
 }
 
+/* sums_i = round(Q_ii 2^S) + sum_{j: x_j = 1} round(W_ij 2^S), exactly. */
 static void recompute_sums(const inst_t* I, int32_t S, const uint8_t* x, int64_t* sums)
 {
     const int64_t N = I->N;
     for (int64_t i = 0; i < N; ++i) {
-        int64_t s = 0;
+        int64_t s = (int64_t)llrintf(ldexpf(I->df[i], S));
         for (int64_t j = 0; j < N; ++j)
             if (x[j]) s += (int64_t)llrintf(ldexpf(I->Wf[i * N + j], S));
         sums[i] = s;
     }
 }
 
+/* E = sum_{i: x_i = 1} (Q_ii + h_i / 2) in fp64, index order, where
+ * h_i = (sums_i - round(Q_ii 2^S)) 2^-S is the exact coupling part. */
 static double recompute_energy(const inst_t* I, int32_t S, const uint8_t* x, const int64_t* sums)
 {
     double E = 0.0;
     for (int64_t i = 0; i < I->N; ++i) {
         if (!x[i]) continue;
-        double hd = ldexp((double)sums[i], -S);
+        const int64_t hfix = sums[i] - (int64_t)llrintf(ldexpf(I->df[i], S));
+        double hd = ldexp((double)hfix, -S);
         E += (double)I->df[i] + 0.5 * hd;
     }
     return E;
@@ -323,7 +331,7 @@ int orc_recompute_f32(int64_t N, const float* Q, const uint32_t* x, float* h, in
     if (N < 1) return -1;
     inst_t I;
     if (inst_make(&I, N, ORC_MODE_F32, Q)) return -2;
-    int32_t S = fix_scale(N, I.Wf);
+    int32_t S = fix_scale(N, I.Wf, I.df);
     uint8_t* xb = (uint8_t*)malloc((size_t)N);
     int64_t* s = (int64_t*)malloc((size_t)N * sizeof(int64_t));
     for (int64_t i = 0; i < N; ++i) xb[i] = (uint8_t)getbit(x, i);
@@ -341,7 +349,7 @@ double orc_recompute_energy_f32(int64_t N, const float* Q, const uint32_t* x)
 {
     inst_t I;
     if (N < 1 || inst_make(&I, N, ORC_MODE_F32, Q)) return NAN;
-    int32_t S = fix_scale(N, I.Wf);
+    int32_t S = fix_scale(N, I.Wf, I.df);
     uint8_t* xb = (uint8_t*)malloc((size_t)N);
     int64_t* s = (int64_t*)malloc((size_t)N * sizeof(int64_t));
     for (int64_t i = 0; i < N; ++i) xb[i] = (uint8_t)getbit(x, i);
@@ -355,9 +363,9 @@ double orc_recompute_energy_f32(int64_t N, const float* Q, const uint32_t* x)
 /* State of one replica of the annealer. */
 typedef struct {
     uint8_t* x;
-    int64_t* hi;   /* ORC_MODE_INT */
-    float* hf;     /* ORC_MODE_F32 */
-    double* hd;    /* ORC_MODE_F64 */
+    int64_t* hi;   /* ORC_MODE_INT: h_i = sum_j W_ij x_j */
+    float* hf;     /* ORC_MODE_F32: effective field g_i = Q_ii + sum_j W_ij x_j */
+    double* hd;    /* ORC_MODE_F64: h_i */
     int64_t Ei;    /* tracked energy, ORC_MODE_INT */
     double Ed;     /* tracked energy, real modes   */
     uint32_t m;    /* steps since the last accepted flip (dynamic offset) */
@@ -371,7 +379,10 @@ static int rep_init(rep_t* s, const inst_t* I)
     s->x = (uint8_t*)calloc((size_t)N, 1);
     s->acc = (int32_t*)malloc((size_t)N * sizeof(int32_t));
     if (I->mode == ORC_MODE_INT) s->hi = (int64_t*)calloc((size_t)N, sizeof(int64_t));
-    else if (I->mode == ORC_MODE_F32) s->hf = (float*)calloc((size_t)N, sizeof(float));
+    else if (I->mode == ORC_MODE_F32) {
+        s->hf = (float*)calloc((size_t)N, sizeof(float));
+        if (s->hf) memcpy(s->hf, I->df, (size_t)N * sizeof(float));   /* x = 0: g = diag */
+    }
     else s->hd = (double*)calloc((size_t)N, sizeof(double));
     if (!s->x || !s->acc || (!s->hi && !s->hf && !s->hd)) return -2;
     return 0;
@@ -402,7 +413,7 @@ static int32_t da_trials(const inst_t* I, rep_t* s, float beta, float inc,
             int64_t dE = s->x[i] ? -v : v;
             delta = (float)dE - E_off;
         } else if (I->mode == ORC_MODE_F32) {
-            float v = I->df[i] + s->hf[i];
+            float v = s->hf[i];
             float dE = s->x[i] ? -v : v;
             delta = dE - E_off;
         } else {
@@ -434,7 +445,7 @@ static void da_flip(const inst_t* I, rep_t* s, int64_t k)
         const int64_t sg = old ? -1 : 1;
         for (int64_t j = 0; j < N; ++j) s->hi[j] += sg * I->Wi[k * N + j];
     } else if (I->mode == ORC_MODE_F32) {
-        float v = I->df[k] + s->hf[k];
+        float v = s->hf[k];
         float dE = old ? -v : v;
         s->Ed += (double)dE;
         const float sg = old ? -1.0f : 1.0f;
@@ -474,6 +485,7 @@ static void pack_bits(const uint8_t* x, int64_t N, uint32_t* out)
         if (x[i]) out[i >> 5] |= 1u << (i & 31);
 }
 
+/* Exact recompute of the effective fields, each rounded once to fp32. */
 static void periodic_recompute(const inst_t* I, rep_t* s, int32_t S, int64_t* sums)
 {
     recompute_sums(I, S, s->x, sums);
@@ -491,7 +503,7 @@ int orc_da_anneal(int64_t N, int mode, const void* Q,
     if (mode < ORC_MODE_INT || mode > ORC_MODE_F64) return -1;
     inst_t I;
     if (inst_make(&I, N, mode, Q)) return -2;
-    const int32_t S = (mode == ORC_MODE_F32) ? fix_scale(N, I.Wf) : 0;
+    const int32_t S = (mode == ORC_MODE_F32) ? fix_scale(N, I.Wf, I.df) : 0;
     const int64_t words = (N + 31) / 32;
     int err = 0;
 #ifdef _OPENMP
@@ -548,6 +560,7 @@ int orc_da_one_step(int64_t N, int mode, const void* Q, const uint32_t* x, uint3
     rep_t s;
     if (rep_init(&s, &I)) { rep_free(&s); inst_free(&I); return -2; }
     for (int64_t i = 0; i < N; ++i) s.x[i] = (uint8_t)getbit(x, i);
+    if (mode == ORC_MODE_F32) memcpy(s.hf, I.df, (size_t)N * sizeof(float));
     /* fields of the given state, summed in index order */
     for (int64_t i = 0; i < N; ++i)
         for (int64_t j = 0; j < N; ++j) {

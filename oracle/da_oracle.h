@@ -31,8 +31,9 @@ extern "C" {
 /* Arithmetic of the field vector h (and the energy tracked step by step). */
 enum {
     ORC_MODE_INT = 0, /* integer couplings: int64 h, int64 E (exact)          */
-    ORC_MODE_F32 = 1, /* real couplings: fp32 h (one rounding per update),
-                         fp64 E accumulated from fp32 Delta E, fp32 decisions */
+    ORC_MODE_F32 = 1, /* real couplings: fp32 effective fields Q_ii + h_i (one
+                         rounding per update), fp64 E accumulated from fp32
+                         Delta E, fp32 decisions                               */
     ORC_MODE_F64 = 2  /* real couplings: fp64 h and E (statistical reference) */
 };
 
@@ -63,10 +64,11 @@ int orc_brute_force_f64(int64_t N, const double* Q, double* Emin, int64_t* count
 
 /* Local fields h = W x of a bit-packed state. */
 int orc_fields_int(int64_t N, const int32_t* Q, const uint32_t* x, int64_t* h);
-/* The periodic field recompute of the fp32 path, as an exact fixed-point sum:
- * W is put on the grid 2^-S (S from max|W| and N, see the .c file), summed
- * exactly in int64, and rounded once to fp32.  sums[N] (may be NULL) receives
- * the exact integer sums, *S_out the scale. */
+/* The periodic recompute of the fp32 path's effective fields
+ * g_i = Q_ii + sum_j W_ij x_j as an exact fixed-point sum: Q_ii and the W_ij
+ * are put on the grid 2^-S (S from max(|W|, |Q_ii|) and N, see the .c file),
+ * summed exactly in int64, and rounded once to fp32.  sums[N] (may be NULL)
+ * receives the exact integer sums, *S_out the scale. */
 int orc_recompute_f32(int64_t N, const float* Q, const uint32_t* x, float* h, int64_t* sums, int32_t* S_out);
 /* The energy that accompanies the recompute: sum_i x_i (Q_ii + h_i/2) in fp64,
  * index order, with h_i = sums_i * 2^-S in fp64. */

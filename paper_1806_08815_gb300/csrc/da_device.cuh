@@ -21,21 +21,46 @@ namespace da {
 
 struct u32x4 { uint32_t x, y, z, w; };
 
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u, kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u, kPhiloxWeylB = 0xBB67AE85u;
+
+// The ten round keys of a Philox key, k + r * Weyl (r = 0..9): computed once
+// per thread, so that each round costs two wide multiplies and two xors.
+struct PhiloxKeys {
+    uint32_t a[10], b[10];
+    __device__ __forceinline__ explicit PhiloxKeys(uint64_t seed)
+    {
+        uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            a[r] = k0; b[r] = k1;
+            k0 += kPhiloxWeylA; k1 += kPhiloxWeylB;
+        }
+    }
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const PhiloxKeys& k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t pa = (uint64_t)kPhiloxMulA * c0;
+        const uint64_t pb = (uint64_t)kPhiloxMulB * c2;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k.a[round];
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k.b[round];
+        c1 = (uint32_t)pb;
+        c3 = (uint32_t)pa;
+        c0 = n0;
+        c2 = n2;
+    }
+    return {c0, c1, c2, c3};
+}
+
 __device__ __forceinline__ u32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                uint32_t k0, uint32_t k1)
 {
-    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-    constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo_a = kMulA * c0, hi_a = __umulhi(kMulA, c0);
-        const uint32_t lo_b = kMulB * c2, hi_b = __umulhi(kMulB, c2);
-        const uint32_t n0 = hi_b ^ c1 ^ k0;
-        const uint32_t n2 = hi_a ^ c3 ^ k1;
-        c0 = n0; c1 = lo_b; c2 = n2; c3 = lo_a;
-        k0 += kWeylA; k1 += kWeylB;
-    }
-    return {c0, c1, c2, c3};
+    const PhiloxKeys k(((uint64_t)k1 << 32) | k0);
+    return philox4x32_10(c0, c1, c2, c3, k);
 }
 
 __device__ __forceinline__ uint32_t pick(const u32x4& r, int lane)
@@ -56,7 +81,10 @@ __device__ __forceinline__ float uniform01(uint32_t w)
 __device__ __forceinline__ float exp_neg(float x)
 {
     if (!(x >= -86.0f)) return 0.0f;
-    const float n = rintf(__fmul_rn(x, 1.44269504088896341f));
+    // rint(x log2 e) by the 1.5 * 2^23 shifter: the sum rounds to an integer
+    // (ties to even) and its low mantissa bits hold n.
+    const float kshift = __fadd_rn(__fmul_rn(x, 1.44269504088896341f), 12582912.0f);
+    const float n = __fsub_rn(kshift, 12582912.0f);
     float r = __fmaf_rn(-n, 0.693145751953125f, x);
     r = __fmaf_rn(-n, 1.428606765330187e-06f, r);
     float p = 1.0f / 5040.0f;
@@ -67,7 +95,8 @@ __device__ __forceinline__ float exp_neg(float x)
     p = __fmaf_rn(p, r, 0.5f);
     p = __fmaf_rn(p, r, 1.0f);
     p = __fmaf_rn(p, r, 1.0f);
-    const float scale = __int_as_float(((int)n + 127) << 23);
+    const int ni = __float_as_int(kshift) - 0x4B400000;
+    const float scale = __int_as_float((ni + 127) << 23);
     return __fmul_rn(p, scale);
 }
 

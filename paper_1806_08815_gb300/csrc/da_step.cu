@@ -124,12 +124,13 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
     long long flips = sc.flips;
     uint32_t m = sc.m;
     const uint32_t rep = p.rep_base + (uint32_t)r;
-    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const PhiloxKeys keys(p.seed);
     const bool per_rep = p.betas != nullptr;
     const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
     u32x4 cr = {0, 0, 0, 0};
     long long cr_blk = -1;
     bool pending = false;
+    constexpr int NQ = V / QS;              // Philox blocks per lane per step
 
     auto snapshot = [&]() {
         uint32_t bw = 0;
@@ -140,46 +141,51 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
         }
         if (lane < V) bestg[w * V + lane] = bw;
     };
+    // The acceptance draws of one step: block q of this lane covers variables
+    // i0 + 32c + lane (c < QS) with i0 = w*32V + 32*q*QS; counter word 0 is
+    // 32*(i0/128) + lane, output lane (i0/32)%4 + c.
+    auto draw_step = [&](u32x4 (&rr)[NQ], uint32_t tt) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int i0 = w * 32 * V + 32 * q * QS;
+            rr[q] = philox4x32_10(32u * (uint32_t)(i0 >> 7) + (uint32_t)lane, tt, rep, 0u, keys);
+        }
+    };
+    u32x4 rr[NQ];
+    if (p.t0 < p.t1) draw_step(rr, (uint32_t)p.t0);
 
     float beta_next = (!per_rep && p.t0 < p.t1) ? p.beta[p.t0] : beta_rep;
     for (long long t = p.t0; t < p.t1; ++t) {
         const float beta = beta_next;
         if (!per_rep && t + 1 < p.t1) beta_next = p.beta[t + 1];
         const float Eoff = __fmul_rn(__uint2float_rn(m), p.inc);
-        const uint32_t tt = (uint32_t)t;
 
-        // (a) + (b): all trials of this lane
-        uint32_t accm = 0;
+        // (a) + (b): every trial of this lane.  Pass 1 decides what it can
+        // without a random number; pass 2 compares u with exp(-beta delta).
+        uint32_t accm = 0, needm = 0;
+        float ax[V];
 #pragma unroll
-        for (int q = 0; q < V / QS; ++q) {
-            float ax[QS];
-            uint32_t need = 0;
+        for (int v = 0; v < V; ++v) {
+            const H tv = A::add(d[v], h[v]);
+            const H dE = ((xm >> v) & 1u) ? -tv : tv;
+            const float delta = A::delta(dE, Eoff);
+            const bool ok = (valid >> v) & 1u;
+            ax[v] = -__fmul_rn(beta, delta);
+            const bool le0 = delta <= 0.0f;
+            accm |= (uint32_t)(ok && le0) << v;
+            needm |= (uint32_t)(ok && !le0 && ax[v] > kExpCut) << v;
+        }
 #pragma unroll
-            for (int c = 0; c < QS; ++c) {
-                const int v = q * QS + c;
-                const H tv = A::add(d[v], h[v]);
-                const H dE = ((xm >> v) & 1u) ? -tv : tv;
-                const float delta = A::delta(dE, Eoff);
-                const bool ok = (valid >> v) & 1u;
-                ax[c] = 0.f;
-                if (delta <= 0.0f) {
-                    accm |= (uint32_t)ok << v;
-                } else {
-                    ax[c] = -__fmul_rn(beta, delta);
-                    if (ok && ax[c] > kExpCut) need |= 1u << c;
-                }
-            }
-            if (need) {
-                const int i0 = w * 32 * V + 32 * q * QS;     // first variable of this chunk (lane 0)
-                const int sub0 = (V % 4 == 0) ? 0 : ((i0 >> 5) & 3);
-                const u32x4 rr = philox4x32_10(32u * (uint32_t)(i0 >> 7) + (uint32_t)lane, tt, rep, 0u, key0, key1);
+        for (int q = 0; q < NQ; ++q) {
+            const uint32_t nq = (needm >> (q * QS)) & ((1u << QS) - 1u);
+            if (__any_sync(0xffffffffu, nq != 0u)) {
+                const int sub0 = (V % 4 == 0) ? 0 : (((w * 32 * V + 32 * q * QS) >> 5) & 3);
 #pragma unroll
                 for (int c = 0; c < QS; ++c) {
-                    if (need & (1u << c)) {
-                        const float pr = exp_neg(ax[c]);
-                        const float u = uniform01(pick(rr, sub0 + c));
-                        if (u < pr) accm |= 1u << (q * QS + c);
-                    }
+                    const int v = q * QS + c;
+                    const float pr = exp_neg(ax[v]);
+                    const float u = uniform01(pick(rr[q], sub0 + c));
+                    accm |= (uint32_t)(((nq >> c) & 1u) && u < pr) << v;
                 }
             }
         }
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
         } else {
             const long long blk = t >> 2;
             if (blk != cr_blk) {
-                cr = philox4x32_10(0u, (uint32_t)(t & ~3ll), rep, 1u, key0, key1);
+                cr = philox4x32_10(0u, (uint32_t)(t & ~3ll), rep, 1u, keys);
                 cr_blk = blk;
             }
             const uint32_t uc = pick(cr, (int)(t & 3));
@@ -274,6 +280,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
             Tw cv[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) cv[v] = ((valid >> v) & 1u) ? __ldg(col + base + 32 * v) : Tw(0);
+            // the next step's draws do not depend on the column: compute them
+            // while its loads are in flight
+            if (t + 1 < p.t1) draw_step(rr, (uint32_t)(t + 1));
 #pragma unroll
             for (int v = 0; v < V; ++v) h[v] = A::apply(h[v], cv[v], xold != 0u);
             if (w == wk && lane == kb) xm ^= 1u << vk;
@@ -282,6 +291,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
                 Ecur = A::book(Ecur, dEk);
                 if (Ecur < Ebest) { Ebest = Ecur; snapshot(); }
             }
+        }
+        else if (t + 1 < p.t1) {
+            draw_step(rr, (uint32_t)(t + 1));
         }
         if constexpr (G > 1) pending = k >= 0;
         if constexpr (TRACE) {

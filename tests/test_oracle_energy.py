@@ -115,17 +115,18 @@ def test_brute_force_planted_state(orc):
 
 
 def _exact_recompute(Q, x, S):
-    """The fixed-point recompute from its definition, in exact integers."""
+    """The fixed-point recompute of the effective fields from its definition, in
+    exact integers: round(Q_ii 2^S) + sum_{x_j = 1} round(W_ij 2^S)."""
     N = Q.shape[0]
     W = np.triu(Q.astype(np.float32), 1)
     W = W + W.T
+    scale = Fraction(2) ** S
     out = []
     for i in range(N):
-        s = 0
+        s = round(Fraction(float(Q[i, i])) * scale)      # Python round: half to even, as llrintf
         for j in range(N):
             if x[j]:
-                v = Fraction(float(W[i, j])) * (Fraction(2) ** S)
-                s += round(v)          # Python round: half to even, as llrintf
+                s += round(Fraction(float(W[i, j])) * scale)
         out.append(s)
     return out
 
@@ -134,29 +135,36 @@ def test_recompute_exact_definition(orc):
     inst = instances.sk_gaussian(40, 9)
     rng = np.random.default_rng(2)
     x = rng.integers(0, 2, inst.N)
-    h, sums, S = orc.recompute_f32(inst.Q, orc.pack(x)[0])
-    # the scale: max|W| < 2^e, 2^L >= N, S = 62 - L - e
-    W = np.triu(inst.Q, 1)
-    amax = np.abs(W).max()
+    g, sums, S = orc.recompute_f32(inst.Q, orc.pack(x)[0])
+    # the scale: max(|W|, |Q_ii|) < 2^e, 2^L >= N + 1, S = 62 - L - e
+    amax = np.abs(inst.Q).max()
     e = int(np.frexp(amax)[1])
-    L = int(np.ceil(np.log2(inst.N)))
+    L = int(np.ceil(np.log2(inst.N + 1)))
     assert S == 62 - L - e
     assert list(sums) == _exact_recompute(inst.Q, x, S)
-    # h is the fp32 rounding of the exact fixed-point value
+    # g is the fp32 rounding of the exact fixed-point value
     for i in range(inst.N):
-        assert h[i] == np.float32(float(Fraction(int(sums[i])) / (Fraction(2) ** S)))
-    # and the fixed-point value is within N 2^-(S+1) of the real sum of W
-    Wf = W.astype(np.float64) + W.T.astype(np.float64)
-    real = Wf @ x
-    assert np.all(np.abs(sums / 2.0 ** S - real) <= inst.N * 2.0 ** -(S + 1) + 1e-15 * np.abs(real))
+        assert g[i] == np.float32(float(Fraction(int(sums[i])) / (Fraction(2) ** S)))
+    # and the fixed-point value is within (N + 1) 2^-(S+1) of the real Q_ii + sum_j W_ij x_j
+    W = np.triu(inst.Q, 1).astype(np.float64)
+    real = np.diag(inst.Q).astype(np.float64) + (W + W.T) @ x
+    assert np.all(np.abs(sums / 2.0 ** S - real) <= (inst.N + 1) * 2.0 ** -(S + 1) + 1e-15 * np.abs(real))
 
 
 def test_recompute_integer_valued_is_exact(orc):
     inst = instances.random_qubo(50, 4, True, -100, 100)
     Qf = inst.Q.astype(np.float32)
     x = np.random.default_rng(6).integers(0, 2, inst.N)
-    h, sums, S = orc.recompute_f32(Qf, orc.pack(x)[0])
-    ref = orc.fields_int(inst.Q, orc.pack(x)[0])
-    assert np.array_equal(h.astype(np.int64), ref)
+    g, sums, S = orc.recompute_f32(Qf, orc.pack(x)[0])
+    ref = orc.fields_int(inst.Q, orc.pack(x)[0]) + np.diag(inst.Q)
+    assert np.array_equal(g.astype(np.int64), ref)
     E = orc.recompute_energy_f32(Qf, orc.pack(x)[0])
     assert E == orc.energy(inst.Q, orc.pack(x))[0]
+
+
+def test_recompute_energy_matches_exact_energy(orc):
+    inst = instances.sk_gaussian(60, 3)
+    X = np.random.default_rng(7).integers(0, 2, (10, inst.N))
+    for x in X:
+        E = orc.recompute_energy_f32(inst.Q, orc.pack(x)[0])
+        assert E == pytest.approx(orc.energy(inst.Q, orc.pack(x))[0], rel=1e-13, abs=1e-13)
