@@ -127,8 +127,9 @@ da_status da_ctx_info(const da_ctx* ctx, int64_t* N, da_dtype* dtype);
 /* Fix the launch shape of the step kernel for this context instead of the
  * automatic choice: a group of G warps per replica, V variables per lane
  * (32 * V * G >= N), rpb replicas per thread block.  Supported: G = 1 with
- * V in {2, 4, 8, 16, 32}; G in {2, 4, 8} with V in {4, 8, 16, 32}; at most
- * 1024 threads per block.  V = 0 restores the automatic choice.  Results do
+ * V in {2, 4, 8, 16, 32} and rpb <= 4; G = 2 with rpb <= 2; G in {4, 8} with
+ * rpb = 1; for G > 1, V in {4, 8, 16, 32}.  V = 0 restores the automatic
+ * choice.  Results do
  * not depend on the shape (the random numbers are keyed by variable index,
  * step and replica).  Errors: DA_EINVAL. */
 da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);
@@ -192,6 +193,12 @@ da_status da_profile_read(da_ctx* ctx, int64_t* launches, double* total_ms);
  * implementations.  Errors: DA_EINVAL, DA_ECUDA. */
 da_status da_diag_expf(const float* x, float* y, int64_t n);
 da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
+/* The kernels decide u < exp(x) first against a band around a fast hardware
+ * estimate of 2^24 exp(x): da_diag_exp_band returns the band edges lo[n],
+ * hi[n] for x[n]; da_diag_accept returns the full decision acc[n] (0/1) for
+ * u = ((w >> 8) + 1) 2^-24 with w[n] 32-bit Philox words. */
+da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n);
+da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n);
 
 #ifdef __cplusplus
 }

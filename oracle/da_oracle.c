@@ -68,13 +68,11 @@ static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2
     return out[lane];
 }
 
-/* The acceptance draw of trial i at step t: counter word 0 is
- * 32 * (i / 128) + i % 32 and the output lane is (i % 128) / 32, so the four
- * lanes of one Philox block serve variables i, i+32, i+64, i+96. */
+/* The acceptance draw of trial i at step t: counter (i / 4, t, replica, 0),
+ * output lane i % 4, so one Philox block serves four consecutive variables. */
 static uint32_t draw_accept(uint64_t seed, int64_t i, uint32_t t, uint32_t rep)
 {
-    uint32_t c0 = (uint32_t)(32 * (i / 128) + (i % 32));
-    return philox_word(seed, c0, t, rep, 0u, (int)((i % 128) / 32));
+    return philox_word(seed, (uint32_t)(i / 4), t, rep, 0u, (int)(i % 4));
 }
 
 /* The choice draw of step t: one Philox block serves four consecutive steps,

@@ -68,21 +68,22 @@ namespace {
 
 bool is_int8(const da_ctx* c) { return c->dtype == DA_INT8; }
 
+// Default launch shape: one warp per replica while V <= 16 variables per
+// lane; beyond that more warps per replica, with shapes that keep the
+// registers within one wave of 7+ replicas per SM and spill nothing.
 StepShape auto_shape(int N)
 {
     StepShape s;
-    if (N <= 1024) {
+    if (N <= 512) {
         int V = 2;
         while (32 * V < N) V *= 2;
-        s.V = V;
-        s.G = 1;
-        s.rpb = 4;
+        s.V = V; s.G = 1; s.rpb = 4;
+    } else if (N <= 1024) {
+        s.V = 16; s.G = 2; s.rpb = 2;
     } else {
-        int G = 2;
-        while (32 * 32 * G < N) G *= 2;
-        s.V = 32;
-        s.G = G;
-        s.rpb = G == 2 ? 2 : 1;
+        int V = 8;
+        while (32 * 8 * V < N) V *= 2;
+        s.V = V; s.G = 8; s.rpb = 1;
     }
     return s;
 }
@@ -185,11 +186,11 @@ StepParams base_params(const da_ctx* c, const RunBuffers& b)
     return p;
 }
 
-// Zero the replica state: x = 0, h = 0, E = 0 (all runs start from the same
-// state, Sec. II).
-da_status reset_state(const RunBuffers& b, cudaStream_t st)
+// The start state of every replica: x = 0, so the effective fields are the
+// linear terms and E = 0 (all runs start from the same state, Sec. II).
+da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
-    DA_CU(cudaMemsetAsync(b.h(), 0, (size_t)b.R * b.s.npad() * 4, st));
+    DA_CU(da::launch_init_state(c->dtype == DA_INT8, c->diag, c->N, b.R, b.h(), b.s.npad(), st));
     DA_CU(cudaMemsetAsync(b.x(), 0, (size_t)2 * b.R * b.s.nwords() * 4, st));
     DA_CU(cudaMemsetAsync(b.sc(), 0, (size_t)b.R * sizeof(ReplicaScalars), st));
     return DA_OK;
@@ -225,7 +226,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
     StepParams p = base_params(c, b);
     p.beta = beta_dev;
     p.inc = inc;
-    p.seed = seed;
+    da::set_seed(p, seed);
     p.rep_base = 0;
     p.trace = trace_dev;
     p.trace_T = T;
@@ -319,6 +320,7 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
         for (int i = 0; i < n; ++i) {
             d[i] = q[(size_t)i * n + i];
             if (!std::isfinite(d[i])) return fail(DA_EINVAL, "non-finite Q entry");
+            amax = std::max(amax, std::fabs(d[i]));
             for (int j = i + 1; j < n; ++j) {
                 const float v = q[(size_t)i * n + j];
                 if (!std::isfinite(v)) return fail(DA_EINVAL, "non-finite Q entry");
@@ -417,7 +419,7 @@ static da_status anneal_common(da_ctx* c, const float* beta, bool beta_on_host, 
         DA_CU(cudaMemcpyAsync(b.base + L.beta, beta, (size_t)steps * 4, cudaMemcpyHostToDevice, st));
         beta_dev = reinterpret_cast<const float*>(b.base + L.beta);
     }
-    if (da_status e = reset_state(b, st)) return e;
+    if (da_status e = reset_state(c, b, st)) return e;
     int* trace_dev = want_trace ? reinterpret_cast<int*>(b.base + L.trace) : nullptr;
     if (da_status e = run_anneal(c, b, beta_dev, steps, inc, seed, recompute_every, trace_dev, st)) return e;
     if (da_status e = evaluate(c, b, st)) return e;
@@ -536,12 +538,12 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     DA_CU(cudaMemcpyAsync(temp_of, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
     DA_CU(cudaMemcpyAsync(rep_at, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
     if (n_sw) DA_CU(cudaMemsetAsync(swaps, 0, n_sw * 8, st));
-    if (da_status e = reset_state(b, st)) return e;
+    if (da_status e = reset_state(c, b, st)) return e;
     StepParams p = base_params(c, b);
     p.betas = betas_dev;
     p.temp_of = temp_of;
     p.inc = inc;
-    p.seed = seed;
+    da::set_seed(p, seed);
     for (long long sw = 0; sw < sweeps; ++sw) {
         p.t0 = sw * c->N;
         p.t1 = p.t0 + c->N;

@@ -43,22 +43,41 @@ struct StepParams {
     const int* temp_of = nullptr;
     float inc = 0.f;
     uint64_t seed = 0;
+    uint32_t round_key[2][10] = {};  // Philox round keys of seed (set by set_seed)
     uint32_t rep_base = 0;        // Philox replica id of replica r is rep_base + r
     long long t0 = 0, t1 = 0;     // steps [t0, t1)
     int* trace = nullptr;         // optional [R][trace_T]
     long long trace_T = 0;
 };
 
+// Philox4x32-10 round keys k + r * Weyl (r = 0..9) of a seed.
+inline void set_seed(StepParams& p, uint64_t seed)
+{
+    p.seed = seed;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.round_key[0][r] = a;
+        p.round_key[1][r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+}
+
+// Start state x = 0 of R replicas: fields g = diag (the effective field of
+// x = 0), words and scalars zero (da_fields.cu).
+cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st);
+
 // Step kernel launcher (da_step.cu).  is_int8 selects int8 W / int32 fields.
 cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 bool step_shape_supported(const StepShape& s);
 
 // Field recompute and energies (da_fields.cu).
-// Exact fields of R bit-packed states xs[R][nw] (words of 32 variables):
-// int8: h = W x in int32.  fp32: every W_ij is put on the grid 2^-S, summed
-// exactly in int64, and rounded once to fp32.  hout[R][npad] (npad >= N)
-// receives the fields (0 beyond N).  If E != nullptr, also writes the
-// energy sum_i x_i (d_i + h_i / 2) (int64 or fp64 bit pattern) to E[r*Estride].
+// Exact effective fields g = diag + W x of R bit-packed states xs[R][nw]
+// (words of 32 variables): int8: in int32.  fp32: every W_ij and diag_i is
+// put on the grid 2^-S, summed exactly in int64, and rounded once to fp32.
+// hout[R][npad] (npad >= N) receives the fields (0 beyond N).  If
+// E != nullptr, also writes the energy sum_i x_i (d_i + h_i / 2) (int64 or
+// fp64 bit pattern) to E[r*Estride].
 // sums_t is scratch of N * R int64 (layout [i][R]), required when E != nullptr.
 cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
@@ -70,7 +89,8 @@ cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                long long* swaps, uint8_t* swap_trace, long long sweep, long long sweeps,
                                uint64_t seed, cudaStream_t st);
 
-// Fixed-point scale of the fp32 recompute for max|W| = amax and N variables.
+// Fixed-point scale of the fp32 recompute for amax = max(|W_ij|, |diag_i|)
+// and N variables (N + 1 terms per sum).
 int fix_scale(float amax, int N);
 
 }  // namespace da

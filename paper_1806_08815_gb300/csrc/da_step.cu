@@ -2,10 +2,11 @@
 // (Algorithm 2 of arXiv:1806.08815) for many replicas at once.
 //
 // One group of G warps anneals one replica; lane l of warp w owns the
-// variables i = w*32V + 32v + l (v < V), keeping their fields h_i, linear
-// terms Q_ii and bits x_i in registers for the whole launch.  Per step:
-//   (a) every lane forms Delta E_i = (1 - 2 x_i)(Q_ii + h_i) for its V
-//       variables (all N trials of the step run in parallel, Sec. II);
+// variables i = w*32V + 32v + l (v < V), keeping their effective fields
+// g_i = Q_ii + sum_j W_ij x_j and bits x_i in registers for the whole launch.
+// Per step:
+//   (a) every lane forms Delta E_i = (1 - 2 x_i) g_i for its V variables (all
+//       N trials of the step run in parallel, Sec. II);
 //   (b) Metropolis against the dynamic offset: delta = Delta E - E_off is
 //       accepted when delta <= 0, else when u < exp(-beta delta); u is drawn
 //       only for trials whose outcome is not already decided (Philox is
@@ -14,7 +15,9 @@
 //       prefix sum of their popcounts finds the j-th accepted index,
 //       j = floor(u * count), and the chosen x_k flips while every lane adds
 //       +-W[k][i] (one coalesced pass over column k, read through L2) to its
-//       fields.  E_off returns to 0 on a flip and grows by inc otherwise.
+//       fields; the Philox words of the next step are computed while that
+//       column is in flight.  E_off returns to 0 on a flip and grows by inc
+//       otherwise.
 // A G = 1 group needs no shared memory or barrier: the words live one per
 // lane.  A G > 1 group exchanges its words through shared memory with one
 // named barrier per step; the energy of step t is booked after the barrier of
@@ -32,7 +35,6 @@ template <typename Tw> struct Arith;
 template <> struct Arith<int8_t> {
     using H = int32_t;    // fields and linear terms
     using E = long long;  // tracked energy
-    static __device__ __forceinline__ H add(H a, H b) { return a + b; }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
     static __device__ __forceinline__ H apply(H h, int8_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
     static __device__ __forceinline__ E load_e(long long b) { return b; }
@@ -42,7 +44,6 @@ template <> struct Arith<int8_t> {
 template <> struct Arith<float> {
     using H = float;
     using E = double;
-    static __device__ __forceinline__ H add(H a, H b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
     static __device__ __forceinline__ H apply(H h, float w, bool minus) { return minus ? __fsub_rn(h, w) : __fadd_rn(h, w); }
     static __device__ __forceinline__ E load_e(long long b) { return __longlong_as_double(b); }
@@ -77,8 +78,17 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Replicas per block and the blocks per SM the register budget is sized for:
+// at least 7 replicas per SM, so that 1024 replicas fill 152 SMs in one wave.
+template <int G> struct Occupancy;
+template <> struct Occupancy<1> { static constexpr int rpb = 4, min_blocks = 2; };
+template <> struct Occupancy<2> { static constexpr int rpb = 2, min_blocks = 4; };
+template <> struct Occupancy<4> { static constexpr int rpb = 1, min_blocks = 7; };
+template <> struct Occupancy<8> { static constexpr int rpb = 1, min_blocks = 2; };
+
 template <typename Tw, int V, int G, bool TRACE>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams p)
+__global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_blocks)
+    step_kernel(const __grid_constant__ StepParams p)
 {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -103,9 +113,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
     H* pub = reinterpret_cast<H*>(gs + 4 * NWG);  // [2] Delta E of the flipped variable
 
     const Tw* __restrict__ Wm = static_cast<const Tw*>(p.W);
-    const H* __restrict__ diag = static_cast<const H*>(p.diag);
     const int base = w * 32 * V + lane;
-    H h[V], d[V];
+    H h[V];
     uint32_t valid = 0, xm = 0;
     H* hg = static_cast<H*>(p.h) + (size_t)r * p.npad;
     uint32_t* xg = p.x + (size_t)r * p.nw;
@@ -115,7 +124,6 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
         const int i = base + 32 * v;
         const bool ok = i < p.N;
         h[v] = hg[i];
-        d[v] = ok ? diag[i] : H(0);
         valid |= (uint32_t)ok << v;
         xm |= ((xg[w * V + v] >> lane) & 1u) << v;
     }
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
     long long flips = sc.flips;
     uint32_t m = sc.m;
     const uint32_t rep = p.rep_base + (uint32_t)r;
-    const PhiloxKeys keys(p.seed);
+    const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
     const bool per_rep = p.betas != nullptr;
     const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
     u32x4 cr = {0, 0, 0, 0};
@@ -160,32 +168,31 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
         if (!per_rep && t + 1 < p.t1) beta_next = p.beta[t + 1];
         const float Eoff = __fmul_rn(__uint2float_rn(m), p.inc);
 
-        // (a) + (b): every trial of this lane.  Pass 1 decides what it can
-        // without a random number; pass 2 compares u with exp(-beta delta).
-        uint32_t accm = 0, needm = 0;
-        float ax[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const H tv = A::add(d[v], h[v]);
-            const H dE = ((xm >> v) & 1u) ? -tv : tv;
-            const float delta = A::delta(dE, Eoff);
-            const bool ok = (valid >> v) & 1u;
-            ax[v] = -__fmul_rn(beta, delta);
-            const bool le0 = delta <= 0.0f;
-            accm |= (uint32_t)(ok && le0) << v;
-            needm |= (uint32_t)(ok && !le0 && ax[v] > kExpCut) << v;
-        }
+        // (a) + (b): every trial of this lane, one Philox block of QS
+        // variables at a time; u is compared only where delta > 0 and
+        // exp(-beta delta) > 2^-24.
+        uint32_t accm = 0;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const uint32_t nq = (needm >> (q * QS)) & ((1u << QS) - 1u);
+            float ax[QS];
+            uint32_t nq = 0;
+#pragma unroll
+            for (int c = 0; c < QS; ++c) {
+                const int v = q * QS + c;
+                const H dE = ((xm >> v) & 1u) ? -h[v] : h[v];
+                const float delta = A::delta(dE, Eoff);
+                const bool ok = (valid >> v) & 1u;
+                ax[c] = -__fmul_rn(beta, delta);
+                const bool le0 = delta <= 0.0f;
+                accm |= (uint32_t)(ok && le0) << v;
+                nq |= (uint32_t)(ok && !le0 && ax[c] > kExpCut) << c;
+            }
             if (__any_sync(0xffffffffu, nq != 0u)) {
                 const int sub0 = (V % 4 == 0) ? 0 : (((w * 32 * V + 32 * q * QS) >> 5) & 3);
 #pragma unroll
                 for (int c = 0; c < QS; ++c) {
-                    const int v = q * QS + c;
-                    const float pr = exp_neg(ax[v]);
-                    const float u = uniform01(pick(rr[q], sub0 + c));
-                    accm |= (uint32_t)(((nq >> c) & 1u) && u < pr) << v;
+                    if ((nq >> c) & 1u)
+                        accm |= (uint32_t)metropolis_accept(ax[c], pick(rr[q], sub0 + c)) << (q * QS + c);
                 }
             }
         }
@@ -259,22 +266,18 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams p)
             const int gwk = k >> 5, kb = k & 31;
             const int wk = gwk / V, vk = gwk - wk * V;
             // Delta E_k from the owner's registers
-            H hk = h[0], dk = d[0];
+            H gk = h[0];
 #pragma unroll
             for (int v = 1; v < V; ++v)
-                if (v == vk) { hk = h[v]; dk = d[v]; }
+                if (v == vk) gk = h[v];
             uint32_t xold;
             H dEk = 0;
             if constexpr (G == 1) {
                 xold = (__shfl_sync(0xffffffffu, xm, kb) >> vk) & 1u;
-                const H tv = A::add(dk, hk);
-                dEk = __shfl_sync(0xffffffffu, xold ? -tv : tv, kb);
+                dEk = __shfl_sync(0xffffffffu, xold ? -gk : gk, kb);
             } else {
                 xold = (xw[gwk] >> kb) & 1u;
-                if (w == wk && lane == kb) {
-                    const H tv = A::add(dk, hk);
-                    pub[t & 1] = xold ? -tv : tv;
-                }
+                if (w == wk && lane == kb) pub[t & 1] = xold ? -gk : gk;
             }
             const Tw* __restrict__ col = Wm + (size_t)k * p.ldw;
             Tw cv[V];
@@ -356,7 +359,8 @@ bool step_shape_supported(const StepShape& s)
 {
     const bool g1 = s.G == 1 && (s.V == 2 || s.V == 4 || s.V == 8 || s.V == 16 || s.V == 32);
     const bool gn = (s.G == 2 || s.G == 4 || s.G == 8) && (s.V == 4 || s.V == 8 || s.V == 16 || s.V == 32);
-    return (g1 || gn) && s.rpb >= 1 && 32 * s.G * s.rpb <= 256;
+    const int max_rpb = s.G == 1 ? Occupancy<1>::rpb : s.G == 2 ? Occupancy<2>::rpb : 1;
+    return (g1 || gn) && s.rpb >= 1 && s.rpb <= max_rpb;
 }
 
 cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)

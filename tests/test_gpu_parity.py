@@ -67,6 +67,43 @@ def test_device_exp_matches_oracle_exhaustively(da):
     assert np.array_equal(da.binding.da_diag_expf(x).view(np.uint32), oracle.expf(x).view(np.uint32))
 
 
+def test_fast_exp_band_contains_exact_exp(da):
+    """For every fp32 x in (-16.7, 0] the kernel's band [lo, hi] around its fast
+    estimate contains 2^24 exp(x) of the exact exponential, so deciding u < exp(x)
+    outside the band gives the exact decision."""
+    import oracle
+    lo_bits = np.float32(-0.0).view(np.uint32)
+    hi_bits = np.float32(-16.7).view(np.uint32)
+    step = 1 << 25
+    worst = 0.0
+    for start in range(int(lo_bits), int(hi_bits), step):
+        x = np.arange(start, min(start + step, int(hi_bits)), dtype=np.uint32).view(np.float32)
+        lo, hi = da.binding.da_diag_exp_band(x)
+        P = oracle.expf(x).astype(np.float64) * 2.0 ** 24
+        assert np.all(lo.astype(np.float64) <= P) and np.all(hi.astype(np.float64) >= P)
+        worst = max(worst, float(np.max(np.minimum(P - lo, hi - P) / P)))
+    x = np.array([0.0], np.float32)
+    lo, hi = da.binding.da_diag_exp_band(x)
+    assert lo[0] <= 2.0 ** 24 <= hi[0]
+
+
+def test_accept_decision_matches_definition(da):
+    import oracle
+    rng = np.random.default_rng(5)
+    n = 1 << 22
+    x = -(rng.random(n) * 16.7).astype(np.float32)
+    p = oracle.expf(x)
+    # words whose u falls right at, just below and just above p, plus random ones
+    P = np.floor(p.astype(np.float64) * 2 ** 24).astype(np.int64)
+    U = np.concatenate([P - 1, P, P + 1, rng.integers(1, 2 ** 24 + 1, n)])
+    U = np.clip(U, 1, 2 ** 24)
+    xs = np.concatenate([x, x, x, x])
+    w = ((U - 1).astype(np.uint64) << 8).astype(np.uint32) | rng.integers(0, 256, xs.size).astype(np.uint32)
+    got = da.binding.da_diag_accept(xs, w)
+    ref = (U.astype(np.float64) * 2.0 ** -24 < oracle.expf(xs).astype(np.float64)).astype(np.uint8)
+    assert np.array_equal(got, ref)
+
+
 def test_device_philox_matches_oracle(da):
     import oracle
     rng = np.random.default_rng(1)
@@ -90,7 +127,7 @@ def test_sk_bimodal_n64_full_config(da, inst):
     _compare_anneal(got, ref, q.Q, True)
 
 
-SHAPES = [(0, 0, 0), (4, 1, 8), (8, 1, 3), (4, 2, 4), (4, 4, 1), (4, 8, 1), (8, 2, 2)]
+SHAPES = [(0, 0, 0), (4, 1, 4), (8, 1, 3), (4, 2, 2), (4, 4, 1), (4, 8, 1), (8, 2, 1)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -125,7 +162,7 @@ def test_int8_larger_sizes(da, inst, N, shape):
     _compare_anneal(got, ref, q.Q, True)
 
 
-@pytest.mark.parametrize("shape", [(0, 0, 0), (4, 2, 2), (8, 1, 4)])
+@pytest.mark.parametrize("shape", [(0, 0, 0), (4, 2, 2), (8, 1, 4), (8, 4, 1), (16, 2, 2)])
 def test_fp32_sk_gaussian_with_recompute(da, inst, shape):
     import oracle
     q = inst.sk_gaussian(256, 5)
@@ -221,7 +258,7 @@ def test_energy_and_recompute_entry_points(da, inst):
         if q.bimodal:
             assert np.array_equal(E, ref.astype(float))
             for r in range(9):
-                assert np.array_equal(h[r], oracle.fields_int(q.Q, xp[r]))
+                assert np.array_equal(h[r], oracle.fields_int(q.Q, xp[r]) + np.diag(q.Q))
         else:
             assert np.allclose(E, ref, rtol=1e-12, atol=1e-12)
             for r in range(9):
