@@ -126,10 +126,10 @@ da_status da_ctx_info(const da_ctx* ctx, int64_t* N, da_dtype* dtype);
 
 /* Fix the launch shape of the step kernel for this context instead of the
  * automatic choice: a group of G warps per replica, V variables per lane
- * (32 * V * G >= N), rpb replicas per thread block.  Supported: G = 1 with
- * V in {2, 4, 8, 16, 32} and rpb <= 4; G = 2 with rpb <= 2; G in {4, 8} with
- * rpb = 1; for G > 1, V in {4, 8, 16, 32}.  V = 0 restores the automatic
- * choice.  Results do
+ * (32 * V * G >= N), rpb replicas per thread block.  Supported: G = 1 or 2
+ * with V in {4, 8, 16, 32}; G = 4 with V in {4, 8, 16}; G = 8 with V in
+ * {8, 16, 32}; rpb <= 4 (G = 1), <= 2 (G = 2), = 1 (G = 4, 8).  V = 0
+ * restores the automatic choice.  Results do
  * not depend on the shape (the random numbers are keyed by variable index,
  * step and replica).  Errors: DA_EINVAL. */
 da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);

@@ -75,7 +75,7 @@ StepShape auto_shape(int N)
 {
     StepShape s;
     if (N <= 512) {
-        int V = 2;
+        int V = 4;
         while (32 * V < N) V *= 2;
         s.V = V; s.G = 1; s.rpb = 4;
     } else if (N <= 1024) {
@@ -288,7 +288,9 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     const int n = (int)N;
     const int ldw = (int)align_up((size_t)n, 128);
     const size_t esz = dtype == DA_INT8 ? 1 : 4;
-    std::vector<char> Wh((size_t)n * ldw * esz, 0);
+    // 8192 zero entries after the last row: a lane whose slice straddles N
+    // reads up to the launch width (at most 8192) past the row start
+    std::vector<char> Wh(((size_t)n * ldw + 8192) * esz, 0);
     std::vector<char> dh((size_t)n * 4, 0);
     float amax = 0.f;
     if (dtype == DA_INT8) {

@@ -127,7 +127,7 @@ def test_sk_bimodal_n64_full_config(da, inst):
     _compare_anneal(got, ref, q.Q, True)
 
 
-SHAPES = [(0, 0, 0), (4, 1, 4), (8, 1, 3), (4, 2, 2), (4, 4, 1), (4, 8, 1), (8, 2, 1)]
+SHAPES = [(0, 0, 0), (4, 1, 4), (8, 1, 3), (4, 2, 2), (4, 4, 1), (8, 8, 1), (8, 2, 1)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
