@@ -310,18 +310,22 @@ static void recompute_sums(const inst_t* I, int32_t S, const uint8_t* x, int64_t
     }
 }
 
-/* E = sum_{i: x_i = 1} (Q_ii + h_i / 2) in fp64, index order, where
- * h_i = (sums_i - round(Q_ii 2^S)) 2^-S is the exact coupling part. */
+/* The energy that goes with the recompute, E = sum_{x_i = 1} (Q_ii + g_i) / 2
+ * with g_i = Q_ii + sum_j W_ij x_j, summed exactly in fixed point:
+ * E 2^(S+1) = sum_{x_i = 1} (round(Q_ii 2^S) + sums_i), an integer below 2^76
+ * held in __int128, then rounded once to fp64 (its top and bottom parts
+ * recombined with one fused multiply-add) and scaled by 2^-(S+1). */
 static double recompute_energy(const inst_t* I, int32_t S, const uint8_t* x, const int64_t* sums)
 {
-    double E = 0.0;
+    __int128 acc = 0;
     for (int64_t i = 0; i < I->N; ++i) {
         if (!x[i]) continue;
-        const int64_t hfix = sums[i] - (int64_t)llrintf(ldexpf(I->df[i], S));
-        double hd = ldexp((double)hfix, -S);
-        E += (double)I->df[i] + 0.5 * hd;
+        acc += (__int128)((int64_t)llrintf(ldexpf(I->df[i], S)) + sums[i]);
     }
-    return E;
+    const int64_t top = (int64_t)(acc >> 32);
+    const uint32_t bottom = (uint32_t)(acc & 0xFFFFFFFF);
+    const double v = fma((double)top, 4294967296.0, (double)bottom);
+    return ldexp(v, -(S + 1));
 }
 
 int orc_recompute_f32(int64_t N, const float* Q, const uint32_t* x, float* h, int64_t* sums, int32_t* S_out)

@@ -70,8 +70,8 @@ int orc_fields_int(int64_t N, const int32_t* Q, const uint32_t* x, int64_t* h);
  * summed exactly in int64, and rounded once to fp32.  sums[N] (may be NULL)
  * receives the exact integer sums, *S_out the scale. */
 int orc_recompute_f32(int64_t N, const float* Q, const uint32_t* x, float* h, int64_t* sums, int32_t* S_out);
-/* The energy that accompanies the recompute: sum_i x_i (Q_ii + h_i/2) in fp64,
- * index order, with h_i = sums_i * 2^-S in fp64. */
+/* The energy that accompanies the recompute: sum_i x_i (Q_ii + g_i) / 2 summed
+ * exactly on the fixed-point grid and rounded once to fp64. */
 double orc_recompute_energy_f32(int64_t N, const float* Q, const uint32_t* x);
 
 /* The Digital Annealer (Algorithm 2) run R times from x = 0.

@@ -168,3 +168,16 @@ def test_recompute_energy_matches_exact_energy(orc):
     for x in X:
         E = orc.recompute_energy_f32(inst.Q, orc.pack(x)[0])
         assert E == pytest.approx(orc.energy(inst.Q, orc.pack(x))[0], rel=1e-13, abs=1e-13)
+
+
+def test_recompute_energy_is_the_rounded_exact_fixed_point_sum(orc):
+    """E = sum_{x_i=1} (round(Q_ii 2^S) + sums_i) / 2^(S+1), rounded once to fp64."""
+    for inst in (instances.sk_gaussian(50, 8), instances.lattice2d(6, 2, True)):
+        rng = np.random.default_rng(11)
+        for _ in range(5):
+            x = rng.integers(0, 2, inst.N)
+            _, sums, S = orc.recompute_f32(inst.Q, orc.pack(x)[0])
+            scale = Fraction(2) ** S
+            exact = sum(round(Fraction(float(inst.Q[i, i])) * scale) + int(sums[i])
+                        for i in range(inst.N) if x[i])
+            assert orc.recompute_energy_f32(inst.Q, orc.pack(x)[0]) == float(Fraction(exact) / (2 * scale))
