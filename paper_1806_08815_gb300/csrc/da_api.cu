@@ -6,7 +6,7 @@
 //   xs     [2R][nw]    current states, then best states (adjacent, so the
 //                      final exact evaluation treats them as 2R states)
 //   sc     [R]         ReplicaScalars (tracked E, best E, flips, offset count)
-//   sums_t [N][2R]     int64 scratch of the exact recompute
+//   sums   [N/64][2R] 128-bit partial energies of the exact recompute
 //   E_ex   [2R]        exact energies of the final and best states
 // The instance itself (symmetric W with row pitch ldw, and diag) lives in the
 // context for its whole life.
@@ -68,18 +68,16 @@ namespace {
 
 bool is_int8(const da_ctx* c) { return c->dtype == DA_INT8; }
 
-// Default launch shape: one warp per replica while V <= 16 variables per
-// lane; beyond that more warps per replica, with shapes that keep the
-// registers within one wave of 7+ replicas per SM and spill nothing.
+// Default launch shape: one warp per replica up to N = 1024 (V <= 32
+// variables per lane); beyond that 8 warps per replica, with shapes that keep
+// the registers within one wave of 7+ replicas per SM and spill nothing.
 StepShape auto_shape(int N)
 {
     StepShape s;
-    if (N <= 512) {
+    if (N <= 1024) {
         int V = 4;
         while (32 * V < N) V *= 2;
         s.V = V; s.G = 1; s.rpb = 4;
-    } else if (N <= 1024) {
-        s.V = 16; s.G = 2; s.rpb = 2;
     } else {
         int V = 8;
         while (32 * 8 * V < N) V *= 2;
@@ -125,7 +123,7 @@ Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_b
     L.h = take((size_t)R * s.npad() * 4);
     L.xs = take((size_t)2 * R * s.nwords() * 4);
     L.sc = take((size_t)R * sizeof(ReplicaScalars));
-    L.sums = take((size_t)c->N * 2 * R * 8);
+    L.sums = take((size_t)16 * ((std::max(s.npad(), c->N) + 63) / 64) * 2 * R);
     L.eex = take((size_t)2 * R * 8);
     L.beta = take(with_beta ? (size_t)T * 4 : 0);
     L.res = take((size_t)4 * R * 8);
@@ -589,7 +587,7 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     const size_t words = (size_t)da_words(c->N);
     const size_t xb = align_up((size_t)R * words * 4, 256);
     const size_t hb = align_up((size_t)R * c->N * 4, 256);
-    const size_t sb = align_up((size_t)R * c->N * 8, 256);
+    const size_t sb = align_up((size_t)16 * ((c->N + 63) / 64) * R, 256);
     const size_t eb = align_up((size_t)R * 8, 256);
     if (da_status e = ensure_ws(c, xb + hb + sb + eb)) return e;
     char* base = static_cast<char*>(c->ws);

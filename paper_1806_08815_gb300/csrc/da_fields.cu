@@ -1,23 +1,26 @@
-// da_fields.cu -- exact full recompute of the local fields h = W x for many
-// states, and the energies that go with it.
+// da_fields.cu -- exact full recompute of the effective fields
+// g = diag(Q) + W x for many states, and the energies that go with it.
 //
 // The DA never computes fields from scratch during a run: all runs start at
-// x = 0, where h = 0 and E = 0 (Sec. II, "avoiding the calculation of the
-// initial N effective fields").  This library recomputes them only to bound
-// the drift of the fp32 fields (one rounding per update) and to evaluate the
-// final and best states exactly:
-//   int8 couplings:  h_i = sum_j W_ij x_j in int32 (exact);
-//   fp32 couplings:  every W_ij is put on the grid 2^-S (S from max|W| and N
-//                    so that no sum can overflow), the products are summed
-//                    exactly in int64, and h_i is the single fp32 rounding of
-//                    that sum.  The result does not depend on the order of the
-//                    summation, so any tiling gives the same bits.
-// The recompute returns the effective fields g_i = Q_ii + sum_j W_ij x_j that
-// the step kernel keeps (Delta E_i = (1 - 2 x_i) g_i); for fp32, Q_ii joins
-// the fixed-point sum as one more term.
-// Energies: E = sum_i x_i (Q_ii + h_i / 2), exact in int64 for int8; for fp32
-// the terms use h_i = (sum_i - round(Q_ii 2^S)) 2^-S in fp64 and are added in
-// index order.
+// x = 0, where the fields are the linear terms and E = 0 (Sec. II, "avoiding
+// the calculation of the initial N effective fields").  This library
+// recomputes them only to bound the drift of the fp32 fields (one rounding per
+// update) and to evaluate final and best states exactly:
+//   int8 couplings:  g_i = Q_ii + sum_j W_ij x_j in integers (exact);
+//   fp32 couplings:  Q_ii and every W_ij are put on the grid 2^-S (S from
+//                    max(|W|, |Q_ii|) and N, so that no sum can overflow),
+//                    summed exactly in int64, and g_i is the single fp32
+//                    rounding of that sum.
+// Energies: E = sum_{x_i=1} (Q_ii + g_i) / 2, summed exactly (int64 for int8;
+// on the fixed-point grid in 128-bit integers for fp32, then rounded once to
+// fp64).  Every sum is exact, so the tiling and the reduction order do not
+// change a single bit.
+//
+// Tiling: a block owns 64 rows (variables i) and 32 states (4 per warp).  For
+// each chunk of 32 columns j it stages the fixed-point tile of W in shared
+// memory once, and every warp walks the set bits of its states' word j/32:
+// only x_j = 1 contributes, and the loop is uniform across the warp.
+#include <algorithm>
 #include <cmath>
 
 #include "da_internal.h"
@@ -25,12 +28,18 @@
 namespace da {
 namespace {
 
-constexpr int kRowsPerBlock = 128;
-constexpr int kRepsPerThread = 16;
+constexpr int kRows = 64;           // rows per block
+constexpr int kStatesPerWarp = 4;
+constexpr int kWarps = 8;
+constexpr int kStates = kWarps * kStatesPerWarp;
 
-// Thread = one row i (variable) and kRepsPerThread states.  W is symmetric,
-// so row j of the matrix is read as column j: consecutive threads read
-// consecutive addresses of row j.
+template <bool INT8>
+__device__ __forceinline__ long long fixed_of(const void* a, size_t idx, int S)
+{
+    if constexpr (INT8) return (long long)static_cast<const int8_t*>(a)[idx];
+    else return __float2ll_rn(ldexpf(static_cast<const float*>(a)[idx], S));
+}
+
 template <bool INT8>
 __device__ __forceinline__ long long fixed_diag(const void* diag, int i, int S)
 {
@@ -38,88 +47,123 @@ __device__ __forceinline__ long long fixed_diag(const void* diag, int i, int S)
     else return __float2ll_rn(ldexpf(static_cast<const float*>(diag)[i], S));
 }
 
-template <bool INT8>
-__global__ void __launch_bounds__(kRowsPerBlock) recompute_kernel(const void* __restrict__ Wv,
-                                                                  const void* __restrict__ diag, int N, int ldw,
-                                                                  int S, const uint32_t* __restrict__ xs, int nw,
-                                                                  int R, void* hout, int npad, long long* sums_t)
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ I128 i128_of(long long v) { return {(unsigned long long)v, v < 0 ? -1ll : 0ll}; }
+
+__device__ __forceinline__ I128 i128_add(I128 a, I128 b)
 {
-    const int i = blockIdx.x * kRowsPerBlock + threadIdx.x;
-    const int r0 = blockIdx.y * kRepsPerThread;
-    const bool row_ok = i < N;
-    const long long d0 = row_ok ? fixed_diag<INT8>(diag, i, S) : 0ll;
-    long long acc[kRepsPerThread];
+    I128 c;
+    c.lo = a.lo + b.lo;
+    c.hi = a.hi + b.hi + (c.lo < a.lo ? 1 : 0);
+    return c;
+}
+
+__device__ __forceinline__ I128 warp_sum(I128 v)
+{
 #pragma unroll
-    for (int q = 0; q < kRepsPerThread; ++q) acc[q] = d0;
-    __shared__ uint32_t xw[kRepsPerThread][33];
+    for (int o = 16; o > 0; o >>= 1) {
+        I128 n;
+        n.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        n.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        v = i128_add(v, n);
+    }
+    return v;
+}
+
+// Fields of states xs[R][nw] for rows [64 bx, 64 bx + 64); partial energy
+// sums of those rows into part[bx][R] (two 64-bit words each).
+template <bool INT8>
+__global__ void __launch_bounds__(kWarps * 32) recompute_kernel(const void* __restrict__ Wv,
+                                                                const void* __restrict__ diag, int N, int ldw, int S,
+                                                                const uint32_t* __restrict__ xs, int nw, int R,
+                                                                void* hout, int npad, I128* part)
+{
+    __shared__ long long M[32][kRows];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int i0 = blockIdx.x * kRows;
+    const int r0 = blockIdx.y * kStates + warp * kStatesPerWarp;
+    const int ia = i0 + lane, ib = i0 + 32 + lane;
+    long long acc[kStatesPerWarp][2];
+    const long long da_ = ia < N ? fixed_diag<INT8>(diag, ia, S) : 0ll;
+    const long long db_ = ib < N ? fixed_diag<INT8>(diag, ib, S) : 0ll;
+#pragma unroll
+    for (int q = 0; q < kStatesPerWarp; ++q) { acc[q][0] = da_; acc[q][1] = db_; }
+
+    // staging: thread t loads 8 consecutive entries of row j0 + t/8
+    const int sj = threadIdx.x >> 3;
+    const int sc = (threadIdx.x & 7) * 8;
     for (int j0 = 0; j0 < N; j0 += 32) {
         __syncthreads();
-        if (threadIdx.x < kRepsPerThread) {
-            const int rr = r0 + threadIdx.x;
-            xw[threadIdx.x][0] = rr < R ? xs[(size_t)rr * nw + (j0 >> 5)] : 0u;
+        const int j = j0 + sj;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int i = i0 + sc + c;
+            M[sj][sc + c] = (j < N && i < N) ? fixed_of<INT8>(Wv, (size_t)j * ldw + i, S) : 0ll;
         }
         __syncthreads();
-        uint32_t bits[kRepsPerThread];
 #pragma unroll
-        for (int q = 0; q < kRepsPerThread; ++q) bits[q] = xw[q][0];
-        const int jn = min(32, N - j0);
-        for (int jj = 0; jj < jn; ++jj) {
-            long long mval = 0;
-            if (row_ok) {
-                const int j = j0 + jj;
-                if constexpr (INT8) {
-                    mval = (long long)static_cast<const int8_t*>(Wv)[(size_t)j * ldw + i];
-                } else {
-                    const float wf = static_cast<const float*>(Wv)[(size_t)j * ldw + i];
-                    mval = __float2ll_rn(ldexpf(wf, S));
-                }
+        for (int q = 0; q < kStatesPerWarp; ++q) {
+            const int r = r0 + q;
+            uint32_t word = r < R ? xs[(size_t)r * nw + (j0 >> 5)] : 0u;
+            while (word) {
+                const int jj = __ffs(word) - 1;
+                word &= word - 1;
+                acc[q][0] += M[jj][lane];
+                acc[q][1] += M[jj][32 + lane];
             }
-#pragma unroll
-            for (int q = 0; q < kRepsPerThread; ++q)
-                acc[q] += ((bits[q] >> jj) & 1u) ? mval : 0ll;
         }
     }
-    if (i >= npad) return;
+
 #pragma unroll
-    for (int q = 0; q < kRepsPerThread; ++q) {
-        const int rr = r0 + q;
-        if (rr >= R) break;
+    for (int q = 0; q < kStatesPerWarp; ++q) {
+        const int r = r0 + q;
+        if (r >= R) break;     // warp-uniform
         if (hout) {
-            if constexpr (INT8)
-                static_cast<int32_t*>(hout)[(size_t)rr * npad + i] = row_ok ? (int32_t)acc[q] : 0;
-            else
-                static_cast<float*>(hout)[(size_t)rr * npad + i] = row_ok ? ldexpf(__ll2float_rn(acc[q]), -S) : 0.f;
+            if (ia < npad) {
+                if constexpr (INT8)
+                    static_cast<int32_t*>(hout)[(size_t)r * npad + ia] = ia < N ? (int32_t)acc[q][0] : 0;
+                else
+                    static_cast<float*>(hout)[(size_t)r * npad + ia] = ia < N ? ldexpf(__ll2float_rn(acc[q][0]), -S) : 0.f;
+            }
+            if (ib < npad) {
+                if constexpr (INT8)
+                    static_cast<int32_t*>(hout)[(size_t)r * npad + ib] = ib < N ? (int32_t)acc[q][1] : 0;
+                else
+                    static_cast<float*>(hout)[(size_t)r * npad + ib] = ib < N ? ldexpf(__ll2float_rn(acc[q][1]), -S) : 0.f;
+            }
         }
-        if (sums_t && row_ok) sums_t[(size_t)i * R + rr] = acc[q];
+        if (part) {
+            const uint32_t xa = ia < N ? (xs[(size_t)r * nw + (ia >> 5)] >> (ia & 31)) & 1u : 0u;
+            const uint32_t xb = ib < N ? (xs[(size_t)r * nw + (ib >> 5)] >> (ib & 31)) & 1u : 0u;
+            I128 t = i128_add(i128_of(xa ? da_ + acc[q][0] : 0ll), i128_of(xb ? db_ + acc[q][1] : 0ll));
+            t = warp_sum(t);
+            if (lane == 0) part[(size_t)blockIdx.x * R + r] = t;
+        }
     }
 }
 
-// One thread per state: E = sum_i x_i (d_i + h_i / 2) in index order.
+// E[r] = (sum over row tiles of the partial sums) / 2^(S+1), exact for int8,
+// rounded once to fp64 for fp32.
 template <bool INT8>
-__global__ void energy_kernel(const void* __restrict__ diag, int N, int S, const uint32_t* __restrict__ xs, int nw,
-                              int R, const long long* __restrict__ sums_t, long long* E, int Estride)
+__global__ void energy_kernel(const I128* __restrict__ part, int tiles, int R, int S, long long* E, int Estride)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
-    const uint32_t* x = xs + (size_t)r * nw;
+    I128 s = {0ull, 0ll};
+    for (int b = 0; b < tiles; ++b) s = i128_add(s, part[(size_t)b * R + r]);
     if constexpr (INT8) {
-        long long lin = 0, quad = 0;
-        for (int i = 0; i < N; ++i) {
-            if (!((x[i >> 5] >> (i & 31)) & 1u)) continue;
-            const long long di = static_cast<const int32_t*>(diag)[i];
-            lin += di;
-            quad += sums_t[(size_t)i * R + r] - di;
-        }
-        E[(size_t)r * Estride] = lin + quad / 2;
+        E[(size_t)r * Estride] = (long long)s.lo / 2;   // |2E| < 2^63
     } else {
-        double e = 0.0;
-        for (int i = 0; i < N; ++i) {
-            if (!((x[i >> 5] >> (i & 31)) & 1u)) continue;
-            const long long hfix = sums_t[(size_t)i * R + r] - fixed_diag<false>(diag, i, S);
-            const double hd = ldexp(__ll2double_rn(hfix), -S);
-            e = __dadd_rn(e, __dadd_rn((double)static_cast<const float*>(diag)[i], __dmul_rn(0.5, hd)));
-        }
-        E[(size_t)r * Estride] = __double_as_longlong(e);
+        // value = hi 2^64 + lo; top = value >> 32 (exact in fp64, |value| < 2^76)
+        const long long top = (long long)((unsigned long long)s.hi << 32 | (s.lo >> 32));
+        const double bottom = (double)(uint32_t)(s.lo & 0xFFFFFFFFull);
+        const double v = __fma_rn((double)top, 4294967296.0, bottom);
+        E[(size_t)r * Estride] = __double_as_longlong(ldexp(v, -(S + 1)));
     }
 }
 
@@ -163,22 +207,24 @@ cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void
 
 cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
-                             long long* E, int Estride, cudaStream_t st, long long* sums_t)
+                             long long* E, int Estride, cudaStream_t st, long long* scratch)
 {
     if (R <= 0) return cudaSuccess;
-    const int rows = hout ? npad : N;
-    dim3 grid((rows + kRowsPerBlock - 1) / kRowsPerBlock, (R + kRepsPerThread - 1) / kRepsPerThread);
+    const int rows = hout ? std::max(npad, N) : N;
+    const int tiles = (rows + kRows - 1) / kRows;
+    dim3 grid(tiles, (R + kStates - 1) / kStates);
+    I128* part = E ? reinterpret_cast<I128*>(scratch) : nullptr;
     if (is_int8)
-        recompute_kernel<true><<<grid, kRowsPerBlock, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, sums_t);
+        recompute_kernel<true><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
     else
-        recompute_kernel<false><<<grid, kRowsPerBlock, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, sums_t);
+        recompute_kernel<false><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !E) return err;
     const int tb = 128;
     if (is_int8)
-        energy_kernel<true><<<(R + tb - 1) / tb, tb, 0, st>>>(diag, N, S, xs, nw, R, sums_t, E, Estride);
+        energy_kernel<true><<<(R + tb - 1) / tb, tb, 0, st>>>(part, tiles, R, S, E, Estride);
     else
-        energy_kernel<false><<<(R + tb - 1) / tb, tb, 0, st>>>(diag, N, S, xs, nw, R, sums_t, E, Estride);
+        energy_kernel<false><<<(R + tb - 1) / tb, tb, 0, st>>>(part, tiles, R, S, E, Estride);
     return cudaGetLastError();
 }
 

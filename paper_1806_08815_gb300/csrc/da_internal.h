@@ -76,12 +76,12 @@ bool step_shape_supported(const StepShape& s);
 // (words of 32 variables): int8: in int32.  fp32: every W_ij and diag_i is
 // put on the grid 2^-S, summed exactly in int64, and rounded once to fp32.
 // hout[R][npad] (npad >= N) receives the fields (0 beyond N).  If
-// E != nullptr, also writes the energy sum_i x_i (d_i + h_i / 2) (int64 or
-// fp64 bit pattern) to E[r*Estride].
-// sums_t is scratch of N * R int64 (layout [i][R]), required when E != nullptr.
+// E != nullptr, also writes the energy sum_{x_i=1} (d_i + g_i) / 2 (int64 or
+// fp64 bit pattern) to E[r*Estride]; scratch must then hold
+// 16 * ceil(max(npad, N) / 64) * R bytes.
 cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
-                             long long* E, int Estride, cudaStream_t st, long long* sums_t);
+                             long long* E, int Estride, cudaStream_t st, long long* scratch);
 
 // PT exchange (da_pt.cu).
 cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
