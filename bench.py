@@ -33,6 +33,17 @@ if ROOT not in sys.path:
 
 C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1, beta1=10.0, inc=0.0,
           instance_seed=0, seed=0)
+
+# DRAM bytes per step-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# capture summarised in profiles/, valid while the kernel source has the recorded hash.
+STEP_TRAFFIC = {"source_sha256_16": "3f9c044d33fd01ed", "bytes_per_launch": 8.606976e6,
+                "profile": "profiles/step_kernel_f32_v32_g1_sk_gaussian_n1024_r1024.md"}
+
+
+def step_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1806_08815_gb300", "csrc", "da_step.cuh")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 METRIC = "single-flip trials/s (DA step, SK-Gaussian N=1024, 1024 replicas, 2e5 steps)"
 UNIT = "trials/s"
 
@@ -170,6 +181,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--steps-per-anneal", type=int, default=C3["steps"])
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="run two 2048-step anneals from the middle of the schedule and exit (for ncu captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +219,14 @@ def main():
 
     def one_step():
         da.da_anneal_async(ctx, beta_dev, T, C3["inc"], R, seed, P, out, stream)
+
+    if args.kernel_case:
+        mid = torch.from_numpy(instances.beta_linear(C3["beta0"], C3["beta1"], C3["steps"])[100_000:102_048]).to(dev)
+        for _ in range(2):
+            da.da_anneal_async(ctx, mid, mid.numel(), C3["inc"], R, seed, P, out, stream)
+            stream.synchronize()
+        print(json.dumps({"kernel_case": "sk_gaussian_N1024_R1024 steps 100000..102047", "ok": True}))
+        return
 
     for _ in range(args.warmup):
         one_step()
@@ -279,7 +300,9 @@ def main():
                 "d2h_bytes_per_step": int(res_bytes)},
         "gpu_launches": gpu_launches * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm, "traffic": None,
+                     "frac": achieved_gbs / hbm,
+                     "traffic": STEP_TRAFFIC["bytes_per_launch"]
+                     if step_source_sha() == STEP_TRAFFIC["source_sha256_16"] else None,
                      "kernel": "step_kernel<float,V=32,G=1>", "peak_source": peak_src,
                      "basis": "nominal bytes per replica-step: fp32 column of W + fields + state bits"},
         "step_kernel": {"launches": launches, "avg_launch_ms": avg_launch_s * 1e3,
