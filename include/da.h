@@ -186,6 +186,37 @@ da_status da_field_recompute(da_ctx* ctx, const uint32_t* x, int32_t R, void* h)
 da_status da_profile_enable(da_ctx* ctx, int32_t on);
 da_status da_profile_read(da_ctx* ctx, int64_t* launches, double* total_ms);
 
+/* An integer anneal that allocates nothing.  Some callers cannot allocate
+ * device memory at the moment they want to anneal: a service that reserves
+ * the GPU's memory up front and forbids later allocations, code inside
+ * another framework's allocator-free region, or a program about to capture
+ * its work into a CUDA graph.  This entry point runs the same anneal as
+ * da_anneal_async on a DA_INT8 instance, with every intermediate buffer in one
+ * fixed 16 MiB device array that the library defines (each device that loads
+ * the library holds it until the process exits); it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The paper has no counterpart: this
+ * is a property of the library, not of the method.
+ *   W      device, int8, N x ldw row-major: the symmetric couplings W_ij = Q_ij
+ *          (i < j) mirrored, zero diagonal; entries in columns N..ldw-1 are read
+ *          but only affect padding.  ldw >= da_static_pitch(N), a multiple of 16.
+ *   diag   device, int32, the N linear terms Q_ii.
+ *   N      1 <= N <= 1024.
+ *   beta   device, [steps] schedule; other arguments as in da_anneal_async.
+ *   out    device result arrays (each may be NULL).
+ * Sizes beyond the array (roughly replicas * N > 3.4e6 at N = 1024) return
+ * DA_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call reuses the same array, so calls that overlap on the GPU
+ * (different streams, or different host threads without ordering) race; order
+ * them on one stream.  The call re-initialises the parts it needs, so results do
+ * not depend on earlier calls.  Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_anneal_static(const int8_t* W, const int32_t* diag, int64_t N, int64_t ldw, const float* beta,
+                           int64_t steps, float offset_inc, int32_t replicas, uint64_t seed,
+                           const da_dev_result* out, void* stream);
+/* The smallest row pitch da_anneal_static accepts for N variables (0 if N is
+ * out of range). */
+int64_t da_static_pitch(int64_t N);
+
 /* Diagnostics: run the device's own fp32 exponential (used for every
  * Metropolis decision) on n host values x[n] -> y[n], and its Philox4x32-10
  * (Salmon et al., SC'11) on n host records ctr_key[6n] = (c0, c1, c2, c3, k0,

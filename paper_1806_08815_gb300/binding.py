@@ -78,6 +78,10 @@ def lib() -> ctypes.CDLL:
     L.da_profile_read.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.da_profile_enable.restype = ctypes.c_int
     L.da_profile_read.restype = ctypes.c_int
+    L.da_anneal_static.argtypes = [_P, _P, i64, i64, _P, i64, f32, i32, u64, ctypes.POINTER(da_dev_result), _P]
+    L.da_anneal_static.restype = ctypes.c_int
+    L.da_static_pitch.argtypes = [i64]
+    L.da_static_pitch.restype = i64
     L.da_diag_exp_band.argtypes = [_P, _P, _P, i64]
     L.da_diag_accept.argtypes = [_P, _P, _P, i64]
     L.da_diag_exp_band.restype = ctypes.c_int
@@ -246,3 +250,19 @@ def da_diag_accept(x: np.ndarray, w: np.ndarray) -> np.ndarray:
     acc = np.empty(xs.size, np.uint8)
     _check(lib().da_diag_accept(_ptr(xs), _ptr(ws), _ptr(acc), xs.size))
     return acc
+
+
+def da_static_pitch(N: int) -> int:
+    return int(lib().da_static_pitch(int(N)))
+
+
+def da_anneal_static(W_dev, diag_dev, N: int, ldw: int, beta_dev, steps: int, offset_inc: float, replicas: int,
+                     seed: int, out: dict, stream) -> None:
+    """The allocation-free integer anneal (see da_anneal_static in include/da.h); every
+    argument that is an array is a device tensor owned by the caller."""
+    res = da_dev_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                      "flips", "trace")))
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().da_anneal_static(_ptr(W_dev), _ptr(diag_dev), int(N), int(ldw), _ptr(beta_dev), int(steps),
+                                  float(offset_inc), int(replicas), int(seed) & (2 ** 64 - 1), ctypes.byref(res),
+                                  _P(int(handle) if handle else 0)))
