@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--steps-per-anneal", type=int, default=C3["steps"])
+    ap.add_argument("--plain-steps", type=int, default=10_000,
+                    help="steps of the plain one-launch-per-step GPU form timed beside (0 = skip)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run two 2048-step anneals from the middle of the schedule and exit (for ncu captures)")
     args = ap.parse_args()
@@ -276,6 +278,17 @@ def main():
         res_bytes = sum(r2[k].nbytes for k in ("final_E", "best_E", "final_x", "best_x", "max_drift", "flips"))
     e2e_v = world * trials / float(np.mean(e2e_times))
 
+    # the plain one-launch-per-step GPU form on a sample of the same workload
+    plain = None
+    if rank == 0 and args.plain_steps > 0:
+        Tp = min(args.plain_steps, T)
+        da.da_anneal_plain(ctx, beta[:64], C3["inc"], R, seed)            # warm-up
+        torch.cuda.synchronize()
+        rp = da.da_anneal_plain(ctx, beta[:Tp], C3["inc"], R, seed)
+        plain = {"value": R * Tp * N / rp["elapsed_s"], "unit": UNIT,
+                 "sample": f"first {Tp} steps of the schedule, {R} replicas, one launch per step",
+                 "speedup_of_value": value / (world * R * Tp * N / rp["elapsed_s"])}
+
     # roofline of the step kernel: nominal bytes per replica-step = one fp32 column of W
     # (4N) plus the replica state (fields 4N + state bits N/8)
     peaks, peak_src = load_peaks()
@@ -308,6 +321,7 @@ def main():
         "step_kernel": {"launches": launches, "avg_launch_ms": avg_launch_s * 1e3,
                         "share_of_step": (step_ms / 1e3) / (t_step * args.steps)},
         "tts99": tts,
+        "plain_gpu": plain,
         "max_fp32_drift": float(drift.max()),
     }
     if clk:

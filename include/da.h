@@ -160,6 +160,39 @@ da_status da_anneal_async(da_ctx* ctx, const float* beta_schedule_dev, int64_t s
                           int32_t replicas, uint64_t seed, int64_t recompute_every,
                           const da_dev_result* out, void* stream);
 
+/* The plain GPU form of the same anneal, kept as the baseline the library's
+ * kernels are measured against: one kernel launch per DA step (Algorithm 2),
+ * one thread block per replica, one thread per variable, fp32 fields and
+ * state in global memory between launches, no field recompute.  It draws the
+ * same random numbers, so its trajectories equal da_anneal's with
+ * recompute_every = 0.  N <= 1024.  Same arguments and results as da_anneal.
+ * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+da_status da_anneal_plain(da_ctx* ctx, const float* beta_schedule, int64_t steps, float offset_inc,
+                          int32_t replicas, uint64_t seed, da_result* out);
+
+/* One instance's share of a batched launch (see da_batch_anneal). */
+typedef struct da_batch_item {
+    da_ctx* ctx;                /* the instance (N <= 1024) */
+    const float* beta;          /* host, [steps] schedule */
+    int64_t steps;
+    float offset_inc;
+    int32_t replicas;
+    uint64_t seed;
+    int64_t recompute_every;    /* DA_FP32 only, 0 = never */
+    da_result* out;             /* host results, as for da_anneal (may be NULL) */
+} da_batch_item;
+
+/* Anneal many instances of different sizes and coupling types together: every
+ * replica of every item is one work unit, and warps of one persistent kernel per
+ * (coupling type, size class) pull units from a device queue until none are left;
+ * all launches and the exact final evaluation form one CUDA graph.  Each item's
+ * results are identical to da_anneal on that item alone (the random numbers are
+ * keyed by the item's seed and replica index).  The block shape of each class's
+ * kernel is chosen by an autotuner that times short probes of the class's own
+ * units once per process and device.  *elapsed_s receives the device time of the
+ * graph.  Errors: DA_EINVAL (bad item, N > 1024), DA_ENOMEM, DA_ECUDA. */
+da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s);
+
 /* Parallel tempering with the DA step (PTDA, Sec. II and Algorithm 4): L
  * independent ladders of K replicas at inverse temperatures betas[0..K-1]
  * (host, ascending), replica k starting at index k from x = 0.  A sweep is N DA

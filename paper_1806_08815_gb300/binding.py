@@ -42,6 +42,12 @@ class da_dev_result(ctypes.Structure):
                 ("max_drift", _P), ("flips", _P), ("trace", _P)]
 
 
+class da_batch_item(ctypes.Structure):
+    _fields_ = [("ctx", _P), ("beta", _P), ("steps", ctypes.c_int64), ("offset_inc", ctypes.c_float),
+                ("replicas", ctypes.c_int32), ("seed", ctypes.c_uint64), ("recompute_every", ctypes.c_int64),
+                ("out", ctypes.POINTER(da_result))]
+
+
 class da_pt_result(ctypes.Structure):
     _fields_ = [("final_E", _P), ("best_E", _P), ("best_x", _P), ("temp_of", _P),
                 ("swaps", _P), ("swap_trace", _P), ("elapsed_s", ctypes.c_double)]
@@ -78,6 +84,10 @@ def lib() -> ctypes.CDLL:
     L.da_profile_read.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.da_profile_enable.restype = ctypes.c_int
     L.da_profile_read.restype = ctypes.c_int
+    L.da_batch_anneal.argtypes = [ctypes.POINTER(da_batch_item), i32, ctypes.POINTER(ctypes.c_double)]
+    L.da_batch_anneal.restype = ctypes.c_int
+    L.da_anneal_plain.argtypes = [_P, _P, i64, f32, i32, u64, ctypes.POINTER(da_result)]
+    L.da_anneal_plain.restype = ctypes.c_int
     L.da_anneal_static.argtypes = [_P, _P, i64, i64, _P, i64, f32, i32, u64, ctypes.POINTER(da_dev_result), _P]
     L.da_anneal_static.restype = ctypes.c_int
     L.da_static_pitch.argtypes = [i64]
@@ -163,6 +173,23 @@ def da_anneal(ctx: Context, beta: np.ndarray, offset_inc: float, replicas: int, 
                                                   "flips", "trace")), 0.0)
     _check(lib().da_anneal(ctx.handle, _ptr(b), T, float(offset_inc), R, int(seed) & (2 ** 64 - 1),
                            int(recompute_every), ctypes.byref(res)))
+    out["elapsed_s"] = res.elapsed_s
+    return out
+
+
+def da_anneal_plain(ctx: Context, beta: np.ndarray, offset_inc: float, replicas: int, seed: int,
+                    trace: bool = False) -> dict:
+    """The plain one-launch-per-step baseline form (see da_anneal_plain in include/da.h)."""
+    b = np.ascontiguousarray(beta, dtype=np.float32)
+    R, T, W = int(replicas), b.size, da_words(ctx.N)
+    out = dict(final_E=np.zeros(R), best_E=np.zeros(R), final_x=np.zeros((R, W), np.uint32),
+               best_x=np.zeros((R, W), np.uint32), max_drift=np.zeros(R), flips=np.zeros(R, np.int64))
+    if trace:
+        out["trace"] = np.zeros((R, T), np.int32)
+    res = da_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                  "flips", "trace")), 0.0)
+    _check(lib().da_anneal_plain(ctx.handle, _ptr(b), T, float(offset_inc), R, int(seed) & (2 ** 64 - 1),
+                                 ctypes.byref(res)))
     out["elapsed_s"] = res.elapsed_s
     return out
 
@@ -266,3 +293,30 @@ def da_anneal_static(W_dev, diag_dev, N: int, ldw: int, beta_dev, steps: int, of
     _check(lib().da_anneal_static(_ptr(W_dev), _ptr(diag_dev), int(N), int(ldw), _ptr(beta_dev), int(steps),
                                   float(offset_inc), int(replicas), int(seed) & (2 ** 64 - 1), ctypes.byref(res),
                                   _P(int(handle) if handle else 0)))
+
+
+def da_batch_anneal(jobs: list) -> tuple:
+    """jobs: dicts with ctx, beta, offset_inc, replicas, seed, recompute_every (optional), trace
+    (optional).  Returns (list of result dicts as from da_anneal, device seconds)."""
+    n = len(jobs)
+    arr = (da_batch_item * n)()
+    keep = []
+    outs = []
+    for i, j in enumerate(jobs):
+        ctx = j["ctx"]
+        b = np.ascontiguousarray(j["beta"], dtype=np.float32)
+        R, T, W = int(j["replicas"]), b.size, da_words(ctx.N)
+        out = dict(final_E=np.zeros(R), best_E=np.zeros(R), final_x=np.zeros((R, W), np.uint32),
+                   best_x=np.zeros((R, W), np.uint32), max_drift=np.zeros(R), flips=np.zeros(R, np.int64))
+        if j.get("trace"):
+            out["trace"] = np.zeros((R, T), np.int32)
+        res = da_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                      "flips", "trace")), 0.0)
+        keep += [b, res]
+        outs.append(out)
+        arr[i] = da_batch_item(ctx.handle, _ptr(b), T, float(j.get("offset_inc", 0.0)), R,
+                               int(j["seed"]) & (2 ** 64 - 1), int(j.get("recompute_every", 0)),
+                               ctypes.pointer(res))
+    el = ctypes.c_double()
+    _check(lib().da_batch_anneal(arr, n, ctypes.byref(el)))
+    return outs, el.value

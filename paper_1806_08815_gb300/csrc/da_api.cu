@@ -267,6 +267,17 @@ struct CtxLock {
 
 }  // namespace
 
+namespace da {
+void set_last_error(const std::string& msg) { g_err = msg; }
+void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S)
+{
+    *W = c->W;
+    *diag = c->diag;
+    *ldw = c->ldw;
+    *S = c->S;
+}
+}  // namespace da
+
 extern "C" {
 
 int da_version(void) { return 100; }
@@ -605,6 +616,63 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     if (E)
         for (int r = 0; r < R; ++r)
             E[r] = is_int8(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
+    return DA_OK;
+}
+
+da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc, int32_t R, uint64_t seed,
+                          da_result* out)
+{
+    g_err.clear();
+    if (da_status s = check_ctx(c)) return s;
+    if (c->N > 1024) return fail(DA_EINVAL, "the plain form supports N <= 1024");
+    if (steps < 0 || (steps > 0 && !beta)) return fail(DA_EINVAL, "bad schedule");
+    if (R < 1) return fail(DA_EINVAL, "replicas < 1");
+    if (steps >= (1ll << 32)) return fail(DA_EINVAL, "steps >= 2^32");
+    if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
+    CtxLock lock(c);
+    cudaStream_t st = c->stream;
+    const int nw = (c->N + 31) / 32;
+    const size_t o_ws = 0;
+    const size_t o_words = align_up(da::plain_workspace_bytes(c->N, R), 256);
+    const size_t o_eex = o_words + align_up((size_t)2 * R * nw * 4, 256);
+    const size_t o_part = o_eex + align_up((size_t)2 * R * 8, 256);
+    const size_t o_beta = o_part + align_up((size_t)16 * ((c->N + 63) / 64) * 2 * R, 256);
+    const size_t o_trace = o_beta + align_up((size_t)steps * 4, 256);
+    const bool want_trace = out && out->trace;
+    const size_t total = o_trace + (want_trace ? (size_t)R * steps * 4 : 0);
+    if (da_status e = ensure_ws(c, total)) return e;
+    char* base = static_cast<char*>(c->ws);
+    std::vector<double> tracked((size_t)R);
+    std::vector<int64_t> flips((size_t)R);
+    DA_CU(cudaEventRecord(c->ev0, st));
+    if (steps > 0) DA_CU(cudaMemcpyAsync(base + o_beta, beta, (size_t)steps * 4, cudaMemcpyHostToDevice, st));
+    uint32_t* words = reinterpret_cast<uint32_t*>(base + o_words);
+    long long* eex = reinterpret_cast<long long*>(base + o_eex);
+    DA_CU(da::plain_anneal(c->W, c->diag, is_int8(c), c->N, c->ldw, c->S, reinterpret_cast<const float*>(base + o_beta),
+                           steps, inc, R, seed, base + o_ws, want_trace ? reinterpret_cast<int*>(base + o_trace) : nullptr,
+                           words, eex, reinterpret_cast<long long*>(base + o_part), tracked.data(), flips.data(), st));
+    DA_CU(cudaEventRecord(c->ev1, st));
+    std::vector<long long> e((size_t)2 * R);
+    DA_CU(cudaMemcpyAsync(e.data(), eex, e.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (out && out->final_x)
+        DA_CU(cudaMemcpyAsync(out->final_x, words, (size_t)R * nw * 4, cudaMemcpyDeviceToHost, st));
+    if (out && out->best_x)
+        DA_CU(cudaMemcpyAsync(out->best_x, words + (size_t)R * nw, (size_t)R * nw * 4, cudaMemcpyDeviceToHost, st));
+    if (want_trace && steps > 0)
+        DA_CU(cudaMemcpyAsync(out->trace, base + o_trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
+    DA_CU(cudaStreamSynchronize(st));
+    if (!out) return DA_OK;
+    float ms = 0.f;
+    DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    out->elapsed_s = ms * 1e-3;
+    for (int r = 0; r < R; ++r) {
+        const double ef = is_int8(c) ? (double)e[r] : reinterpret_cast<const double*>(e.data())[r];
+        const double eb = is_int8(c) ? (double)e[R + r] : reinterpret_cast<const double*>(e.data())[R + r];
+        if (out->final_E) out->final_E[r] = ef;
+        if (out->best_E) out->best_E[r] = eb;
+        if (out->max_drift) out->max_drift[r] = std::fabs(tracked[r] - ef);
+        if (out->flips) out->flips[r] = flips[r];
+    }
     return DA_OK;
 }
 

@@ -1,0 +1,459 @@
+// da_batch.cu -- many instances of different sizes and coupling types annealed
+// by one persistent launch per size class, captured in one CUDA graph.
+//
+// A work unit is one replica of one instance, run for all of its steps by one
+// warp with its state in registers (WarpReplica): warps pull units from a
+// device counter until none are left, so short and long instances share the
+// GPU without a wave per instance.  fp32 units recompute their fields exactly
+// inside the warp every `recompute_every` steps.  Units are grouped by
+// (coupling type, V = variables per lane); each group is one persistent kernel
+// whose block shape is chosen by a small autotuner that times short probes of
+// the real work and caches the winner per device and class.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "da.h"
+#include "da_internal.h"
+#include "da_replica.cuh"
+
+namespace da {
+
+struct BatchItemDev {
+    const void* W;
+    const void* diag;
+    const float* beta;
+    uint32_t* xs;         // [2R][nw]: final states, then best states
+    ReplicaScalars* sc;   // [R]
+    int* trace;           // [R][T] or null
+    long long T;
+    long long recompute_every;
+    long long unit0;      // first unit of this item in its class
+    uint64_t seed;
+    int N, ldw, S, R;
+    float inc;
+    int pad;
+};
+
+struct BatchClassParams {
+    const BatchItemDev* items;
+    int n_items;
+    long long total_units;
+    unsigned long long* head;   // work counter
+    long long t_limit;          // > 0: run only this many steps per unit (autotuner probes)
+};
+
+namespace {
+
+using step_detail::WarpReplica;
+
+template <typename Tw, int V>
+__global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ BatchClassParams bp)
+{
+    using R_ = WarpReplica<Tw, V>;
+    using A = step_detail::Arith<Tw>;
+    using H = typename R_::H;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long unit = 0;
+        if (lane == 0) unit = atomicAdd(bp.head, 1ull);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= (unsigned long long)bp.total_units) break;
+        // the item holding this unit (items sorted by unit0)
+        int lo = 0, hi = bp.n_items - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned long long)bp.items[mid].unit0 <= unit) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItemDev it = bp.items[lo];
+        const int r = (int)(unit - (unsigned long long)it.unit0);
+        constexpr int nw = V;   // state words per replica (the padded width 32V / 32)
+        R_ rp;
+        rp.init(static_cast<const Tw*>(it.W), it.N, it.ldw, (uint32_t)r, it.xs + ((size_t)it.R + r) * nw);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            rp.h[v] = ((rp.valid >> v) & 1u) ? static_cast<const H*>(it.diag)[rp.base + v] : H(0);
+        rp.xm = 0;
+        rp.m = 0;
+        rp.Ecur = 0;
+        rp.Ebest = 0;
+        rp.flips = 0;
+        const PhiloxKeys keys(it.seed);
+        const long long T = bp.t_limit > 0 ? std::min(bp.t_limit, it.T) : it.T;
+        if (T > 0) rp.draw(0u, keys);
+        float beta_next = T > 0 ? it.beta[0] : 0.f;
+        for (long long t = 0; t < T; ++t) {
+            const float beta = beta_next;
+            if (t + 1 < T) beta_next = it.beta[t + 1];
+            const int k = rp.template step<false>(t, t + 1 < T, beta, it.inc, keys);
+            if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
+            if constexpr (sizeof(Tw) == 4) {
+                if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
+                    rp.recompute(static_cast<const float*>(it.diag), it.S);
+                    if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
+                }
+            }
+        }
+        const uint32_t word = rp.word();
+        if (lane % R_::P == 0) it.xs[(size_t)r * nw + (rp.base >> 5)] = word;
+        if (lane == 0) {
+            ReplicaScalars s;
+            s.E = A::store_e(rp.Ecur);
+            s.best = A::store_e(rp.Ebest);
+            s.flips = rp.flips;
+            s.m = rp.m;
+            s.pad = 0;
+            it.sc[r] = s;
+        }
+    }
+}
+
+typedef void (*BatchKernel)(BatchClassParams);
+
+BatchKernel kernel_for(bool int8, int V)
+{
+    if (int8) {
+        switch (V) {
+        case 4: return batch_kernel<int8_t, 4>;
+        case 8: return batch_kernel<int8_t, 8>;
+        case 16: return batch_kernel<int8_t, 16>;
+        case 32: return batch_kernel<int8_t, 32>;
+        }
+    } else {
+        switch (V) {
+        case 4: return batch_kernel<float, 4>;
+        case 8: return batch_kernel<float, 8>;
+        case 16: return batch_kernel<float, 16>;
+        case 32: return batch_kernel<float, 32>;
+        }
+    }
+    return nullptr;
+}
+
+__global__ void batch_finalize_kernel(bool int8, int R, const ReplicaScalars* sc, const long long* eex,
+                                      double* out /* [4][R] */)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const double ef = int8 ? (double)eex[r] : __longlong_as_double(eex[r]);
+    const double eb = int8 ? (double)eex[R + r] : __longlong_as_double(eex[R + r]);
+    const double tr = int8 ? (double)sc[r].E : __longlong_as_double(sc[r].E);
+    out[r] = ef;
+    out[R + r] = eb;
+    out[2 * R + r] = fabs(tr - ef);
+    reinterpret_cast<long long*>(out)[3 * R + r] = sc[r].flips;
+}
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+// Autotuner: warps per block of the persistent kernel of one class, chosen by
+// timing probes of the class's own first units; cached per (device, class).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, bool, int>, int> g_tune_cache;
+
+int blocks_for(BatchKernel k, int warps_per_block, int sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(k), warps_per_block * 32, 0) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * sms;
+}
+
+}  // namespace
+
+// Host side of one class: items already laid out in device memory.
+struct BatchClass {
+    bool int8;
+    int V;
+    std::vector<int> item_idx;   // indices into the caller's item array
+    BatchItemDev* items_dev;
+    int n_items;
+    long long units;
+    unsigned long long* head;
+    int warps_per_block;
+};
+
+int tune_class(BatchClass& c, int dev, int sms, cudaStream_t st)
+{
+    const auto key = std::make_tuple(dev, c.int8, c.V);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto f = g_tune_cache.find(key);
+        if (f != g_tune_cache.end()) return f->second;
+    }
+    BatchKernel k = kernel_for(c.int8, c.V);
+    int best = 4;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
+    for (int wpb : {1, 2, 4}) {
+        BatchClassParams bp{c.items_dev, c.n_items, std::min<long long>(c.units, (long long)sms * 16), c.head, 256};
+        cudaMemsetAsync(c.head, 0, 8, st);
+        cudaEventRecord(e0, st);
+        k<<<blocks_for(k, wpb, sms), wpb * 32, 0, st>>>(bp);
+        cudaEventRecord(e1, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = wpb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    return best;
+}
+
+}  // namespace da
+
+using da::BatchClass;
+using da::BatchItemDev;
+
+
+namespace {
+da_status bfail(da_status s, const std::string& m)
+{
+    da::set_last_error(m);
+    return s;
+}
+}  // namespace
+
+extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s)
+{
+    da::set_last_error("");
+    if (!items || n < 1) return bfail(DA_EINVAL, "need items");
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bfail(DA_ECUDA, "no device");
+    struct Host {
+        const void* W;
+        const void* diag;
+        int N, ldw, S;
+        bool int8;
+        int V;
+    };
+    std::vector<Host> hi((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const da_batch_item& it = items[i];
+        int64_t N = 0;
+        da_dtype dt;
+        if (!it.ctx || da_ctx_info(it.ctx, &N, &dt) != DA_OK) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad context");
+        if (N > 1024) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes N <= 1024");
+        if (it.replicas < 1 || it.steps < 0 || it.steps >= (1ll << 32) || (it.steps > 0 && !it.beta))
+            return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad replicas/steps/schedule");
+        if (!(it.offset_inc >= 0.f) || !std::isfinite(it.offset_inc) || it.recompute_every < 0)
+            return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad offset or recompute period");
+        Host h{};
+        int32_t ldw = 0, S = 0;
+        da::ctx_device_view(it.ctx, &h.W, &h.diag, &ldw, &S);
+        h.N = (int)N;
+        h.ldw = ldw;
+        h.S = S;
+        h.int8 = dt == DA_INT8;
+        int V = 4;
+        while (32 * V < h.N) V *= 2;
+        h.V = V;
+        hi[i] = h;
+    }
+    // device layout: per item betas, states, scalars, traces, results; per class descriptors
+    std::vector<size_t> o_beta(n), o_xs(n), o_sc(n), o_tr(n), o_eex(n), o_part(n), o_res(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const int R = items[i].replicas, nw = hi[i].V;
+        o_beta[i] = off; off += da::al((size_t)items[i].steps * 4);
+        o_xs[i] = off; off += da::al((size_t)2 * R * nw * 4);
+        o_sc[i] = off; off += da::al((size_t)R * sizeof(da::ReplicaScalars));
+        o_tr[i] = off; off += items[i].out && items[i].out->trace ? da::al((size_t)R * items[i].steps * 4) : 0;
+        o_eex[i] = off; off += da::al((size_t)2 * R * 8);
+        o_part[i] = off; off += da::al((size_t)16 * ((hi[i].N + 63) / 64) * 2 * R);
+        o_res[i] = off; off += da::al((size_t)4 * R * 8);
+    }
+    std::map<std::pair<bool, int>, BatchClass> classes;
+    for (int i = 0; i < n; ++i) {
+        auto& c = classes[{hi[i].int8, hi[i].V}];
+        c.int8 = hi[i].int8;
+        c.V = hi[i].V;
+        c.item_idx.push_back(i);
+    }
+    const size_t o_desc = off;
+    off += da::al((size_t)n * sizeof(BatchItemDev));
+    const size_t o_heads = off;
+    off += da::al(classes.size() * 8);
+    char* base = nullptr;
+    if (cudaMalloc(&base, off) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(DA_ENOMEM, "batch workspace of " + std::to_string(off) + " bytes");
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    da_status status = DA_OK;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+        cudaFree(base);
+    };
+#define DA_B(call)                                                                         \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            status = bfail(DA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+            cudaGetLastError();                                                            \
+            cleanup();                                                                     \
+            return status;                                                                 \
+        }                                                                                  \
+    } while (0)
+    DA_B(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    DA_B(cudaEventCreate(&e0));
+    DA_B(cudaEventCreate(&e1));
+    std::vector<BatchItemDev> desc((size_t)n);
+    {
+        size_t di = 0;
+        int ci = 0;
+        for (auto& kv : classes) {
+            BatchClass& c = kv.second;
+            long long units = 0;
+            c.items_dev = reinterpret_cast<BatchItemDev*>(base + o_desc) + di;
+            c.n_items = (int)c.item_idx.size();
+            c.head = reinterpret_cast<unsigned long long*>(base + o_heads) + ci;
+            for (int i : c.item_idx) {
+                const da_batch_item& it = items[i];
+                BatchItemDev d{};
+                d.W = hi[i].W;
+                d.diag = hi[i].diag;
+                d.beta = reinterpret_cast<const float*>(base + o_beta[i]);
+                d.xs = reinterpret_cast<uint32_t*>(base + o_xs[i]);
+                d.sc = reinterpret_cast<da::ReplicaScalars*>(base + o_sc[i]);
+                d.trace = it.out && it.out->trace ? reinterpret_cast<int*>(base + o_tr[i]) : nullptr;
+                d.T = it.steps;
+                d.recompute_every = hi[i].int8 ? 0 : it.recompute_every;
+                d.unit0 = units;
+                d.seed = it.seed;
+                d.N = hi[i].N;
+                d.ldw = hi[i].ldw;
+                d.S = hi[i].S;
+                d.R = it.replicas;
+                d.inc = it.offset_inc;
+                desc[di++] = d;
+                units += it.replicas;
+            }
+            c.units = units;
+            ++ci;
+        }
+    }
+    // uploads (outside the graph: the schedules and descriptors)
+    for (int i = 0; i < n; ++i)
+        if (items[i].steps > 0)
+            DA_B(cudaMemcpyAsync(base + o_beta[i], items[i].beta, (size_t)items[i].steps * 4, cudaMemcpyHostToDevice, st));
+    {
+        // descriptors in class order
+        size_t di = 0;
+        std::vector<BatchItemDev> ordered((size_t)n);
+        for (auto& kv : classes)
+            for (size_t q = 0; q < kv.second.item_idx.size(); ++q) ordered[di] = desc[di], ++di;
+        DA_B(cudaMemcpyAsync(base + o_desc, ordered.data(), (size_t)n * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st));
+    }
+    for (int i = 0; i < n; ++i)
+        DA_B(cudaMemsetAsync(base + o_xs[i], 0, (size_t)2 * items[i].replicas * hi[i].V * 4, st));
+    DA_B(cudaStreamSynchronize(st));
+    for (auto& kv : classes) kv.second.warps_per_block = da::tune_class(kv.second, dev, sms, st);
+    for (int i = 0; i < n; ++i)
+        DA_B(cudaMemsetAsync(base + o_xs[i], 0, (size_t)2 * items[i].replicas * hi[i].V * 4, st));
+    DA_B(cudaStreamSynchronize(st));
+
+    // the graph: persistent kernel per class, then the exact evaluation of every item
+    DA_B(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    bool capture_ok = true;
+    DA_B(cudaMemsetAsync(base + o_heads, 0, classes.size() * 8, st));
+    for (auto& kv : classes) {
+        BatchClass& c = kv.second;
+        da::BatchKernel k = da::kernel_for(c.int8, c.V);
+        da::BatchClassParams bp{c.items_dev, c.n_items, c.units, c.head, 0};
+        k<<<da::blocks_for(k, c.warps_per_block, sms), c.warps_per_block * 32, 0, st>>>(bp);
+        if (cudaGetLastError() != cudaSuccess) capture_ok = false;
+    }
+    for (auto& kv : classes) {
+        for (int i : kv.second.item_idx) {
+            const int R = items[i].replicas, nw = hi[i].V;
+            long long* eex = reinterpret_cast<long long*>(base + o_eex[i]);
+            if (da::launch_recompute(hi[i].int8, hi[i].W, hi[i].diag, hi[i].N, hi[i].ldw, hi[i].S,
+                                     reinterpret_cast<uint32_t*>(base + o_xs[i]), nw, 2 * R, nullptr, hi[i].N, eex, 1, st,
+                                     reinterpret_cast<long long*>(base + o_part[i])) != cudaSuccess)
+                capture_ok = false;
+            da::batch_finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(
+                hi[i].int8, R, reinterpret_cast<da::ReplicaScalars*>(base + o_sc[i]), eex,
+                reinterpret_cast<double*>(base + o_res[i]));
+        }
+    }
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (ce != cudaSuccess || !capture_ok) {
+        status = bfail(DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        cudaGetLastError();
+        cleanup();
+        return status;
+    }
+    DA_B(cudaGraphInstantiate(&exec, graph, 0));
+    DA_B(cudaEventRecord(e0, st));
+    DA_B(cudaGraphLaunch(exec, st));
+    DA_B(cudaEventRecord(e1, st));
+    // results
+    for (int i = 0; i < n; ++i) {
+        da_result* out = items[i].out;
+        if (!out) continue;
+        const int R = items[i].replicas, nw = hi[i].V;
+        const size_t words = (size_t)(hi[i].N + 31) / 32;
+        if (out->final_x)
+            DA_B(cudaMemcpy2DAsync(out->final_x, words * 4, base + o_xs[i], (size_t)nw * 4, words * 4, R,
+                                   cudaMemcpyDeviceToHost, st));
+        if (out->best_x)
+            DA_B(cudaMemcpy2DAsync(out->best_x, words * 4, base + o_xs[i] + (size_t)R * nw * 4, (size_t)nw * 4, words * 4,
+                                   R, cudaMemcpyDeviceToHost, st));
+        if (out->trace && items[i].steps > 0)
+            DA_B(cudaMemcpyAsync(out->trace, base + o_tr[i], (size_t)R * items[i].steps * 4, cudaMemcpyDeviceToHost, st));
+    }
+    std::vector<std::vector<double>> res((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        res[i].resize((size_t)4 * items[i].replicas);
+        DA_B(cudaMemcpyAsync(res[i].data(), base + o_res[i], res[i].size() * 8, cudaMemcpyDeviceToHost, st));
+    }
+    DA_B(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    DA_B(cudaEventElapsedTime(&ms, e0, e1));
+    if (elapsed_s) *elapsed_s = ms * 1e-3;
+    for (int i = 0; i < n; ++i) {
+        da_result* out = items[i].out;
+        if (!out) continue;
+        const int R = items[i].replicas;
+        for (int r = 0; r < R; ++r) {
+            if (out->final_E) out->final_E[r] = res[i][r];
+            if (out->best_E) out->best_E[r] = res[i][R + r];
+            if (out->max_drift) out->max_drift[r] = res[i][2 * R + r];
+            if (out->flips) out->flips[r] = reinterpret_cast<const int64_t*>(res[i].data())[3 * R + r];
+        }
+        out->elapsed_s = ms * 1e-3;
+    }
+    cleanup();
+    return DA_OK;
+#undef DA_B
+}

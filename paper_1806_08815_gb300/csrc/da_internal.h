@@ -4,6 +4,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <string>
+
+struct da_ctx;
+
 namespace da {
 
 // Per-replica scalars kept in global memory between kernel launches.
@@ -88,6 +92,22 @@ cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                const ReplicaScalars* sc, int* temp_of, int* rep_at,
                                long long* swaps, uint8_t* swap_trace, long long sweep, long long sweeps,
                                uint64_t seed, cudaStream_t st);
+
+// The plain one-launch-per-step form of the DA step (da_plain.cu), N <= 1024:
+// ws holds plain_workspace_bytes(N, R); words_out [2R][ceil(N/32)] receives the
+// final and best states, eex [2R] their exact energies (part: recompute
+// scratch), tracked_E / flips [R] (host) the tracked energies and flip counts.
+cudaError_t plain_anneal(const void* W, const void* diag, bool int8, int N, int ldw, int S, const float* beta_dev,
+                         long long T, float inc, int R, uint64_t seed, void* ws, int* trace, uint32_t* words_out,
+                         long long* eex, long long* part, double* tracked_E, int64_t* flips, cudaStream_t st);
+size_t plain_workspace_bytes(int N, int R);
+
+// Error text returned by da_last_error() on the calling thread (da_api.cu).
+void set_last_error(const std::string& msg);
+
+// Device copies of a context's instance: W (row pitch ldw), diag, and the
+// fixed-point scale S of its fp32 recompute (da_api.cu).
+void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S);
 
 // Fixed-point scale of the fp32 recompute for amax = max(|W_ij|, |diag_i|)
 // and N variables (N + 1 terms per sum).

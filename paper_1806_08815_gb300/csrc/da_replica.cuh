@@ -1,0 +1,201 @@
+// da_replica.cuh -- one replica annealed by one warp (the G = 1 form of the
+// step in da_step.cuh), packaged so that the chunked step kernel and the
+// persistent batched kernel share it.
+//
+// Lane l owns the V consecutive variables i = l*V + v of the replica and keeps
+// their effective fields g_i, bits x_i and the Philox words of the current step
+// in registers.  step() performs one step of Algorithm 2 (see da_step.cuh for
+// the decomposition); recompute() replaces the fp32 fields and the tracked
+// energy by their exact fixed-point values (the same definition as the tiled
+// recompute in da_fields.cu, evaluated by the warp itself).
+#pragma once
+#include "da_device.cuh"
+#include "da_internal.h"
+#include "da_step_common.cuh"
+
+namespace da {
+namespace step_detail {
+
+template <typename Tw, int V>
+struct WarpReplica {
+    using A = Arith<Tw>;
+    using H = typename A::H;
+    using E = typename A::E;
+    static_assert(V % 4 == 0 && V <= 32, "V must be 4, 8, 16 or 32");
+    static constexpr int NQ = V / 4;
+    static constexpr uint32_t VMASK = V == 32 ? 0xffffffffu : ((1u << V) - 1u);
+    static constexpr int P = 32 / V;
+
+    H h[V];
+    u32x4 rr[NQ];
+    u32x4 cr;
+    long long cr_blk;
+    uint32_t xm, valid, m;
+    E Ecur, Ebest;
+    long long flips;
+    int lane, base, N, ldw;
+    uint32_t rep;
+    const Tw* __restrict__ W;
+    uint32_t* bestg;  // best-state words of this replica
+
+    __device__ __forceinline__ void init(const Tw* W_, int N_, int ldw_, uint32_t rep_, uint32_t* bestg_)
+    {
+        lane = threadIdx.x & 31;
+        base = lane * V;
+        N = N_;
+        ldw = ldw_;
+        rep = rep_;
+        W = W_;
+        bestg = bestg_;
+        valid = base >= N ? 0u : (N - base >= V ? VMASK : ((1u << (N - base)) - 1u));
+        cr = {0, 0, 0, 0};
+        cr_blk = -1;
+    }
+
+    __device__ __forceinline__ uint32_t word() const { return gather_word<V>(xm, lane); }
+
+    __device__ __forceinline__ void snapshot()
+    {
+        const uint32_t wv = word();
+        if (lane % P == 0) bestg[base >> 5] = wv;
+    }
+
+    template <class Keys>
+    __device__ __forceinline__ void draw(uint32_t tt, const Keys& keys)
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) rr[q] = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+    }
+
+    // One step t (the draws of t are in rr).  If draw_next, the draws of t + 1
+    // are computed while row k is in flight.  Returns the flipped index or -1.
+    template <bool FULL, class Keys>
+    __device__ __forceinline__ int step(long long t, bool draw_next, float beta, float inc, const Keys& keys)
+    {
+        const float Eoff = __fmul_rn(__uint2float_rn(m), inc);
+        uint32_t accm = 0, band = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const H dE = A::signed_field(h[v], (xm >> v) & 1u);
+            const float delta = A::delta(dE, Eoff);
+            const float ax = -__fmul_rn(beta, delta);
+            const uint32_t wd = pick(rr[v >> 2], v & 3);
+            const float est = exp_estimate(ax);
+            const float U = __uint2float_rn((wd >> 8) + 1u);
+            const bool le0 = delta <= 0.0f;
+            const bool need = !le0 && ax > kExpCut;
+            const bool sure = U < __fmul_rn(est, kBandLo);
+            const bool maybe = U < __fmul_rn(est, kBandHi);
+            accm |= (uint32_t)(le0 || (need && sure)) << v;
+            band |= (uint32_t)(need && !sure && maybe) << v;
+        }
+        if (__any_sync(0xffffffffu, band != 0u)) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if ((band >> v) & 1u) {
+                    const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
+                    const float ax = -__fmul_rn(beta, delta);
+                    accm |= (uint32_t)(uniform01(pick(rr[v >> 2], v & 3)) < exp_neg(ax)) << v;
+                }
+            }
+        }
+        if constexpr (!FULL) accm &= valid;
+
+        const int cnt = __popc(accm);
+        const int incl = warp_inclusive_scan(cnt, lane);
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) {
+            m += 1;
+            if (draw_next) draw((uint32_t)(t + 1), keys);
+            return -1;
+        }
+        const long long blk = t >> 2;
+        if (blk != cr_blk) {
+            cr = philox4x32_10(0u, (uint32_t)(t & ~3ll), rep, 1u, keys);
+            cr_blk = blk;
+        }
+        const int j = (int)__umulhi(pick(cr, (int)(t & 3)), (uint32_t)total);
+        const int excl = incl - cnt;
+        const int own = __ffs(__ballot_sync(0xffffffffu, j >= excl && j < incl)) - 1;
+        const int vk = __shfl_sync(0xffffffffu, nth_set_bit(accm, j - excl), own);
+        const uint32_t xold = (__shfl_sync(0xffffffffu, xm, own) >> vk) & 1u;
+        H gk = h[0];
+#pragma unroll
+        for (int v = 1; v < V; ++v)
+            if (v == vk) gk = h[v];
+        const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
+        const int k = own * V + vk;
+        Tw cv[V];
+        if (FULL || base < N) Row<Tw, V>::load(W + (size_t)k * ldw + base, cv);
+        if (draw_next) draw((uint32_t)(t + 1), keys);
+        if (FULL || base < N) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) h[v] = A::apply(h[v], cv[v], xold != 0u);
+        }
+        if (lane == own) xm ^= 1u << vk;
+        ++flips;
+        m = 0;
+        Ecur = A::book(Ecur, dEk);
+        if (Ecur < Ebest) {
+            Ebest = Ecur;
+            snapshot();
+        }
+        return k;
+    }
+
+    // Exact fixed-point recompute of the fp32 fields and of the tracked
+    // energy (same definition as da_fields.cu): g_i = fl32(2^-S (round(d_i 2^S)
+    // + sum_{x_j = 1} round(W_ij 2^S))), E = fl64(2^-(S+1) sum_{x_i = 1}
+    // (round(d_i 2^S) + sum_i)).
+    __device__ __forceinline__ void recompute(const float* __restrict__ diag, int S)
+    {
+        static_assert(sizeof(Tw) == 4, "only the fp32 fields are recomputed");
+        long long acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            acc[v] = ((valid >> v) & 1u) ? __float2ll_rn(ldexpf(diag[base + v], S)) : 0ll;
+        const uint32_t myword = word();
+        const int nw = (N + 31) >> 5;
+        for (int wi = 0; wi < nw; ++wi) {
+            uint32_t wbits = __shfl_sync(0xffffffffu, myword, wi * P);
+            while (wbits) {
+                const int b = __ffs(wbits) - 1;
+                wbits &= wbits - 1;
+                const int j = wi * 32 + b;
+                if (base < N) {
+                    Tw cv[V];
+                    Row<Tw, V>::load(W + (size_t)j * ldw + base, cv);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] += __float2ll_rn(ldexpf(cv[v], S));
+                }
+            }
+        }
+        // energy: sum over x_i = 1 of (round(d_i 2^S) + acc_i), exact in 128 bits
+        unsigned long long lo = 0;
+        long long hi = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (((valid & xm) >> v) & 1u) {
+                const long long t = __float2ll_rn(ldexpf(diag[base + v], S)) + acc[v];
+                const unsigned long long nlo = lo + (unsigned long long)t;
+                hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
+                lo = nlo;
+            }
+            if ((valid >> v) & 1u) h[v] = ldexpf(__ll2float_rn(acc[v]), -S);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, o);
+            const long long ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+            const unsigned long long nlo = lo + olo;
+            hi = hi + ohi + (nlo < lo ? 1ll : 0ll);
+            lo = nlo;
+        }
+        const long long top = (long long)((unsigned long long)hi << 32 | (lo >> 32));
+        const double v = __fma_rn((double)top, 4294967296.0, (double)(uint32_t)(lo & 0xFFFFFFFFull));
+        Ecur = ldexp(v, -(S + 1));
+    }
+};
+
+}  // namespace step_detail
+}  // namespace da

@@ -29,119 +29,11 @@
 #pragma once
 #include "da_device.cuh"
 #include "da_internal.h"
+#include "da_replica.cuh"
+#include "da_step_common.cuh"
 
 namespace da {
 namespace step_detail {
-
-template <typename Tw> struct Arith;
-template <> struct Arith<int8_t> {
-    using H = int32_t;    // effective fields
-    using E = long long;  // tracked energy
-    static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
-    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
-    static __device__ __forceinline__ H apply(H h, int8_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
-    static __device__ __forceinline__ E load_e(long long b) { return b; }
-    static __device__ __forceinline__ long long store_e(E e) { return e; }
-    static __device__ __forceinline__ E book(E e, H dE) { return e + (E)dE; }
-};
-template <> struct Arith<float> {
-    using H = float;
-    using E = double;
-    static __device__ __forceinline__ H signed_field(H g, uint32_t x)
-    {
-        return __int_as_float(__float_as_int(g) ^ (int)(x << 31));
-    }
-    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
-    static __device__ __forceinline__ H apply(H h, float w, bool minus) { return minus ? __fsub_rn(h, w) : __fadd_rn(h, w); }
-    static __device__ __forceinline__ E load_e(long long b) { return __longlong_as_double(b); }
-    static __device__ __forceinline__ long long store_e(E e) { return __double_as_longlong(e); }
-    static __device__ __forceinline__ E book(E e, H dE) { return __dadd_rn(e, (double)dE); }
-};
-
-__device__ __forceinline__ int warp_inclusive_scan(int v, int lane)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    return v;
-}
-
-// Position of the r-th (0-based) set bit of w; requires r < popc(w).
-__device__ __forceinline__ int nth_set_bit(uint32_t w, int r)
-{
-    int pos = 0, c;
-    c = __popc(w & 0xFFFFu); if (r >= c) { r -= c; pos += 16; w >>= 16; }
-    c = __popc(w & 0xFFu);   if (r >= c) { r -= c; pos += 8;  w >>= 8; }
-    c = __popc(w & 0xFu);    if (r >= c) { r -= c; pos += 4;  w >>= 4; }
-    c = __popc(w & 0x3u);    if (r >= c) { r -= c; pos += 2;  w >>= 2; }
-    c = (int)(w & 1u);       if (r >= c) { pos += 1; }
-    return pos;
-}
-
-__device__ __forceinline__ void group_barrier(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Row k of W at the V consecutive entries of this lane (16-byte loads where
-// the lane's slice allows).
-template <typename Tw, int V> struct Row;
-template <int V> struct Row<float, V> {
-    static __device__ __forceinline__ void load(const float* p, float (&c)[V])
-    {
-        static_assert(V % 4 == 0, "V");
-#pragma unroll
-        for (int q = 0; q < V / 4; ++q) {
-            const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
-            c[4 * q] = f.x; c[4 * q + 1] = f.y; c[4 * q + 2] = f.z; c[4 * q + 3] = f.w;
-        }
-    }
-};
-template <int V> struct Row<int8_t, V> {
-    static __device__ __forceinline__ void unpack(uint32_t u, int8_t* c)
-    {
-        c[0] = (int8_t)(u & 0xFFu); c[1] = (int8_t)((u >> 8) & 0xFFu);
-        c[2] = (int8_t)((u >> 16) & 0xFFu); c[3] = (int8_t)(u >> 24);
-    }
-    static __device__ __forceinline__ void load(const int8_t* p, int8_t (&c)[V])
-    {
-        if constexpr (V == 4) {
-            unpack(__ldg(reinterpret_cast<const unsigned int*>(p)), c);
-        } else if constexpr (V == 8) {
-            const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-            unpack(u.x, c); unpack(u.y, c + 4);
-        } else {
-#pragma unroll
-            for (int q = 0; q < V / 16; ++q) {
-                const uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + q);
-                unpack(u.x, c + 16 * q); unpack(u.y, c + 16 * q + 4);
-                unpack(u.z, c + 16 * q + 8); unpack(u.w, c + 16 * q + 12);
-            }
-        }
-    }
-};
-
-// Replicas per block and the blocks per SM the register budget is sized for:
-// at least 7 replicas per SM, so that 1024 replicas fill 152 SMs in one wave.
-template <int G> struct Occupancy;
-template <> struct Occupancy<1> { static constexpr int rpb = 4, min_blocks = 2; };
-template <> struct Occupancy<2> { static constexpr int rpb = 2, min_blocks = 4; };
-template <> struct Occupancy<4> { static constexpr int rpb = 1, min_blocks = 7; };
-template <> struct Occupancy<8> { static constexpr int rpb = 1, min_blocks = 2; };
-
-// The state words of a replica are standard bit-packed words (x_i is bit i%32
-// of word i/32); a lane's V bits are one slice of word (w*32V + l*V) / 32.
-template <int V>
-__device__ __forceinline__ uint32_t gather_word(uint32_t bits, int lane)
-{
-    constexpr int P = 32 / V;  // lanes per word
-    uint32_t m = (V == 32) ? bits : (bits << ((lane % P) * V));
-#pragma unroll
-    for (int o = 1; o < P; o <<= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
-    return m;
-}
 
 template <typename Tw, int V, int G, bool FULL, bool TRACE>
 __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_blocks)
@@ -368,6 +260,53 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
     }
 }
 
+// G = 1: one warp per replica, the body of WarpReplica.
+template <typename Tw, int V, bool FULL, bool TRACE>
+__global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_blocks)
+    step_kernel_g1(const __grid_constant__ StepParams p)
+{
+    using R_ = WarpReplica<Tw, V>;
+    using H = typename R_::H;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= p.R) return;
+    R_ rp;
+    rp.init(static_cast<const Tw*>(p.W), p.N, p.ldw, p.rep_base + (uint32_t)r, p.bestx + (size_t)r * p.nw);
+    H* hg = static_cast<H*>(p.h) + (size_t)r * p.npad + rp.base;
+    uint32_t* xg = p.x + (size_t)r * p.nw;
+#pragma unroll
+    for (int v = 0; v < V; ++v) rp.h[v] = hg[v];
+    rp.xm = (xg[rp.base >> 5] >> (rp.base & 31)) & R_::VMASK;
+    ReplicaScalars sc = p.sc[r];
+    rp.Ecur = Arith<Tw>::load_e(sc.E);
+    rp.Ebest = Arith<Tw>::load_e(sc.best);
+    rp.flips = sc.flips;
+    rp.m = sc.m;
+    const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
+    const bool per_rep = p.betas != nullptr;
+    const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
+    if (p.t0 < p.t1) rp.draw((uint32_t)p.t0, keys);
+    float beta_next = (!per_rep && p.t0 < p.t1) ? p.beta[p.t0] : beta_rep;
+    for (long long t = p.t0; t < p.t1; ++t) {
+        const float beta = beta_next;
+        if (!per_rep && t + 1 < p.t1) beta_next = p.beta[t + 1];
+        const int k = rp.template step<FULL>(t, t + 1 < p.t1, beta, p.inc, keys);
+        if constexpr (TRACE) {
+            if (rp.lane == 0) p.trace[(size_t)r * p.trace_T + t] = k;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) hg[v] = rp.h[v];
+    const uint32_t word = rp.word();
+    if (rp.lane % R_::P == 0) xg[rp.base >> 5] = word;
+    if (rp.lane == 0) {
+        sc.E = Arith<Tw>::store_e(rp.Ecur);
+        sc.best = Arith<Tw>::store_e(rp.Ebest);
+        sc.flips = rp.flips;
+        sc.m = rp.m;
+        p.sc[r] = sc;
+    }
+}
+
 template <typename Tw, int V, int G>
 cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)
 {
@@ -376,6 +315,16 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
     const size_t shm = G > 1 ? (size_t)s.rpb * (4 * 32 * G + 4) * sizeof(uint32_t) : 0;
     if (blocks == 0) return cudaSuccess;
     const bool full = p.N == 32 * V * G;
+    if constexpr (G == 1) {
+        if (full) {
+            if (trace) step_kernel_g1<Tw, V, true, true><<<blocks, threads, 0, st>>>(p);
+            else step_kernel_g1<Tw, V, true, false><<<blocks, threads, 0, st>>>(p);
+        } else {
+            if (trace) step_kernel_g1<Tw, V, false, true><<<blocks, threads, 0, st>>>(p);
+            else step_kernel_g1<Tw, V, false, false><<<blocks, threads, 0, st>>>(p);
+        }
+        return cudaGetLastError();
+    }
     if (full) {
         if (trace) step_kernel<Tw, V, G, true, true><<<blocks, threads, shm, st>>>(p);
         else step_kernel<Tw, V, G, true, false><<<blocks, threads, shm, st>>>(p);

@@ -1,0 +1,121 @@
+// da_step_common.cuh -- arithmetic and warp helpers shared by the step
+// kernels (da_step.cuh, da_replica.cuh, da_batch.cu).
+#pragma once
+#include "da_device.cuh"
+#include "da_internal.h"
+
+namespace da {
+namespace step_detail {
+
+template <typename Tw> struct Arith;
+template <> struct Arith<int8_t> {
+    using H = int32_t;    // effective fields
+    using E = long long;  // tracked energy
+    static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
+    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
+    static __device__ __forceinline__ H apply(H h, int8_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
+    static __device__ __forceinline__ E load_e(long long b) { return b; }
+    static __device__ __forceinline__ long long store_e(E e) { return e; }
+    static __device__ __forceinline__ E book(E e, H dE) { return e + (E)dE; }
+};
+template <> struct Arith<float> {
+    using H = float;
+    using E = double;
+    static __device__ __forceinline__ H signed_field(H g, uint32_t x)
+    {
+        return __int_as_float(__float_as_int(g) ^ (int)(x << 31));
+    }
+    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
+    static __device__ __forceinline__ H apply(H h, float w, bool minus) { return minus ? __fsub_rn(h, w) : __fadd_rn(h, w); }
+    static __device__ __forceinline__ E load_e(long long b) { return __longlong_as_double(b); }
+    static __device__ __forceinline__ long long store_e(E e) { return __double_as_longlong(e); }
+    static __device__ __forceinline__ E book(E e, H dE) { return __dadd_rn(e, (double)dE); }
+};
+
+__device__ __forceinline__ int warp_inclusive_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Position of the r-th (0-based) set bit of w; requires r < popc(w).
+__device__ __forceinline__ int nth_set_bit(uint32_t w, int r)
+{
+    int pos = 0, c;
+    c = __popc(w & 0xFFFFu); if (r >= c) { r -= c; pos += 16; w >>= 16; }
+    c = __popc(w & 0xFFu);   if (r >= c) { r -= c; pos += 8;  w >>= 8; }
+    c = __popc(w & 0xFu);    if (r >= c) { r -= c; pos += 4;  w >>= 4; }
+    c = __popc(w & 0x3u);    if (r >= c) { r -= c; pos += 2;  w >>= 2; }
+    c = (int)(w & 1u);       if (r >= c) { pos += 1; }
+    return pos;
+}
+
+__device__ __forceinline__ void group_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Row k of W at the V consecutive entries of this lane (16-byte loads where
+// the lane's slice allows).
+template <typename Tw, int V> struct Row;
+template <int V> struct Row<float, V> {
+    static __device__ __forceinline__ void load(const float* p, float (&c)[V])
+    {
+        static_assert(V % 4 == 0, "V");
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+            c[4 * q] = f.x; c[4 * q + 1] = f.y; c[4 * q + 2] = f.z; c[4 * q + 3] = f.w;
+        }
+    }
+};
+template <int V> struct Row<int8_t, V> {
+    static __device__ __forceinline__ void unpack(uint32_t u, int8_t* c)
+    {
+        c[0] = (int8_t)(u & 0xFFu); c[1] = (int8_t)((u >> 8) & 0xFFu);
+        c[2] = (int8_t)((u >> 16) & 0xFFu); c[3] = (int8_t)(u >> 24);
+    }
+    static __device__ __forceinline__ void load(const int8_t* p, int8_t (&c)[V])
+    {
+        if constexpr (V == 4) {
+            unpack(__ldg(reinterpret_cast<const unsigned int*>(p)), c);
+        } else if constexpr (V == 8) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+            unpack(u.x, c); unpack(u.y, c + 4);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V / 16; ++q) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + q);
+                unpack(u.x, c + 16 * q); unpack(u.y, c + 16 * q + 4);
+                unpack(u.z, c + 16 * q + 8); unpack(u.w, c + 16 * q + 12);
+            }
+        }
+    }
+};
+
+// Replicas per block and the blocks per SM the register budget is sized for:
+// at least 7 replicas per SM, so that 1024 replicas fill 152 SMs in one wave.
+template <int G> struct Occupancy;
+template <> struct Occupancy<1> { static constexpr int rpb = 4, min_blocks = 2; };
+template <> struct Occupancy<2> { static constexpr int rpb = 2, min_blocks = 4; };
+template <> struct Occupancy<4> { static constexpr int rpb = 1, min_blocks = 7; };
+template <> struct Occupancy<8> { static constexpr int rpb = 1, min_blocks = 2; };
+
+// The state words of a replica are standard bit-packed words (x_i is bit i%32
+// of word i/32); a lane's V bits are one slice of word (w*32V + l*V) / 32.
+template <int V>
+__device__ __forceinline__ uint32_t gather_word(uint32_t bits, int lane)
+{
+    constexpr int P = 32 / V;  // lanes per word
+    uint32_t m = (V == 32) ? bits : (bits << ((lane % P) * V));
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+    return m;
+}
+
+}  // namespace step_detail
+}  // namespace da

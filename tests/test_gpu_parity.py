@@ -321,3 +321,49 @@ def test_ptda_c4b_shape(da, inst):
     assert np.array_equal(got["swap_trace"], ref["swap_trace"])
     assert np.array_equal(got["best_E"], ref["E_best"])
     assert np.array_equal(got["temp_of"], ref["temp_of"])
+
+
+@pytest.mark.parametrize("kind", ["int8", "fp32"])
+def test_plain_form_matches_oracle(da, inst, kind):
+    """The one-launch-per-step baseline draws the same numbers and uses the same fp32
+    arithmetic (exact for integer couplings) and no recompute."""
+    import oracle
+    q = inst.sk_bimodal(100, 4) if kind == "int8" else inst.sk_gaussian(200, 4)
+    beta = inst.beta_linear(0.1, 4.0, 600)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal_plain(ctx, beta, 0.5, 9, 21, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=9, seed=21, inc=0.5, recompute_every=0, trace=True, nthreads=NT)
+    assert np.array_equal(got["trace"], ref["trace"])
+    assert np.array_equal(got["final_x"], ref["x_final"])
+    assert np.array_equal(got["best_x"], ref["x_best"])
+    assert np.array_equal(got["flips"], ref["flips"])
+    fast = da.da_anneal(ctx, beta, 0.5, 9, 21, recompute_every=0, trace=True)
+    assert np.array_equal(fast["trace"], got["trace"])
+
+
+def test_batched_launch_matches_single_instances(da, inst):
+    """Mixed sizes and coupling types in one batched launch: every item equals its own
+    da_anneal run (and, through it, the oracle) bit for bit."""
+    import oracle
+    rng = np.random.default_rng(0)
+    jobs, refs = [], []
+    sizes = [64, 128, 96, 256, 512, 1024, 300]
+    for n, N in enumerate(sizes):
+        q = inst.sk_bimodal(N, n) if n % 2 == 0 else inst.sk_gaussian(N, n)
+        T = int(rng.integers(200, 900))
+        beta = inst.beta_linear(0.1, 3.0, T)
+        ctx = da.da_create(q.Q)
+        R = int(rng.integers(3, 40))
+        P = 0 if q.bimodal else 128
+        jobs.append(dict(ctx=ctx, beta=beta, offset_inc=0.5, replicas=R, seed=100 + n, recompute_every=P, trace=True))
+        refs.append(da.da_anneal(ctx, beta, 0.5, R, 100 + n, recompute_every=P, trace=True))
+    outs, el = da.binding.da_batch_anneal(jobs)
+    assert el > 0
+    for o, r in zip(outs, refs):
+        for k in ("trace", "final_x", "best_x", "flips", "final_E", "best_E", "max_drift"):
+            assert np.array_equal(o[k], r[k]), k
+    # one fp32 item against the oracle directly
+    j = jobs[1]
+    ref = oracle.da_anneal(inst.sk_gaussian(128, 1).Q, j["beta"], R=j["replicas"], seed=j["seed"], inc=0.5,
+                           recompute_every=128, trace=True, nthreads=NT)
+    assert np.array_equal(outs[1]["trace"], ref["trace"])
