@@ -193,6 +193,59 @@ typedef struct da_batch_item {
  * graph.  Errors: DA_EINVAL (bad item, N > 1024), DA_ENOMEM, DA_ECUDA. */
 da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s);
 
+/* ---- Request loop (continuous batching) ------------------------------------
+ * A server keeps a persistent kernel whose warps pull work units (one replica of
+ * one request) from a queue that keeps growing while the kernel runs: requests
+ * that arrive while others are on the GPU are admitted as soon as device memory
+ * (within the server's budget) and a request slot are free, and their replicas
+ * run beside those already in flight.  Requests with N > 1024 run as chunked
+ * multi-warp launches on their own streams, concurrently with the kernel.  A
+ * request's results are identical to da_anneal on the same instance, schedule
+ * and seed (recompute_every applies to DA_FP32, as in da_anneal). */
+typedef struct da_server da_server;
+typedef struct da_req da_req;
+
+typedef struct da_job {
+    const void* Q;            /* host, N x N upper-triangular QUBO (as da_create);
+                                 Q and beta must stay valid until da_poll returns
+                                 DA_OK or an error for this request */
+    int64_t N;                /* 1 <= N <= 8192 */
+    da_dtype dtype;
+    const float* beta;        /* host, [steps] */
+    int64_t steps;
+    float offset_inc;
+    int32_t replicas;         /* 1 <= replicas <= 65536 */
+    uint64_t seed;
+    int64_t recompute_every;
+} da_job;
+
+/* Start a server on the current device.  hbm_budget_bytes bounds the device
+ * memory of admitted requests (instance, schedule, state, results);
+ * max_requests bounds how many are admitted at once.
+ * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_server** out);
+
+/* Queue a request; returns at once.  The instance is validated and built on the
+ * host here (as da_create).  Errors: DA_EINVAL; DA_EBUDGET if the request alone
+ * exceeds the budget (it could never be admitted); DA_EBUSY while the server is
+ * shutting down. */
+da_status da_submit(da_server* srv, const da_job* job, da_req** out);
+
+/* Wait up to timeout_us microseconds for a request.  DA_OK: results written to
+ * out (host arrays as for da_anneal; out->elapsed_s = submit-to-completion
+ * latency in seconds).  DA_ENOTREADY (timeout_us = 0) or DA_ETIMEOUT if it has
+ * not finished; the request's own error if it failed. */
+da_status da_poll(da_req* req, int32_t timeout_us, da_result* out);
+
+/* Release a request handle (after its last poll). */
+void da_req_free(da_req* req);
+
+/* Requests completed, persistent-kernel launches so far, device bytes in use. */
+da_status da_server_stats(da_server* srv, int64_t* completed, int64_t* kernel_launches, int64_t* bytes_in_use);
+
+/* Wait for every submitted request to finish, stop the kernel, free everything. */
+void da_server_destroy(da_server* srv);
+
 /* Parallel tempering with the DA step (PTDA, Sec. II and Algorithm 4): L
  * independent ladders of K replicas at inverse temperatures betas[0..K-1]
  * (host, ascending), replica k starting at index k from x = 0.  A sweep is N DA

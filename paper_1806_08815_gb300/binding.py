@@ -48,6 +48,12 @@ class da_batch_item(ctypes.Structure):
                 ("out", ctypes.POINTER(da_result))]
 
 
+class da_job(ctypes.Structure):
+    _fields_ = [("Q", _P), ("N", ctypes.c_int64), ("dtype", ctypes.c_int), ("beta", _P), ("steps", ctypes.c_int64),
+                ("offset_inc", ctypes.c_float), ("replicas", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("recompute_every", ctypes.c_int64)]
+
+
 class da_pt_result(ctypes.Structure):
     _fields_ = [("final_E", _P), ("best_E", _P), ("best_x", _P), ("temp_of", _P),
                 ("swaps", _P), ("swap_trace", _P), ("elapsed_s", ctypes.c_double)]
@@ -84,6 +90,16 @@ def lib() -> ctypes.CDLL:
     L.da_profile_read.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.da_profile_enable.restype = ctypes.c_int
     L.da_profile_read.restype = ctypes.c_int
+    L.da_server_create.argtypes = [i64, i32, ctypes.POINTER(_P)]
+    L.da_submit.argtypes = [_P, ctypes.POINTER(da_job), ctypes.POINTER(_P)]
+    L.da_poll.argtypes = [_P, i32, ctypes.POINTER(da_result)]
+    L.da_req_free.argtypes = [_P]
+    L.da_req_free.restype = None
+    L.da_server_destroy.argtypes = [_P]
+    L.da_server_destroy.restype = None
+    L.da_server_stats.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    for name in ("da_server_create", "da_submit", "da_poll", "da_server_stats"):
+        getattr(L, name).restype = ctypes.c_int
     L.da_batch_anneal.argtypes = [ctypes.POINTER(da_batch_item), i32, ctypes.POINTER(ctypes.c_double)]
     L.da_batch_anneal.restype = ctypes.c_int
     L.da_anneal_plain.argtypes = [_P, _P, i64, f32, i32, u64, ctypes.POINTER(da_result)]
@@ -320,3 +336,70 @@ def da_batch_anneal(jobs: list) -> tuple:
     el = ctypes.c_double()
     _check(lib().da_batch_anneal(arr, n, ctypes.byref(el)))
     return outs, el.value
+
+
+class Server:
+    """A request loop on the current device (wraps da_server*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_requests: int = 1024):
+        h = _P()
+        _check(lib().da_server_create(int(hbm_budget_bytes), int(max_requests), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().da_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().da_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(completed=a.value, kernel_launches=b.value, bytes_in_use=c.value)
+
+
+class Request:
+    def __init__(self, handle, keep, N, R, T, trace=False):
+        self.handle, self.keep, self.N, self.R, self.T = handle, keep, N, R, T
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().da_req_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def da_submit(srv: Server, Q: np.ndarray, beta: np.ndarray, offset_inc: float, replicas: int, seed: int,
+              recompute_every: int = 0) -> Request:
+    Q = np.asarray(Q)
+    N = Q.shape[0]
+    dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
+    Qc = np.ascontiguousarray(Q, dtype=np.int32 if dtype == DA_INT8 else np.float32)
+    b = np.ascontiguousarray(beta, dtype=np.float32)
+    job = da_job(_ptr(Qc), N, dtype, _ptr(b), b.size, float(offset_inc), int(replicas), int(seed) & (2 ** 64 - 1),
+                 int(recompute_every))
+    h = _P()
+    _check(lib().da_submit(srv.handle, ctypes.byref(job), ctypes.byref(h)))
+    return Request(h, (Qc, b), N, int(replicas), b.size)
+
+
+def da_poll(req: Request, timeout_us: int = 0):
+    """Result dict once finished, None while not ready (or on timeout)."""
+    R, W = req.R, da_words(req.N)
+    out = dict(final_E=np.zeros(R), best_E=np.zeros(R), final_x=np.zeros((R, W), np.uint32),
+               best_x=np.zeros((R, W), np.uint32), max_drift=np.zeros(R), flips=np.zeros(R, np.int64))
+    res = da_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                  "flips", "trace")), 0.0)
+    st = lib().da_poll(req.handle, int(timeout_us), ctypes.byref(res))
+    if st in (5, 7):
+        return None
+    _check(st)
+    out["latency_s"] = res.elapsed_s
+    return out

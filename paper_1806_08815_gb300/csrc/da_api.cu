@@ -268,6 +268,72 @@ struct CtxLock {
 }  // namespace
 
 namespace da {
+bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::string& why)
+{
+    const int ldw = (int)align_up((size_t)n, 128);
+    const size_t esz = int8 ? 1 : 4;
+    out.ldw = ldw;
+    out.S = 0;
+    // 8192 zero entries after the last row: a lane whose slice straddles N
+    // reads up to the launch width (at most 8192) past the row start
+    out.W.assign(((size_t)n * ldw + 8192) * esz, 0);
+    out.diag.assign((size_t)n * 4, 0);
+    float amax = 0.f;
+    if (int8) {
+        const int32_t* q = static_cast<const int32_t*>(Q);
+        int8_t* w = reinterpret_cast<int8_t*>(out.W.data());
+        int32_t* d = reinterpret_cast<int32_t*>(out.diag.data());
+        std::vector<long long> rowabs(n, 0);
+        for (int i = 0; i < n; ++i) {
+            d[i] = q[(size_t)i * n + i];
+            rowabs[i] += std::llabs((long long)d[i]);
+            for (int j = i + 1; j < n; ++j) {
+                const int32_t v = q[(size_t)i * n + j];
+                if (v < -128 || v > 127) {
+                    why = "DA_INT8 coupling Q[" + std::to_string(i) + "][" + std::to_string(j) + "] = " +
+                          std::to_string(v) + " outside [-128, 127]";
+                    return false;
+                }
+                w[(size_t)i * ldw + j] = (int8_t)v;
+                w[(size_t)j * ldw + i] = (int8_t)v;
+                rowabs[i] += std::abs(v);
+                rowabs[j] += std::abs(v);
+            }
+        }
+        for (int i = 0; i < n; ++i)
+            if (rowabs[i] >= (1ll << 24)) {
+                why = "DA_INT8 row " + std::to_string(i) + ": |Q_ii| + sum |Q_ij| >= 2^24";
+                return false;
+            }
+    } else {
+        const float* q = static_cast<const float*>(Q);
+        float* w = reinterpret_cast<float*>(out.W.data());
+        float* d = reinterpret_cast<float*>(out.diag.data());
+        for (int i = 0; i < n; ++i) {
+            d[i] = q[(size_t)i * n + i];
+            if (!std::isfinite(d[i])) {
+                why = "non-finite Q entry";
+                return false;
+            }
+            amax = std::max(amax, std::fabs(d[i]));
+            for (int j = i + 1; j < n; ++j) {
+                const float v = q[(size_t)i * n + j];
+                if (!std::isfinite(v)) {
+                    why = "non-finite Q entry";
+                    return false;
+                }
+                w[(size_t)i * ldw + j] = v;
+                w[(size_t)j * ldw + i] = v;
+                amax = std::max(amax, std::fabs(v));
+            }
+        }
+        out.S = fix_scale(amax, n);
+    }
+    return true;
+}
+
+StepShape default_shape(int N) { return auto_shape(N); }
+
 void set_last_error(const std::string& msg) { g_err = msg; }
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S)
 {
@@ -295,52 +361,12 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     if (N < 1 || N > 8192) return fail(DA_EINVAL, "N must be in [1, 8192]");
     if (dtype != DA_INT8 && dtype != DA_FP32) return fail(DA_EINVAL, "unknown dtype");
     const int n = (int)N;
-    const int ldw = (int)align_up((size_t)n, 128);
-    const size_t esz = dtype == DA_INT8 ? 1 : 4;
-    // 8192 zero entries after the last row: a lane whose slice straddles N
-    // reads up to the launch width (at most 8192) past the row start
-    std::vector<char> Wh(((size_t)n * ldw + 8192) * esz, 0);
-    std::vector<char> dh((size_t)n * 4, 0);
-    float amax = 0.f;
-    if (dtype == DA_INT8) {
-        const int32_t* q = static_cast<const int32_t*>(Q);
-        int8_t* w = reinterpret_cast<int8_t*>(Wh.data());
-        int32_t* d = reinterpret_cast<int32_t*>(dh.data());
-        std::vector<long long> rowabs(n, 0);
-        for (int i = 0; i < n; ++i) {
-            d[i] = q[(size_t)i * n + i];
-            rowabs[i] += std::llabs((long long)d[i]);
-            for (int j = i + 1; j < n; ++j) {
-                const int32_t v = q[(size_t)i * n + j];
-                if (v < -128 || v > 127)
-                    return fail(DA_EINVAL, "DA_INT8 coupling Q[" + std::to_string(i) + "][" + std::to_string(j) +
-                                               "] = " + std::to_string(v) + " outside [-128, 127]");
-                w[(size_t)i * ldw + j] = (int8_t)v;
-                w[(size_t)j * ldw + i] = (int8_t)v;
-                rowabs[i] += std::abs(v);
-                rowabs[j] += std::abs(v);
-            }
-        }
-        for (int i = 0; i < n; ++i)
-            if (rowabs[i] >= (1ll << 24))
-                return fail(DA_EINVAL, "DA_INT8 row " + std::to_string(i) + ": |Q_ii| + sum |Q_ij| >= 2^24");
-    } else {
-        const float* q = static_cast<const float*>(Q);
-        float* w = reinterpret_cast<float*>(Wh.data());
-        float* d = reinterpret_cast<float*>(dh.data());
-        for (int i = 0; i < n; ++i) {
-            d[i] = q[(size_t)i * n + i];
-            if (!std::isfinite(d[i])) return fail(DA_EINVAL, "non-finite Q entry");
-            amax = std::max(amax, std::fabs(d[i]));
-            for (int j = i + 1; j < n; ++j) {
-                const float v = q[(size_t)i * n + j];
-                if (!std::isfinite(v)) return fail(DA_EINVAL, "non-finite Q entry");
-                w[(size_t)i * ldw + j] = v;
-                w[(size_t)j * ldw + i] = v;
-                amax = std::max(amax, std::fabs(v));
-            }
-        }
-    }
+    da::HostInstance hin;
+    std::string why;
+    if (!da::build_instance(Q, n, dtype == DA_INT8, hin, why)) return fail(DA_EINVAL, why);
+    const int ldw = hin.ldw;
+    std::vector<char>& Wh = hin.W;
+    std::vector<char>& dh = hin.diag;
     int dev = 0;
     DA_CU(cudaGetDevice(&dev));
     da_ctx* c = new (std::nothrow) da_ctx;
@@ -349,7 +375,7 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     c->dtype = dtype;
     c->ldw = ldw;
     c->device = dev;
-    c->S = dtype == DA_FP32 ? da::fix_scale(amax, n) : 0;
+    c->S = hin.S;
     auto bail = [&](da_status s, const std::string& m) {
         da_destroy(c);
         return fail(s, m);

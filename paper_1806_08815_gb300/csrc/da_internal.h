@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 struct da_ctx;
 
@@ -101,6 +102,18 @@ cudaError_t plain_anneal(const void* W, const void* diag, bool int8, int N, int 
                          long long T, float inc, int R, uint64_t seed, void* ws, int* trace, uint32_t* words_out,
                          long long* eex, long long* part, double* tracked_E, int64_t* flips, cudaStream_t st);
 size_t plain_workspace_bytes(int N, int R);
+
+// An instance in the library's device layout, built on the host from the
+// upper triangle of Q (da_api.cu): W symmetric with zero diagonal, row pitch
+// ldw, 8192 zero entries of slack; diag; fixed-point scale S (fp32).
+struct HostInstance {
+    std::vector<char> W, diag;
+    int ldw = 0, S = 0;
+};
+bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::string& why);
+
+// The default launch shape of the step kernel for N variables.
+StepShape default_shape(int N);
 
 // Error text returned by da_last_error() on the calling thread (da_api.cu).
 void set_last_error(const std::string& msg);

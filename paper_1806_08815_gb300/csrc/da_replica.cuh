@@ -4,7 +4,8 @@
 //
 // Lane l owns the V consecutive variables i = l*V + v of the replica and keeps
 // their effective fields g_i, bits x_i and the Philox words of the current step
-// in registers.  step() performs one step of Algorithm 2 (see da_step.cuh for
+// in registers.  CG selects L2-only loads of the instance (for the persistent
+// request loop, whose inputs change while it runs).  step() performs one step of Algorithm 2 (see da_step.cuh for
 // the decomposition); recompute() replaces the fp32 fields and the tracked
 // energy by their exact fixed-point values (the same definition as the tiled
 // recompute in da_fields.cu, evaluated by the warp itself).
@@ -16,7 +17,7 @@
 namespace da {
 namespace step_detail {
 
-template <typename Tw, int V>
+template <typename Tw, int V, bool CG = false>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -126,7 +127,7 @@ struct WarpReplica {
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
-        if (FULL || base < N) Row<Tw, V>::load(W + (size_t)k * ldw + base, cv);
+        if (FULL || base < N) Row<Tw, V, CG>::load(W + (size_t)k * ldw + base, cv);
         if (draw_next) draw((uint32_t)(t + 1), keys);
         if (FULL || base < N) {
 #pragma unroll
@@ -153,7 +154,7 @@ struct WarpReplica {
         long long acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            acc[v] = ((valid >> v) & 1u) ? __float2ll_rn(ldexpf(diag[base + v], S)) : 0ll;
+            acc[v] = ((valid >> v) & 1u) ? __float2ll_rn(ldexpf(ldx<CG>(diag + base + v), S)) : 0ll;
         const uint32_t myword = word();
         const int nw = (N + 31) >> 5;
         for (int wi = 0; wi < nw; ++wi) {
@@ -164,7 +165,7 @@ struct WarpReplica {
                 const int j = wi * 32 + b;
                 if (base < N) {
                     Tw cv[V];
-                    Row<Tw, V>::load(W + (size_t)j * ldw + base, cv);
+                    Row<Tw, V, CG>::load(W + (size_t)j * ldw + base, cv);
 #pragma unroll
                     for (int v = 0; v < V; ++v) acc[v] += __float2ll_rn(ldexpf(cv[v], S));
                 }
@@ -176,7 +177,7 @@ struct WarpReplica {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             if (((valid & xm) >> v) & 1u) {
-                const long long t = __float2ll_rn(ldexpf(diag[base + v], S)) + acc[v];
+                const long long t = __float2ll_rn(ldexpf(ldx<CG>(diag + base + v), S)) + acc[v];
                 const unsigned long long nlo = lo + (unsigned long long)t;
                 hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
                 lo = nlo;

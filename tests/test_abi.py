@@ -68,3 +68,12 @@ def test_no_cpu_fallback(libda):
     h = ctypes.c_void_p()
     Q = np.triu(np.ones((8, 8), np.int32))
     assert libda.da_create(Q.ctypes.data_as(ctypes.c_void_p), 8, 0, ctypes.byref(h)) == 6
+
+
+def test_server_needs_a_device(libda):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p()
+    assert libda.da_server_create(ctypes.c_int64(1 << 30), 16, ctypes.byref(h)) == 6
+    assert libda.da_server_create(ctypes.c_int64(0), 16, ctypes.byref(h)) == 1

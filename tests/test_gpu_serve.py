@@ -1,0 +1,79 @@
+"""The request loop (da_server_create / da_submit / da_poll): every request's
+result is the same alone and in the mix, whatever else is on the GPU.
+
+Requests of mixed sizes and coupling types are submitted together (small ones
+become units of the persistent kernel, large ones chunked launches on their own
+streams); each must equal da_anneal on the same instance, schedule and seed,
+bit for bit.  A budget that admits one request at a time must give the same
+results, and a request that can never fit is refused."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def da():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_08815_gb300 import binding
+    return binding
+
+
+def _jobs(inst):
+    rng = np.random.default_rng(7)
+    jobs = []
+    for n, N in enumerate([64, 300, 1024, 96, 1500, 512, 2048]):
+        q = inst.sk_bimodal(N, n) if n % 2 == 0 else inst.sk_gaussian(N, n)
+        T = int(rng.integers(300, 1200))
+        jobs.append(dict(Q=q.Q, beta=inst.beta_linear(0.1, 4.0, T), inc=0.5 if n % 3 == 0 else 0.0,
+                         R=int(rng.integers(2, 24)), seed=500 + n, P=0 if q.bimodal else 256))
+    return jobs
+
+
+def _alone(da, j):
+    ctx = da.da_create(j["Q"])
+    return da.da_anneal(ctx, j["beta"], j["inc"], j["R"], j["seed"], recompute_every=j["P"])
+
+
+def _same(a, b):
+    for k in ("final_x", "best_x", "flips", "final_E", "best_E", "max_drift"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_results_same_alone_and_in_the_mix(da):
+    from paper_1806_08815_gb300 import instances as inst
+    jobs = _jobs(inst)
+    srv = da.Server(8 << 30, 64)
+    reqs = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], j["P"]) for j in jobs]
+    outs = [da.da_poll(r, 60_000_000) for r in reqs]
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(jobs) and stats["kernel_launches"] >= 1
+    for j, o in zip(jobs, outs):
+        assert o is not None and o["latency_s"] > 0
+        _same(o, _alone(da, j))
+
+
+def test_tight_budget_queues_and_gives_the_same_results(da):
+    from paper_1806_08815_gb300 import instances as inst
+    jobs = _jobs(inst)[:4]
+    srv = da.Server(64 << 20, 2)
+    reqs = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], j["P"]) for j in jobs]
+    outs = [da.da_poll(r, 60_000_000) for r in reqs]
+    srv.close()
+    for j, o in zip(jobs, outs):
+        _same(o, _alone(da, j))
+
+
+def test_request_over_budget_is_refused(da):
+    from paper_1806_08815_gb300 import instances as inst
+    q = inst.sk_gaussian(2048, 1)
+    srv = da.Server(1 << 20, 4)
+    with pytest.raises(da.DAError) as e:
+        da.da_submit(srv, q.Q, inst.beta_linear(0.1, 1.0, 10), 0.0, 4, 0)
+    assert e.value.status == 3
+    srv.close()
