@@ -136,6 +136,116 @@ def tts99(best_E, tau_run):
     return dict(E_ref=Eref, hits=y, runs=r, theta=theta, R99=R99, tts99_s=tau_run * R99)
 
 
+def _tts_from_best(best_E, tau_run):
+    """TTS99 of one instance from its runs' best energies (reference = best over the runs)."""
+    return tts99(np.asarray(best_E), tau_run)
+
+
+def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_T=400):
+    """Batched launch: n_inst fully connected instances, N uniform in {64..1024}, half bimodal (int8),
+    half Gaussian (fp32, exact recompute every 1024 steps), R replicas each, one persistent CUDA-graph
+    launch; compared with the plain one-launch-per-step form run instance after instance."""
+    rng = np.random.default_rng(1234)
+    sizes = rng.choice([64, 128, 256, 512, 1024], n_inst)
+    jobs, meta = [], []
+    for i, N in enumerate(sizes):
+        bim = i % 2 == 0
+        q = instances.sk_bimodal(int(N), 1000 + i) if bim else instances.sk_gaussian(int(N), 1000 + i)
+        beta = instances.beta_linear(0.05, 3.0, T) if bim else instances.beta_linear(0.1, 10.0, T)
+        jobs.append(dict(ctx=da.da_create(q.Q), beta=beta, offset_inc=1.0 if bim else 0.0, replicas=R, seed=i,
+                         recompute_every=0 if bim else 1024))
+        meta.append((bim, int(N)))
+    da.da_batch_anneal(jobs[:8])                      # warm-up (and autotuning of the classes it touches)
+    outs, el = da.da_batch_anneal(jobs)
+    trials = sum(R * T * N for _, N in meta)
+    # plain form: per-step time of each (coupling, size) class from a short run, one instance at a time
+    per_step = {}
+    for (bim, N) in sorted(set(meta)):
+        i = meta.index((bim, N))
+        da.da_anneal_plain(jobs[i]["ctx"], jobs[i]["beta"][:16], jobs[i]["offset_inc"], R, 0)
+        r = da.da_anneal_plain(jobs[i]["ctx"], jobs[i]["beta"][:plain_T], jobs[i]["offset_inc"], R, 0)
+        per_step[(bim, N)] = r["elapsed_s"] / plain_T
+    plain_time = sum(T * per_step[m] for m in meta)
+    tau_b = el / (n_inst * R)
+    tts_b = [_tts_from_best(o["best_E"], tau_b)["tts99_s"] for o in outs]
+    tts_p = [_tts_from_best(o["best_E"], T * per_step[m] / R)["tts99_s"] for o, m in zip(outs, meta)]
+    return {"workload": f"{n_inst} SK instances, N in {{64,128,256,512,1024}}, half bimodal int8 / half "
+                        f"Gaussian fp32, {R} replicas, {T} steps, one persistent CUDA-graph launch",
+            "value": trials / el, "unit": UNIT, "seconds": el,
+            "plain_gpu": {"value": trials / plain_time, "unit": UNIT,
+                          "basis": f"per-step time of each class from {plain_T}-step plain runs, "
+                                   "instances one after another"},
+            "speedup_vs_plain": plain_time / el,
+            "tts99_median_s": float(np.median(tts_b)), "tts99_median_plain_s": float(np.median(tts_p)),
+            "tts99_basis": "per instance: reference = best energy over its runs, same hit rate for both forms"}
+
+
+def run_ptda(da, instances, L=32, K=32, sweeps=100):
+    """PTDA: SK bimodal N = 512, K = 32 geometric betas in 0.2-5.0, exchange after every sweep."""
+    q = instances.sk_bimodal(512, 77)
+    betas = instances.beta_geometric(0.2, 5.0, K)
+    ctx = da.da_create(q.Q)
+    da.da_pt(ctx, betas, 2, 2, 0)
+    r = da.da_pt(ctx, betas, sweeps, L, 1)
+    trials = L * K * sweeps * q.N * q.N
+    acc = r["swaps"].sum(axis=0) / (L * sweeps)
+    return {"workload": f"SK bimodal N=512, {K} geometric betas 0.2-5.0, {L} ladders, {sweeps} sweeps, "
+                        "device-side exchange after every sweep",
+            "value": trials / r["elapsed_s"], "unit": UNIT, "seconds": r["elapsed_s"],
+            "exchange_acceptance_min": float(acc.min()), "exchange_acceptance_mean": float(acc.mean()),
+            "best_E": float(r["best_E"].min())}
+
+
+def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30):
+    """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
+    [256, 8192], half bimodal / half Gaussian, R replicas, T steps, HBM budget 120 GB."""
+    import threading
+    rng = np.random.default_rng(99)
+    pool = []
+    for i in range(24):
+        N = int(round(np.exp(rng.uniform(np.log(256), np.log(8192)))))
+        bim = i % 2 == 0
+        pool.append(instances.sk_bimodal(N, 3000 + i) if bim else instances.sk_gaussian(N, 3000 + i))
+    betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
+    picks = rng.integers(0, len(pool), n_req)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    srv = da.Server(budget, 1024)
+    warm = da.da_submit(srv, pool[0].Q, betas[pool[0].bimodal][:100], 0.0, 4, 0)
+    da.da_poll(warm, 60_000_000)
+    reqs = [None] * n_req
+    t0 = time.perf_counter()
+
+    def feed():
+        t = t0
+        for k in range(n_req):
+            t += gaps[k]
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            q = pool[picks[k]]
+            reqs[k] = da.da_submit(srv, q.Q, betas[q.bimodal], 1.0 if q.bimodal else 0.0, R, k,
+                                   0 if q.bimodal else 1024)
+
+    th = threading.Thread(target=feed)
+    th.start()
+    th.join()
+    lat = []
+    for k in range(n_req):
+        o = da.da_poll(reqs[k], 600_000_000)
+        lat.append(o["latency_s"])
+    t1 = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    trials = sum(R * T * pool[i].N for i in picks)
+    lat = np.array(lat)
+    return {"workload": f"{n_req} requests, Poisson {rate:.0f} req/s, N log-uniform 256-8192 (pool of 24 "
+                        f"instances), half bimodal / half Gaussian, {R} replicas, {T} steps, HBM budget "
+                        f"{budget >> 30} GB",
+            "value": trials / (t1 - t0), "unit": UNIT, "makespan_s": t1 - t0,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"]}
+
+
 def cpu_baseline(sample_R=None, sample_T=16384):
     """The oracle, as it stands, on the host cores over a bounded sample of the workload."""
     import oracle
@@ -183,6 +293,8 @@ def main():
     ap.add_argument("--steps-per-anneal", type=int, default=C3["steps"])
     ap.add_argument("--plain-steps", type=int, default=10_000,
                     help="steps of the plain one-launch-per-step GPU form timed beside (0 = skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, PTDA and served workloads reported beside the headline")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run two 2048-step anneals from the middle of the schedule and exit (for ncu captures)")
     args = ap.parse_args()
@@ -326,6 +438,10 @@ def main():
     }
     if clk:
         line["clocks"] = clk
+    if rank == 0 and not args.no_extras:
+        line["batched"] = run_batched(da, instances)
+        line["ptda"] = run_ptda(da, instances)
+        line["served"] = run_served(da, instances)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
