@@ -246,6 +246,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
                                        (int)(sizeof(ReplicaScalars) / 8), st, b.sums()));
         }
     }
+    DA_CU(da::launch_best_fixup(b.R, b.sc(), is_int8(c), b.x(), b.bestx(), b.s.nwords(), st));
     return DA_OK;
 }
 
@@ -588,6 +589,7 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
         DA_CU(da::launch_pt_exchange(is_int8(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
                                      seed, st));
     }
+    DA_CU(da::launch_best_fixup(R, b.sc(), is_int8(c), b.x(), b.bestx(), s.nwords(), st));
     if (da_status e = evaluate(c, b, st)) return e;
     DA_CU(cudaEventRecord(c->ev1, st));
     std::vector<long long> eex((size_t)2 * R);

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
                 }
             }
         }
+        rp.flush_best();
         const uint32_t word = rp.word();
         if (lane % R_::P == 0) it.xs[(size_t)r * nw + (rp.base >> 5)] = word;
         if (lane == 0) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
             s.best = A::store_e(rp.Ebest);
             s.flips = rp.flips;
             s.m = rp.m;
-            s.pad = 0;
+            s.check = 0;
             it.sc[r] = s;
         }
     }

@@ -180,7 +180,32 @@ __global__ void init_state_kernel(const void* __restrict__ diag, int N, int R, v
         static_cast<float*>(g)[idx] = i < N ? static_cast<const float*>(diag)[i] : 0.f;
 }
 
+__global__ void best_fixup_kernel(int R, ReplicaScalars* sc, bool int8, const uint32_t* x, uint32_t* bestx, int nw)
+{
+    const int r = blockIdx.x;
+    ReplicaScalars s = sc[r];
+    if (!s.check) return;
+    const bool better = int8 ? s.E < s.best : __longlong_as_double(s.E) < __longlong_as_double(s.best);
+    if (better) {
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) bestx[(size_t)r * nw + w] = x[(size_t)r * nw + w];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (better) s.best = s.E;
+        s.check = 0;
+        sc[r] = s;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_best_fixup(int R, ReplicaScalars* sc, bool is_int8, const uint32_t* x, uint32_t* bestx, int nw,
+                              cudaStream_t st)
+{
+    if (R <= 0) return cudaSuccess;
+    best_fixup_kernel<<<R, 64, 0, st>>>(R, sc, is_int8, x, bestx, nw);
+    return cudaGetLastError();
+}
 
 int fix_scale(float amax, int N)
 {

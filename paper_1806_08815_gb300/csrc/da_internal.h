@@ -18,7 +18,7 @@ struct alignas(32) ReplicaScalars {
     long long best;    // lowest tracked energy seen
     long long flips;   // accepted flips
     uint32_t m;        // consecutive steps without an accepted flip (E_off = m * inc)
-    uint32_t pad;
+    uint32_t check;    // 1: the best-state test of the last step is still to be made
 };
 
 // Launch shape of the parallel-trial step: a group of G warps per replica,
@@ -71,6 +71,12 @@ inline void set_seed(StepParams& p, uint64_t seed)
 // Start state x = 0 of R replicas: fields g = diag (the effective field of
 // x = 0), words and scalars zero (da_fields.cu).
 cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st);
+
+// The best-state test left pending by the last step of an anneal (made after
+// any recompute of that step): if E < best, best = E and the state words are
+// copied to the best-state words (da_fields.cu).
+cudaError_t launch_best_fixup(int R, ReplicaScalars* sc, bool is_int8, const uint32_t* x, uint32_t* bestx, int nw,
+                              cudaStream_t st);
 
 // Step kernel launcher (da_step.cu).  is_int8 selects int8 W / int32 fields.
 cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);

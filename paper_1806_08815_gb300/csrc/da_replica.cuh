@@ -32,6 +32,7 @@ struct WarpReplica {
     u32x4 cr;
     long long cr_blk;
     uint32_t xm, valid, m;
+    bool chk;         // the best-state test of the last step (or recompute) is pending
     E Ecur, Ebest;
     long long flips;
     int lane, base, N, ldw;
@@ -51,6 +52,22 @@ struct WarpReplica {
         valid = base >= N ? 0u : (N - base >= V ? VMASK : ((1u << (N - base)) - 1u));
         cr = {0, 0, 0, 0};
         cr_blk = -1;
+        chk = false;
+    }
+
+    // The test of Algorithm 2's result: a strictly lower tracked energy than any
+    // seen makes the current state the best one.  It is made one step late (x is
+    // unchanged until the next flip) so that the energy's fp64 latency hides
+    // behind the next step's trials, and after any recompute of the step.
+    __device__ __forceinline__ void flush_best()
+    {
+        if (chk) {
+            chk = false;
+            if (Ecur < Ebest) {
+                Ebest = Ecur;
+                snapshot();
+            }
+        }
     }
 
     __device__ __forceinline__ uint32_t word() const { return gather_word<V>(xm, lane); }
@@ -84,11 +101,11 @@ struct WarpReplica {
             const float est = exp_estimate(ax);
             const float U = __uint2float_rn((wd >> 8) + 1u);
             const bool le0 = delta <= 0.0f;
-            const bool need = !le0 && ax > kExpCut;
+            // below kExpCut the band lies under U >= 1, so no cut test is needed
             const bool sure = U < __fmul_rn(est, kBandLo);
             const bool maybe = U < __fmul_rn(est, kBandHi);
-            accm |= (uint32_t)(le0 || (need && sure)) << v;
-            band |= (uint32_t)(need && !sure && maybe) << v;
+            accm |= (uint32_t)(le0 || sure) << v;
+            band |= (uint32_t)(!le0 && !sure && maybe) << v;
         }
         if (__any_sync(0xffffffffu, band != 0u)) {
 #pragma unroll
@@ -101,6 +118,7 @@ struct WarpReplica {
             }
         }
         if constexpr (!FULL) accm &= valid;
+        flush_best();
 
         const int cnt = __popc(accm);
         const int incl = warp_inclusive_scan(cnt, lane);
@@ -120,27 +138,22 @@ struct WarpReplica {
         const int own = __ffs(__ballot_sync(0xffffffffu, j >= excl && j < incl)) - 1;
         const int vk = __shfl_sync(0xffffffffu, nth_set_bit(accm, j - excl), own);
         const uint32_t xold = (__shfl_sync(0xffffffffu, xm, own) >> vk) & 1u;
-        H gk = h[0];
-#pragma unroll
-        for (int v = 1; v < V; ++v)
-            if (v == vk) gk = h[v];
+        const H gk = select_slot<H, V>(h, vk);
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
         if (FULL || base < N) Row<Tw, V, CG>::load(W + (size_t)k * ldw + base, cv);
         if (draw_next) draw((uint32_t)(t + 1), keys);
         if (FULL || base < N) {
+            const typename A::Sign sg = A::sign(xold);
 #pragma unroll
-            for (int v = 0; v < V; ++v) h[v] = A::apply(h[v], cv[v], xold != 0u);
+            for (int v = 0; v < V; ++v) h[v] = A::apply_signed(h[v], cv[v], sg);
         }
         if (lane == own) xm ^= 1u << vk;
         ++flips;
         m = 0;
         Ecur = A::book(Ecur, dEk);
-        if (Ecur < Ebest) {
-            Ebest = Ecur;
-            snapshot();
-        }
+        chk = true;
         return k;
     }
 
@@ -195,6 +208,7 @@ struct WarpReplica {
         const long long top = (long long)((unsigned long long)hi << 32 | (lo >> 32));
         const double v = __fma_rn((double)top, 4294967296.0, (double)(uint32_t)(lo & 0xFFFFFFFFull));
         Ecur = ldexp(v, -(S + 1));
+        chk = true;
     }
 };
 

@@ -336,6 +336,8 @@ bool admit(da_server* s, Req& q)
                        q, "recompute"))
                 return false;
         }
+        if (!cu_ok(da::launch_best_fixup(R, sc, q.int8, xs, xs + (size_t)R * q.xs_stride, q.xs_stride, st), q, "fixup"))
+            return false;
         if (!cu_ok(da::launch_recompute(q.int8, W, diag, q.N, q.inst.ldw, q.inst.S, xs, sh.nwords(), 2 * R, nullptr,
                                         sh.npad(), eex, 1, st, part),
                    q, "evaluate"))

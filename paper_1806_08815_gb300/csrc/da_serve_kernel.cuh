@@ -90,6 +90,7 @@ __device__ __noinline__ void run_unit(const ServeDesc& d, int r)
             }
         }
     }
+    rp.flush_best();
     const uint32_t word = rp.word();
     if (lane % R_::P == 0) d.xs[(size_t)r * V + (rp.base >> 5)] = word;
     double ef, eb, drift;

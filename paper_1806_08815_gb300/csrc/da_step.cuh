@@ -22,7 +22,10 @@
 // A G = 1 group needs no shared memory or barrier.  A G > 1 group publishes
 // its lanes' acceptance and state masks in shared memory behind one named
 // barrier per step; the energy of step t is booked after the barrier of step
-// t + 1, while x still holds the state right after step t.
+// t + 1, while x still holds the state right after step t.  The best-state
+// test of a launch's last step is left pending (ReplicaScalars::check) so that
+// it sees the energy after any recompute between launches, as Algorithm 2's
+// result is defined after each complete step.
 //
 // Launches cover steps [t0, t1) and keep the state in global memory between
 // launches (the fp32 path recomputes the fields between launches).
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
     E Ecur = A::load_e(sc.E), Ebest = A::load_e(sc.best);
     long long flips = sc.flips;
     uint32_t m = sc.m;
+    bool chk = sc.check != 0;       // best-state test pending from the previous launch
     const uint32_t rep = p.rep_base + (uint32_t)r;
     const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
     const bool per_rep = p.betas != nullptr;
@@ -168,6 +172,10 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
             group_barrier(1 + g, 32 * G);
             if (pending) {          // book the flip of step t - 1
                 Ecur = A::book(Ecur, pub[(t - 1) & 1]);
+                chk = true;
+            }
+            if (chk) {              // and test it: x is still the state after step t - 1
+                chk = false;
                 if (Ecur < Ebest) { Ebest = Ecur; snapshot(); }
             }
             uint32_t e[G];
@@ -241,9 +249,9 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
     }
     if constexpr (G > 1) {
         group_barrier(1 + g, 32 * G);
-        if (pending) {
+        if (pending) {              // book the last flip; its test waits for any recompute
             Ecur = A::book(Ecur, pub[(p.t1 - 1) & 1]);
-            if (Ecur < Ebest) { Ebest = Ecur; snapshot(); }
+            chk = true;
         }
     }
 
@@ -256,6 +264,7 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
         sc.best = A::store_e(Ebest);
         sc.flips = flips;
         sc.m = m;
+        sc.check = chk ? 1u : 0u;
         p.sc[r] = sc;
     }
 }
@@ -281,6 +290,7 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
     rp.Ebest = Arith<Tw>::load_e(sc.best);
     rp.flips = sc.flips;
     rp.m = sc.m;
+    rp.chk = sc.check != 0;
     const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
     const bool per_rep = p.betas != nullptr;
     const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
@@ -303,6 +313,7 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
         sc.best = Arith<Tw>::store_e(rp.Ebest);
         sc.flips = rp.flips;
         sc.m = rp.m;
+        sc.check = rp.chk ? 1u : 0u;
         p.sc[r] = sc;
     }
 }

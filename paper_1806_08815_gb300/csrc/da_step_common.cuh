@@ -14,6 +14,9 @@ template <> struct Arith<int8_t> {
     static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
     static __device__ __forceinline__ H apply(H h, int8_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
+    using Sign = int32_t;
+    static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1 : 1; }
+    static __device__ __forceinline__ H apply_signed(H h, int8_t w, Sign s) { return h + s * (H)w; }
     static __device__ __forceinline__ E load_e(long long b) { return b; }
     static __device__ __forceinline__ long long store_e(E e) { return e; }
     static __device__ __forceinline__ E book(E e, H dE) { return e + (E)dE; }
@@ -27,6 +30,11 @@ template <> struct Arith<float> {
     }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
     static __device__ __forceinline__ H apply(H h, float w, bool minus) { return minus ? __fsub_rn(h, w) : __fadd_rn(h, w); }
+    using Sign = float;
+    static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1.0f : 1.0f; }
+    // h + s w with s = +-1: the product is exact, so this is the same single
+    // rounding as __fadd_rn / __fsub_rn
+    static __device__ __forceinline__ H apply_signed(H h, float w, Sign s) { return __fmaf_rn(s, w, h); }
     static __device__ __forceinline__ E load_e(long long b) { return __longlong_as_double(b); }
     static __device__ __forceinline__ long long store_e(E e) { return __double_as_longlong(e); }
     static __device__ __forceinline__ E book(E e, H dE) { return __dadd_rn(e, (double)dE); }
@@ -52,6 +60,23 @@ __device__ __forceinline__ int nth_set_bit(uint32_t w, int r)
     c = __popc(w & 0x3u);    if (r >= c) { r -= c; pos += 2;  w >>= 2; }
     c = (int)(w & 1u);       if (r >= c) { pos += 1; }
     return pos;
+}
+
+// h[vk] for a warp-uniform vk, as one switch instead of V selects.
+template <typename H, int V>
+__device__ __forceinline__ H select_slot(const H (&h)[V], int vk)
+{
+#define DA_SLOT(n) \
+    case n:        \
+        if constexpr (V > n) return h[n]; else return h[0];
+    switch (vk) {
+        DA_SLOT(0) DA_SLOT(1) DA_SLOT(2) DA_SLOT(3) DA_SLOT(4) DA_SLOT(5) DA_SLOT(6) DA_SLOT(7)
+        DA_SLOT(8) DA_SLOT(9) DA_SLOT(10) DA_SLOT(11) DA_SLOT(12) DA_SLOT(13) DA_SLOT(14) DA_SLOT(15)
+        DA_SLOT(16) DA_SLOT(17) DA_SLOT(18) DA_SLOT(19) DA_SLOT(20) DA_SLOT(21) DA_SLOT(22) DA_SLOT(23)
+        DA_SLOT(24) DA_SLOT(25) DA_SLOT(26) DA_SLOT(27) DA_SLOT(28) DA_SLOT(29) DA_SLOT(30) DA_SLOT(31)
+    default: return h[0];
+    }
+#undef DA_SLOT
 }
 
 __device__ __forceinline__ void group_barrier(int id, int nthreads)

@@ -85,6 +85,16 @@ def test_fast_exp_band_contains_exact_exp(da):
     x = np.array([0.0], np.float32)
     lo, hi = da.binding.da_diag_exp_band(x)
     assert lo[0] <= 2.0 ** 24 <= hi[0]
+    # below the cut the band's lower edge stays under U >= 1, so the fast path never
+    # accepts there (the kernels make no separate cut test): every fp32 x in
+    # [-30, -16.7], and a sample down to -1e30
+    a = np.float32(-16.7).view(np.uint32)
+    b = np.float32(-30.0).view(np.uint32)
+    x = np.arange(int(a), int(b) + 1, dtype=np.uint32).view(np.float32)
+    x = np.concatenate([x, -np.exp(np.random.default_rng(3).uniform(np.log(30), np.log(1e30), 1 << 20)).astype(np.float32),
+                        np.array([-np.inf], np.float32)])
+    lo, _ = da.binding.da_diag_exp_band(x)
+    assert lo.max() < 1.0
 
 
 def test_accept_decision_matches_definition(da):
