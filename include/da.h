@@ -137,7 +137,8 @@ da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);
 /* Run the Digital Annealer (Algorithm 2) R times from x = 0 (all runs start
  * from one state, Sec. II) for `steps` iterations, blocking until done.
  *   beta_schedule  host, [steps] inverse temperature of every step (the
- *                  temperature is updated every iteration, "DA parameters").
+ *                  temperature is updated every iteration, "DA parameters");
+ *                  every entry finite and >= 0 (DA_EINVAL otherwise).
  *   offset_inc     dynamic-offset increase rate: after m steps without an
  *                  accepted flip the trials use Delta E - m * offset_inc;
  *                  0 switches the offset off (as in the paper's runs).
@@ -154,7 +155,8 @@ da_status da_anneal(da_ctx* ctx, const float* beta_schedule, int64_t steps, floa
 
 /* As da_anneal, with the schedule and every output in device memory, queued
  * on `stream` (a cudaStream_t; NULL = the legacy default stream) and
- * returning without waiting.  The context's workspace is reused: calls on one
+ * returning without waiting.  The device schedule is not inspected: its
+ * entries must be finite and >= 0 (other values give undefined results).  The context's workspace is reused: calls on one
  * context must be ordered on one stream. */
 da_status da_anneal_async(da_ctx* ctx, const float* beta_schedule_dev, int64_t steps, float offset_inc,
                           int32_t replicas, uint64_t seed, int64_t recompute_every,

@@ -447,6 +447,7 @@ static da_status anneal_common(da_ctx* c, const float* beta, bool beta_on_host, 
     if (steps >= (1ll << 32)) return fail(DA_EINVAL, "steps >= 2^32");
     if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
     if (recompute_every < 0) return fail(DA_EINVAL, "recompute_every < 0");
+    if (beta_on_host && !da::schedule_ok(beta, steps)) return fail(DA_EINVAL, "beta must be finite and >= 0");
     const StepShape s = shape_for(c);
     if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
     const Layout L = plan(c, s, R, steps, beta_on_host, want_trace, 0);
@@ -547,7 +548,7 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     if ((double)sweeps * c->N >= 4294967296.0) return fail(DA_EINVAL, "sweeps * N >= 2^32");
     if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
     for (int k = 0; k < K; ++k) {
-        if (!std::isfinite(betas[k]) || betas[k] < 0.f) return fail(DA_EINVAL, "betas must be finite and >= 0");
+        if (!da::schedule_ok(betas + k, 1)) return fail(DA_EINVAL, "betas must be finite and >= 0");
         if (k > 0 && betas[k] < betas[k - 1]) return fail(DA_EINVAL, "betas must be ascending");
     }
     CtxLock lock(c);
@@ -654,6 +655,7 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     if (da_status s = check_ctx(c)) return s;
     if (c->N > 1024) return fail(DA_EINVAL, "the plain form supports N <= 1024");
     if (steps < 0 || (steps > 0 && !beta)) return fail(DA_EINVAL, "bad schedule");
+    if (!da::schedule_ok(beta, steps)) return fail(DA_EINVAL, "beta must be finite and >= 0");
     if (R < 1) return fail(DA_EINVAL, "replicas < 1");
     if (steps >= (1ll << 32)) return fail(DA_EINVAL, "steps >= 2^32");
     if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");

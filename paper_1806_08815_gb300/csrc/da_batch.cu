@@ -259,6 +259,8 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         if (N > 1024) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes N <= 1024");
         if (it.replicas < 1 || it.steps < 0 || it.steps >= (1ll << 32) || (it.steps > 0 && !it.beta))
             return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad replicas/steps/schedule");
+        if (it.steps > 0 && !da::schedule_ok(it.beta, it.steps))
+            return bfail(DA_EINVAL, "item " + std::to_string(i) + ": beta must be finite and >= 0");
         if (!(it.offset_inc >= 0.f) || !std::isfinite(it.offset_inc) || it.recompute_every < 0)
             return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad offset or recompute period");
         Host h{};

@@ -121,6 +121,15 @@ bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::str
 // The default launch shape of the step kernel for N variables.
 StepShape default_shape(int N);
 
+// True when every entry of a host schedule is finite and >= 0 (the kernels'
+// fast Metropolis test relies on beta >= 0).
+inline bool schedule_ok(const float* beta, long long n)
+{
+    for (long long t = 0; t < n; ++t)
+        if (!(beta[t] >= 0.f) || beta[t] == __builtin_huge_valf()) return false;
+    return true;
+}
+
 // Error text returned by da_last_error() on the calling thread (da_api.cu).
 void set_last_error(const std::string& msg);
 

@@ -537,6 +537,8 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     if (job->dtype != DA_INT8 && job->dtype != DA_FP32) return sfail(DA_EINVAL, "unknown dtype");
     if (job->steps < 0 || job->steps >= (1ll << 32) || (job->steps > 0 && !job->beta))
         return sfail(DA_EINVAL, "bad schedule");
+    if (job->steps > 0 && !da::schedule_ok(job->beta, job->steps))
+        return sfail(DA_EINVAL, "beta must be finite and >= 0");
     if (job->replicas < 1 || job->replicas > 65536) return sfail(DA_EINVAL, "need 1 <= replicas <= 65536");
     if (!(job->offset_inc >= 0.f) || !std::isfinite(job->offset_inc) || job->recompute_every < 0)
         return sfail(DA_EINVAL, "bad offset or recompute period");

@@ -95,6 +95,13 @@ def test_fast_exp_band_contains_exact_exp(da):
                         np.array([-np.inf], np.float32)])
     lo, _ = da.binding.da_diag_exp_band(x)
     assert lo.max() < 1.0
+    # for x >= 0 (delta <= 0) the band's upper edge lies above every U <= 2^24, so
+    # such a trial is surely accepted or decided by the exact rule: every fp32 x in
+    # [0, 2^-8] and a dense grid up to 100
+    x = np.arange(0, int(np.float32(2.0 ** -8).view(np.uint32)) + 1, dtype=np.uint32).view(np.float32)
+    x = np.concatenate([x, np.linspace(0, 100, 1 << 20, dtype=np.float32), np.array([-0.0, np.inf], np.float32)])
+    _, hi = da.binding.da_diag_exp_band(x)
+    assert hi.min() > 2.0 ** 24
 
 
 def test_accept_decision_matches_definition(da):
@@ -244,6 +251,17 @@ def test_edge_cases(da, inst):
     # and with the offset on, the first flip comes at the closed-form step
     got = da.da_anneal(ctx2, np.full(40, 1e6, np.float32), 2.0, 2, 1, trace=True)
     assert np.all(got["trace"][:, :25] == -1) and np.all(got["trace"][:, 25] >= 0)
+
+
+def test_schedule_must_be_finite_and_nonnegative(da, inst):
+    q = inst.sk_bimodal(40, 1)
+    ctx = da.da_create(q.Q)
+    for bad in (-1.0, np.inf, np.nan):
+        beta = np.full(10, 0.5, np.float32)
+        beta[3] = bad
+        with pytest.raises(da.DAError) as e:
+            da.da_anneal(ctx, beta, 0.0, 2, 0)
+        assert e.value.status == 1
 
 
 def test_results_do_not_depend_on_replica_count(da, inst):
