@@ -36,16 +36,30 @@ C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1,
 
 # DRAM bytes per step-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # capture summarised in profiles/, valid while the kernel source has the recorded hash.
-STEP_TRAFFIC = {"source_sha256_16": "3f9c044d33fd01ed", "bytes_per_launch": 8.606976e6,
+# Warp instructions per replica-step of the step kernel (smsp__inst_executed.sum / (R x steps))
+# from the same capture: the issue-slot roofline of a kernel bound by instruction issue.
+STEP_INST_PER_REPLICA_STEP = 1094.0
+STEP_TRAFFIC = {"source_sha256_16": "1ffbebd47c2d3128", "bytes_per_launch": 8.605952e6,
                 "profile": "profiles/step_kernel_f32_v32_g1_sk_gaussian_n1024_r1024.md"}
 
 
 def step_source_sha():
     import hashlib
-    path = os.path.join(ROOT, "paper_1806_08815_gb300", "csrc", "da_step.cuh")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
-METRIC = "single-flip trials/s (DA step, SK-Gaussian N=1024, 1024 replicas, 2e5 steps)"
-UNIT = "trials/s"
+    h = hashlib.sha256()
+    for f in ("da_step.cuh", "da_replica.cuh", "da_step_common.cuh", "da_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1806_08815_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def issue_roofline(replica_steps_per_launch, launch_s):
+    """Issue-slot roofline of the step kernel: warp instructions per launch (from the ncu count per
+    replica-step) over the launch time, against 4 issue slots per SM per cycle x 152 SMs x 2.07 GHz."""
+    if step_source_sha() != STEP_TRAFFIC["source_sha256_16"]:
+        return None
+    achieved = STEP_INST_PER_REPLICA_STEP * replica_steps_per_launch / launch_s / 1e9
+    peak = 152 * 4 * 2.07
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s", "frac": achieved / peak,
+            "basis": "ncu smsp__inst_executed.sum per replica-step x replica-steps per launch / launch time"}
 
 
 def load_peaks():
@@ -428,8 +442,9 @@ def main():
                      "frac": achieved_gbs / hbm,
                      "traffic": STEP_TRAFFIC["bytes_per_launch"]
                      if step_source_sha() == STEP_TRAFFIC["source_sha256_16"] else None,
-                     "kernel": "step_kernel<float,V=32,G=1>", "peak_source": peak_src,
+                     "kernel": "step_kernel_g1<float,V=32>", "peak_source": peak_src,
                      "basis": "nominal bytes per replica-step: fp32 column of W + fields + state bits"},
+        "roofline_issue": issue_roofline(R * per_launch_steps, avg_launch_s),
         "step_kernel": {"launches": launches, "avg_launch_ms": avg_launch_s * 1e3,
                         "share_of_step": (step_ms / 1e3) / (t_step * args.steps)},
         "tts99": tts,
