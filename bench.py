@@ -31,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+METRIC = "single-flip trials/s (DA step, SK-Gaussian N=1024, 1024 replicas, 2e5 steps)"
+UNIT = "trials/s"
+
 C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1, beta1=10.0, inc=0.0,
           instance_seed=0, seed=0)
 

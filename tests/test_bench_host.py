@@ -1,0 +1,52 @@
+"""Host-side checks of bench.py and __graft_entry__.py that need no GPU: every name
+they load is bound somewhere in the module (a name dropped by an edit only fails
+when its line runs, which may be minutes into a GPU run), and the JSON keys the
+measurement line promises are spelled in the source."""
+import ast
+import builtins
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def unbound_names(path):
+    tree = ast.parse(open(path).read())
+    bound = set(dir(builtins)) | {"__file__", "__name__"}
+    for n in ast.walk(tree):
+        if isinstance(n, (ast.FunctionDef, ast.AsyncFunctionDef, ast.ClassDef)):
+            bound.add(n.name)
+        elif isinstance(n, ast.Name) and isinstance(n.ctx, (ast.Store, ast.Del)):
+            bound.add(n.id)
+        elif isinstance(n, ast.arg):
+            bound.add(n.arg)
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            for a in n.names:
+                bound.add((a.asname or a.name).split(".")[0])
+        elif isinstance(n, ast.ExceptHandler) and n.name:
+            bound.add(n.name)
+    loaded = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
+    return sorted(loaded - bound)
+
+
+@pytest.mark.parametrize("name", ["bench.py", "__graft_entry__.py"])
+def test_every_loaded_name_is_bound(name):
+    assert unbound_names(os.path.join(ROOT, name)) == []
+
+
+def test_bench_line_keys_present():
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "h2d_bytes_per_step",
+                "d2h_bytes_per_step", "gpu_launches", "roofline", "cpu_baseline", "clocks", "impl"):
+        assert f'"{key}"' in src, key
+
+
+def test_bench_constants():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    assert mod.UNIT == "trials/s" and "trials/s" in mod.METRIC
+    assert mod.C3["N"] == 1024 and mod.C3["replicas"] == 1024 and mod.C3["steps"] == 200_000
