@@ -263,7 +263,7 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
             "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"]}
 
 
-def cpu_baseline(sample_R=None, sample_T=16384):
+def cpu_baseline(sample_R=None, sample_T=32768):
     """The oracle, as it stands, on the host cores over a bounded sample of the workload."""
     import oracle
     from paper_1806_08815_gb300 import instances
