@@ -428,7 +428,9 @@ def main():
     achieved_gbs = bytes_per_launch / avg_launch_s / 1e9
     n_step_launches = math.ceil(T / P)
     n_recompute = T // P
-    gpu_launches = n_step_launches + 2 * n_recompute + 2 + 1     # steps, recompute+energy, final eval, finalize
+    # init, step launches, 3 per recompute (state expansion, tensor-core recompute, energy sum), the same 3
+    # for the final evaluation, best-state fixup, finalize
+    gpu_launches = 1 + n_step_launches + 3 * n_recompute + 3 + 1 + 1
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -52,6 +52,7 @@ struct da_ctx {
     int device = 0;
     void* W = nullptr;
     void* diag = nullptr;
+    da::TcOperand tc;  // digit planes of W for the tensor-core recompute
     void* ws = nullptr;
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -112,7 +113,7 @@ da_status ensure_ws(da_ctx* c, size_t bytes)
 
 // Workspace carve-up for one anneal-like call.
 struct Layout {
-    size_t h, xs, sc, sums, eex, beta, res, trace, pt, total;
+    size_t h, xs, sc, sums, tca, eex, beta, res, trace, pt, total;
 };
 
 Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_beta, bool with_trace, size_t pt_bytes)
@@ -124,6 +125,7 @@ Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_b
     L.xs = take((size_t)2 * R * s.nwords() * 4);
     L.sc = take((size_t)R * sizeof(ReplicaScalars));
     L.sums = take((size_t)16 * ((std::max(s.npad(), c->N) + 63) / 64) * 2 * R);
+    L.tca = take(da::tc_state_bytes(c->N, 2 * R));
     L.eex = take((size_t)2 * R * 8);
     L.beta = take(with_beta ? (size_t)T * 4 : 0);
     L.res = take((size_t)4 * R * 8);
@@ -165,6 +167,7 @@ struct RunBuffers {
     ReplicaScalars* sc() const { return reinterpret_cast<ReplicaScalars*>(base + L.sc); }
     long long* sums() const { return reinterpret_cast<long long*>(base + L.sums); }
     long long* eex() const { return reinterpret_cast<long long*>(base + L.eex); }
+    void* tca() const { return base + L.tca; }
 };
 
 StepParams base_params(const da_ctx* c, const RunBuffers& b)
@@ -197,8 +200,21 @@ da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 // Exact energies of the final and best states into eex[0..2R).
 da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
-    DA_CU(da::launch_recompute(is_int8(c), c->W, c->diag, c->N, c->ldw, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
-                               b.s.npad(), b.eex(), 1, st, b.sums()));
+    DA_CU(da::launch_recompute_tc(is_int8(c), c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
+                                  b.s.npad(), b.eex(), 1, st, b.sums(), b.tca()));
+    return DA_OK;
+}
+
+// After a call's stream work has completed: a bounded wait inside the
+// tensor-core recompute that gave up invalidates the call's results.
+da_status check_tc(da_ctx* c)
+{
+    int flag = 0;
+    DA_CU(cudaMemcpy(&flag, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        DA_CU(cudaMemset(c->tc.err, 0, sizeof(int)));
+        return fail(DA_ETIMEOUT, "tensor-core recompute: a bounded wait on a pipeline barrier gave up");
+    }
     return DA_OK;
 }
 
@@ -241,9 +257,9 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
         DA_CU(da::launch_step(is_int8(c), b.s, p, trace_dev != nullptr, st));
         if (e1) DA_CU(cudaEventRecord(e1, st));
         if (rec && p.t1 % recompute_every == 0) {
-            DA_CU(da::launch_recompute(false, c->W, c->diag, c->N, c->ldw, c->S, b.x(), b.s.nwords(), b.R, b.h(),
-                                       b.s.npad(), reinterpret_cast<long long*>(b.sc()),
-                                       (int)(sizeof(ReplicaScalars) / 8), st, b.sums()));
+            DA_CU(da::launch_recompute_tc(false, c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), b.R, b.h(),
+                                          b.s.npad(), reinterpret_cast<long long*>(b.sc()),
+                                          (int)(sizeof(ReplicaScalars) / 8), st, b.sums(), b.tca()));
         }
     }
     DA_CU(da::launch_best_fixup(b.R, b.sc(), is_int8(c), b.x(), b.bestx(), b.s.nwords(), st));
@@ -394,6 +410,13 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
+    e = da::tc_operand_build(dtype == DA_INT8, c->W, n, ldw, c->S, &c->tc, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(e == cudaErrorMemoryAllocation ? DA_ENOMEM : DA_ECUDA,
+                    std::string("tensor-core operand: ") + cudaGetErrorString(e));
+    }
     *out = c;
     return DA_OK;
 }
@@ -404,6 +427,7 @@ void da_destroy(da_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->W) cudaFree(c->W);
     if (c->diag) cudaFree(c->diag);
+    da::tc_operand_free(&c->tc);
     if (c->ws) cudaFree(c->ws);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -484,7 +508,7 @@ da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int3
     DA_CU(cudaEventRecord(c->ev1, st));
     if (!out) {
         DA_CU(cudaStreamSynchronize(st));
-        return DA_OK;
+        return check_tc(c);
     }
     const size_t words = (size_t)da_words(c->N);
     std::vector<double> hres((size_t)4 * R);
@@ -498,6 +522,7 @@ da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int3
     if (want_trace && steps > 0)
         DA_CU(cudaMemcpyAsync(out->trace, b.base + b.L.trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
+    if (da_status e = check_tc(c)) return e;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out->elapsed_s = ms * 1e-3;
@@ -605,6 +630,7 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     if (want_trace && sweeps > 0)
         DA_CU(cudaMemcpyAsync(out->swap_trace, strace, n_sw * (size_t)sweeps, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
+    if (da_status e = check_tc(c)) return e;
     if (!out) return DA_OK;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
@@ -629,19 +655,21 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     const size_t hb = align_up((size_t)R * c->N * 4, 256);
     const size_t sb = align_up((size_t)16 * ((c->N + 63) / 64) * R, 256);
     const size_t eb = align_up((size_t)R * 8, 256);
-    if (da_status e = ensure_ws(c, xb + hb + sb + eb)) return e;
+    const size_t ab = align_up(da::tc_state_bytes(c->N, R), 256);
+    if (da_status e = ensure_ws(c, xb + hb + sb + eb + ab)) return e;
     char* base = static_cast<char*>(c->ws);
     uint32_t* xd = reinterpret_cast<uint32_t*>(base);
     void* hd = base + xb;
     long long* sums = reinterpret_cast<long long*>(base + xb + hb);
     long long* ed = reinterpret_cast<long long*>(base + xb + hb + sb);
     DA_CU(cudaMemcpyAsync(xd, x, (size_t)R * words * 4, cudaMemcpyHostToDevice, st));
-    DA_CU(da::launch_recompute(is_int8(c), c->W, c->diag, c->N, c->ldw, c->S, xd, (int)words, R, h ? hd : nullptr,
-                               c->N, E ? ed : nullptr, 1, st, sums));
+    DA_CU(da::launch_recompute_tc(is_int8(c), c->tc, c->diag, c->N, c->S, xd, (int)words, R, h ? hd : nullptr, c->N,
+                                  E ? ed : nullptr, 1, st, sums, base + xb + hb + sb + eb));
     std::vector<long long> eh(E ? (size_t)R : 0);
     if (h) DA_CU(cudaMemcpyAsync(h, hd, (size_t)R * c->N * 4, cudaMemcpyDeviceToHost, st));
     if (E) DA_CU(cudaMemcpyAsync(eh.data(), ed, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
+    if (da_status e = check_tc(c)) return e;
     if (E)
         for (int r = 0; r < R; ++r)
             E[r] = is_int8(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
@@ -691,6 +719,7 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     if (want_trace && steps > 0)
         DA_CU(cudaMemcpyAsync(out->trace, base + o_trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
+    if (da_status e = check_tc(c)) return e;
     if (!out) return DA_OK;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));

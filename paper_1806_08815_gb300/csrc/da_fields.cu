@@ -230,6 +230,19 @@ cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void
     return cudaGetLastError();
 }
 
+cudaError_t launch_energy_sum(bool is_int8, const long long* part, int tiles, int R, int S, long long* E, int Estride,
+                              cudaStream_t st)
+{
+    if (R <= 0) return cudaSuccess;
+    const int tb = 128;
+    const I128* pp = reinterpret_cast<const I128*>(part);
+    if (is_int8)
+        energy_kernel<true><<<(R + tb - 1) / tb, tb, 0, st>>>(pp, tiles, R, S, E, Estride);
+    else
+        energy_kernel<false><<<(R + tb - 1) / tb, tb, 0, st>>>(pp, tiles, R, S, E, Estride);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
                              long long* E, int Estride, cudaStream_t st, long long* scratch)
@@ -245,12 +258,7 @@ cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int 
         recompute_kernel<false><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !E) return err;
-    const int tb = 128;
-    if (is_int8)
-        energy_kernel<true><<<(R + tb - 1) / tb, tb, 0, st>>>(part, tiles, R, S, E, Estride);
-    else
-        energy_kernel<false><<<(R + tb - 1) / tb, tb, 0, st>>>(part, tiles, R, S, E, Estride);
-    return cudaGetLastError();
+    return launch_energy_sum(is_int8, scratch, tiles, R, S, E, Estride, st);
 }
 
 }  // namespace da

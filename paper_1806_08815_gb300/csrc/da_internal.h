@@ -94,6 +94,33 @@ cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int 
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
                              long long* E, int Estride, cudaStream_t st, long long* scratch);
 
+// E[r * Estride] from the 128-bit partial sums part[tiles][R] of a recompute:
+// the energy sum / 2^(S+1) (int64, or the fp64 bit pattern of its single
+// rounding for fp32) (da_fields.cu).
+cudaError_t launch_energy_sum(bool is_int8, const long long* part, int tiles, int R, int S, long long* E, int Estride,
+                              cudaStream_t st);
+
+// Tensor-core form of the same recompute (da_mma.cu), bit-identical to
+// launch_recompute.  The operand holds the instance's couplings on the
+// fixed-point grid (the int8 couplings themselves) split into `limbs`
+// balanced digits of `bits` bits, each exact in f16, laid out for the tensor
+// cores; `err` is a device flag set to 1 if a bounded wait inside the kernel
+// gave up (the results of that call are then invalid).
+struct TcOperand {
+    void* B = nullptr;
+    int* err = nullptr;
+    int bits = 0, limbs = 0, kchunks = 0;
+};
+void tc_digits(bool is_int8, int N, int* bits, int* limbs);
+cudaError_t tc_operand_build(bool is_int8, const void* W, int N, int ldw, int S, TcOperand* op, cudaStream_t st);
+void tc_operand_free(TcOperand* op);
+// Workspace for R states expanded to f16 (state_ws of launch_recompute_tc).
+size_t tc_state_bytes(int N, int R);
+// Arguments as launch_recompute; scratch must hold 16 * ceil(max(npad, N) / 64) * R bytes.
+cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
+                                const uint32_t* xs, int nw, int R, void* hout, int npad, long long* E, int Estride,
+                                cudaStream_t st, long long* scratch, void* state_ws);
+
 // PT exchange (da_pt.cu).
 cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                const ReplicaScalars* sc, int* temp_of, int* rep_at,

@@ -1,0 +1,430 @@
+// da_mma.cu -- the exact field recompute on the tensor cores (tcgen05).
+//
+// The recompute g = diag + W x of R states is a dense contraction
+// G[r][i] = sum_j X[r][j] W[j][i] with X in {0, 1}: the states are the M side
+// (128 per tile, one per TMEM lane), the variables i the N side (64 per tile)
+// and the couplings j the K side.  Its value is defined exactly (da_fields.cu):
+// every coupling is put on the fixed-point grid, v_ij = round(W_ij 2^S) (the
+// int8 couplings themselves), and summed in integers.  The tensor cores reach
+// the same integers: v is split into balanced digits of b bits,
+//   v = sum_l d_l 2^(b l),   d_l in [-2^(b-1), 2^(b-1)),
+// every digit is exact in fp16 (|d| <= 2048), and b is chosen so that no
+// partial sum of digits over the K side exceeds 2^21 in magnitude, far inside
+// the 24-bit integer range of the fp32 accumulator.  Each digit plane is one
+// accumulator in tensor memory; the epilogue combines the planes in 64-bit
+// integers, adds the fixed-point diagonal and rounds once, exactly like the
+// CUDA-core form.
+//
+// Operands are laid out in HBM in the tensor core's canonical K-major layout
+// (8-row x 16-byte core matrices, [K chunk][row group][8][8] halves per tile),
+// so every pipeline stage is two contiguous bulk copies: the digit planes of
+// the instance are built once per context, the states are expanded from bits
+// to f16 before each recompute.
+//
+// Block: 4 warps.  Warp 0 allocates tensor memory and one of its threads
+// issues the bulk copies of a 3-stage ring; one thread of warp 1 issues the
+// MMAs (4 K-steps of 16 per stage, one per digit plane each) and commits the
+// stage back to the copier; then all 4 warps read their 32 TMEM lanes (one
+// state each) and write fields and 128-bit partial energies.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "da_internal.h"
+#include "da_tc.cuh"
+
+namespace da {
+namespace {
+
+constexpr int kBM = 128;   // states per tile (TMEM lanes)
+constexpr int kBN = 64;    // variables per tile (TMEM columns per digit plane)
+constexpr int kBK = 64;    // couplings per pipeline stage
+constexpr int kStages = 3;
+constexpr int kThreads = 128;
+constexpr uint32_t kATile = kBM * kBK * 2;   // bytes of one state tile (16 KB)
+constexpr uint32_t kBTile = kBN * kBK * 2;   // bytes of one digit-plane tile (8 KB)
+constexpr uint32_t kWaitLimit = 1u << 26;    // polls of one mbarrier before giving up ...
+constexpr uint64_t kWaitNs = 2000000000ull;  // ... or 2 s, whichever comes first
+constexpr int kMaxLimbs = 6;                 // digit planes for any N <= 8192 (tc_digits)
+
+// Offset (in halves) of element (row, k) inside a tile of `rows` x 64 halves
+// in the canonical K-major layout without swizzling.
+__device__ __forceinline__ size_t core_offset(int rows, int row, int k)
+{
+    return (size_t)((k >> 3) * (rows >> 3) + (row >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+template <bool INT8>
+__device__ __forceinline__ long long fixed_w(const void* W, size_t idx, int S)
+{
+    if constexpr (INT8) return (long long)static_cast<const int8_t*>(W)[idx];
+    else return __float2ll_rn(ldexpf(static_cast<const float*>(W)[idx], S));
+}
+
+template <bool INT8>
+__device__ __forceinline__ long long fixed_d(const void* diag, int i, int S)
+{
+    if constexpr (INT8) return (long long)static_cast<const int32_t*>(diag)[i];
+    else return __float2ll_rn(ldexpf(static_cast<const float*>(diag)[i], S));
+}
+
+// Digit planes: one thread per (tile i, chunk j, row i, group of 8 j).
+template <bool INT8>
+__global__ void build_digits_kernel(const void* __restrict__ W, int N, int ldw, int S, int bits, int limbs,
+                                    int kchunks, __half* __restrict__ B, long long total)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int g = (int)(idx & 7);
+    const int row = (int)((idx >> 3) & 63);
+    const long long tile = idx >> 9;           // itile * kchunks + kchunk
+    const int kchunk = (int)(tile % kchunks);
+    const int itile = (int)(tile / kchunks);
+    const int i = itile * kBN + row;
+    const int jb = kchunk * kBK + g * 8;
+    long long v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = jb + e;
+        v[e] = (i < N && j < N) ? fixed_w<INT8>(W, (size_t)j * ldw + i, S) : 0ll;
+    }
+    const long long half_range = 1ll << (bits - 1);
+    const long long mask = (1ll << bits) - 1;
+    for (int l = 0; l < limbs; ++l) {
+        __align__(16) __half h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            long long d = v[e] & mask;
+            if (d >= half_range) d -= mask + 1;
+            v[e] = (v[e] - d) >> bits;
+            h[e] = __int2half_rn((int)d);
+        }
+        __half* dst = B + ((size_t)tile * limbs + l) * (kBN * kBK) + core_offset(kBN, row, g * 8);
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+    }
+}
+
+// States as f16 {0, 1}: one thread per 8 variables of one state, in the
+// order of the destination (coalesced 16-byte stores).
+__global__ void expand_states_kernel(const uint32_t* __restrict__ xs, int nw, int N, int R, int kchunks,
+                                     __half* __restrict__ A, long long total)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int row = (int)(idx & 127);
+    const int kc = (int)((idx >> 7) & 7);
+    const long long tile = idx >> 10;          // rtile * kchunks + kchunk
+    const int kchunk = (int)(tile % kchunks);
+    const int rtile = (int)(tile / kchunks);
+    const int r = rtile * kBM + row;
+    const int j8 = kchunk * kBK + kc * 8;
+    uint32_t byte = 0;
+    if (r < R && j8 < N) {
+        byte = (xs[(size_t)r * nw + (j8 >> 5)] >> (j8 & 31)) & 0xFFu;
+        if (N - j8 < 8) byte &= (1u << (N - j8)) - 1u;
+    }
+    __align__(16) unsigned short h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h[e] = ((byte >> e) & 1u) ? 0x3C00 : 0;   // f16 1.0 / 0.0
+    __half* dst = A + (size_t)tile * (kBM * kBK) + core_offset(kBM, row, kc * 8);
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+}
+
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ void i128_add(I128& a, long long v)
+{
+    const unsigned long long lo = a.lo + (unsigned long long)v;
+    a.hi += (v < 0 ? -1ll : 0ll) + (lo < a.lo ? 1ll : 0ll);
+    a.lo = lo;
+}
+
+struct TcParams {
+    const __half* A;        // [rtiles][kchunks] state tiles
+    const __half* B;        // [ceil(N/64)][kchunks][limbs] digit-plane tiles
+    const void* diag;
+    const uint32_t* xs;     // [R][nw]
+    void* hout;             // [R][npad] or null
+    I128* part;             // [gridDim.x][R] or null
+    int* err;
+    int N, S, bits, limbs, kchunks, nw, R, npad;
+    uint32_t ncols;         // tensor-memory columns allocated
+};
+
+template <bool INT8>
+__device__ __forceinline__ void store_field(void* hout, size_t at, long long acc, int S)
+{
+    if constexpr (INT8) static_cast<int32_t*>(hout)[at] = (int32_t)acc;
+    else static_cast<float*>(hout)[at] = ldexpf(__ll2float_rn(acc), -S);
+}
+
+template <bool INT8>
+__global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_constant__ TcParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ int s_fail;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * kBN;
+    const int r = blockIdx.y * kBM + threadIdx.x;   // TMEM lane threadIdx.x holds state r
+
+    if (i0 >= p.N) {   // padding beyond N (whole block): zero fields and partial sums
+        if (r < p.R) {
+            if (p.hout)
+                for (int e = 0; e < kBN; ++e)
+                    if (i0 + e < p.npad) store_field<INT8>(p.hout, (size_t)r * p.npad + i0 + e, 0ll, 0);
+            if (p.part) p.part[(size_t)blockIdx.x * p.R + r] = I128{0ull, 0ll};
+        }
+        return;
+    }
+
+    const uint32_t stage_bytes = kATile + (uint32_t)p.limbs * kBTile;
+    uint8_t* sm = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + kStages * stage_bytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_init_fence();
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, p.ncols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *tslot;
+    const int nk = p.kchunks;
+
+    if (warp == 0) {
+        if (lane == 0) {   // bulk-copy issuer
+            const __half* a_src = p.A + (size_t)blockIdx.y * nk * (kBM * kBK);
+            const __half* b_src = p.B + (size_t)blockIdx.x * nk * p.limbs * (kBN * kBK);
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % kStages;
+                const uint32_t u = (uint32_t)(c / kStages);
+                if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit, kWaitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                uint8_t* st = sm + s * stage_bytes;
+                tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
+                tc::bulk_g2s(st, a_src + (size_t)c * (kBM * kBK), kATile, &full[s]);
+                tc::bulk_g2s(st + kATile, b_src + (size_t)c * p.limbs * (kBN * kBK), (uint32_t)p.limbs * kBTile,
+                             &full[s]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            constexpr uint32_t idesc = tc::idesc_f16_f32(kBM, kBN);
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % kStages;
+                const uint32_t u = (uint32_t)(c / kStages);
+                if (!tc::mbar_wait(&full[s], u & 1u, kWaitLimit, kWaitNs)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t a0 = tc::smem_u32(sm + s * stage_bytes);
+                const uint32_t b0 = a0 + kATile;
+#pragma unroll
+                for (int q = 0; q < kBK / 16; ++q) {
+                    // K-step q covers core-matrix columns 2q, 2q + 1 of the stage
+                    const uint64_t ad = tc::smem_desc(a0 + q * 2 * (kBM / 8) * 128, (kBM / 8) * 128, 128);
+                    for (int l = 0; l < p.limbs; ++l) {
+                        const uint64_t bd =
+                            tc::smem_desc(b0 + l * kBTile + q * 2 * (kBN / 8) * 128, (kBN / 8) * 128, 128);
+                        tc::mma_f16(tbase + (uint32_t)(l * kBN), ad, bd, idesc, (c > 0 || q > 0) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(done);
+        }
+        __syncwarp();
+    }
+
+    // epilogue: state r = TMEM lane threadIdx.x, variables i0 .. i0 + 63
+    if (!tc::mbar_wait(done, 0, kWaitLimit, kWaitNs)) s_fail = 1;
+    __syncwarp();
+    tc::fence_after_sync();
+    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    I128 esum{0ull, 0ll};
+    const bool live = r < p.R;
+#pragma unroll 1
+    for (int cg = 0; cg < kBN / 16; ++cg) {
+        const int ib = i0 + cg * 16;
+        __syncwarp();
+        long long acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = ib + e < p.N ? fixed_d<INT8>(p.diag, ib + e, p.S) : 0ll;
+        for (int l = 0; l < p.limbs; ++l) {
+            uint32_t v[16];
+            tc::tmem_ld16(lane_addr + (uint32_t)(l * kBN + cg * 16), v);
+            const int sh = p.bits * l;
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                acc[e] = (long long)((unsigned long long)acc[e] +
+                                     ((unsigned long long)__float2ll_rn(__uint_as_float(v[e])) << sh));
+        }
+        if (live) {
+            if (p.hout) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    if (ib + e < p.npad)
+                        store_field<INT8>(p.hout, (size_t)r * p.npad + ib + e, ib + e < p.N ? acc[e] : 0ll, p.S);
+            }
+            if (p.part && ib < p.N) {
+                const uint32_t xw = (p.xs[(size_t)r * p.nw + (ib >> 5)] >> (ib & 31)) & 0xFFFFu;
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    if (((xw >> e) & 1u) && ib + e < p.N) i128_add(esum, fixed_d<INT8>(p.diag, ib + e, p.S) + acc[e]);
+            }
+        }
+    }
+    if (live && p.part) p.part[(size_t)blockIdx.x * p.R + r] = esum;
+
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, p.ncols);
+    }
+    if (threadIdx.x == 0 && s_fail) atomicExch(p.err, 1);
+}
+
+size_t smem_bytes(int limbs) { return 1024 + (size_t)kStages * (kATile + (size_t)limbs * kBTile) + 8 * (2 * kStages + 1) + 16; }
+
+int ceil_log2(long long n)
+{
+    int L = 0;
+    while ((1ll << L) < n) ++L;
+    return L;
+}
+
+}  // namespace
+
+void tc_digits(bool is_int8, int N, int* bits, int* limbs)
+{
+    if (is_int8) {   // the couplings are balanced 8-bit digits already
+        *bits = 8;
+        *limbs = 1;
+        return;
+    }
+    // |partial sum| <= 2^(b-1) * N <= 2^21; |v| <= 2^(62 - L), 2^L >= N + 1
+    const int b = std::min(12, 22 - ceil_log2(std::max(N, 2)));
+    const int L = ceil_log2((long long)N + 1);
+    *bits = b;
+    *limbs = (64 - L + b - 1) / b;
+}
+
+size_t tc_state_bytes(int N, int R)
+{
+    const size_t kchunks = (size_t)(N + kBK - 1) / kBK;
+    const size_t rtiles = (size_t)(R + kBM - 1) / kBM;
+    return rtiles * kchunks * kATile;
+}
+
+cudaError_t tc_operand_build(bool is_int8, const void* W, int N, int ldw, int S, TcOperand* op, cudaStream_t st)
+{
+    tc_digits(is_int8, N, &op->bits, &op->limbs);
+    op->kchunks = (N + kBK - 1) / kBK;
+    const int itiles = (N + kBN - 1) / kBN;
+    const size_t bytes = (size_t)itiles * op->kchunks * op->limbs * kBTile;
+    cudaError_t e = cudaMalloc(&op->B, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&op->err, sizeof(int));
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(op->err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)itiles * op->kchunks * kBN * 8;
+    const int tb = 256;
+    const unsigned blocks = (unsigned)((total + tb - 1) / tb);
+    if (is_int8)
+        build_digits_kernel<true><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
+                                                         static_cast<__half*>(op->B), total);
+    else
+        build_digits_kernel<false><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
+                                                          static_cast<__half*>(op->B), total);
+    return cudaGetLastError();
+}
+
+void tc_operand_free(TcOperand* op)
+{
+    if (op->B) cudaFree(op->B);
+    if (op->err) cudaFree(op->err);
+    *op = TcOperand{};
+}
+
+cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
+                                const uint32_t* xs, int nw, int R, void* hout, int npad, long long* E, int Estride,
+                                cudaStream_t st, long long* scratch, void* state_ws)
+{
+    if (R <= 0) return cudaSuccess;
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t smem = smem_bytes(op.limbs);
+    const int max_limbs = is_int8 ? 1 : kMaxLimbs;
+    if (op.limbs < 1 || op.limbs > max_limbs) return cudaErrorInvalidValue;
+    if (dev < 64 && !attr_set[is_int8][dev]) {
+        const int bytes = (int)smem_bytes(max_limbs);
+        cudaError_t e = is_int8 ? cudaFuncSetAttribute(recompute_tc_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                                : cudaFuncSetAttribute(recompute_tc_kernel<false>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr_set[is_int8][dev] = true;
+    }
+
+    const int rtiles = (R + kBM - 1) / kBM;
+    const long long total = (long long)rtiles * op.kchunks * kBM * 8;
+    const int tb = 256;
+    __half* A = static_cast<__half*>(state_ws);
+    expand_states_kernel<<<(unsigned)((total + tb - 1) / tb), tb, 0, st>>>(xs, nw, N, R, op.kchunks, A, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    const int rows = hout ? std::max(npad, N) : N;
+    const int itiles = (rows + kBN - 1) / kBN;
+    TcParams p;
+    p.A = A;
+    p.B = static_cast<const __half*>(op.B);
+    p.diag = diag;
+    p.xs = xs;
+    p.hout = hout;
+    p.part = E ? reinterpret_cast<I128*>(scratch) : nullptr;
+    p.err = op.err;
+    p.N = N;
+    p.S = S;
+    p.bits = op.bits;
+    p.limbs = op.limbs;
+    p.kchunks = op.kchunks;
+    p.nw = nw;
+    p.R = R;
+    p.npad = npad;
+    uint32_t nc = 32;
+    while (nc < (uint32_t)(op.limbs * kBN)) nc <<= 1;
+    p.ncols = nc;
+    dim3 grid(itiles, rtiles);
+    if (is_int8)
+        recompute_tc_kernel<true><<<grid, kThreads, smem, st>>>(p);
+    else
+        recompute_tc_kernel<false><<<grid, kThreads, smem, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !E) return e;
+    return launch_energy_sum(is_int8, scratch, itiles, R, S, E, Estride, st);
+}
+
+}  // namespace da
