@@ -318,6 +318,15 @@ da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
  * u = ((w >> 8) + 1) 2^-24 with w[n] 32-bit Philox words. */
 da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n);
 da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n);
+/* The fixed-point conversions of the exact recompute (da_field_recompute) as
+ * the kernels evaluate them, in integer arithmetic (got), beside the same
+ * conversions through the 64-bit conversion instructions (ref):
+ * da_diag_fixed:  got[i], ref[i] = round(w[i] 2^S[i]) to nearest, ties to even
+ *                 (defined for |w[i] 2^S[i]| < 2^63);
+ * da_diag_scaled: got[i], ref[i] = fl32(v[i]) 2^-S[i] (fl32 = round to nearest
+ *                 even).  Host arrays of n entries.  Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_diag_fixed(const float* w, const int32_t* S, int64_t* got, int64_t* ref, int64_t n);
+da_status da_diag_scaled(const int64_t* v, const int32_t* S, float* got, float* ref, int64_t n);
 
 #ifdef __cplusplus
 }

@@ -112,6 +112,10 @@ def lib() -> ctypes.CDLL:
     L.da_diag_accept.argtypes = [_P, _P, _P, i64]
     L.da_diag_exp_band.restype = ctypes.c_int
     L.da_diag_accept.restype = ctypes.c_int
+    L.da_diag_fixed.argtypes = [_P, _P, _P, _P, i64]
+    L.da_diag_scaled.argtypes = [_P, _P, _P, _P, i64]
+    L.da_diag_fixed.restype = ctypes.c_int
+    L.da_diag_scaled.restype = ctypes.c_int
     L.da_diag_expf.argtypes = [_P, _P, i64]
     L.da_diag_philox.argtypes = [_P, _P, i64]
     for name in ("da_diag_expf", "da_diag_philox", "da_create", "da_ctx_info", "da_set_launch_shape", "da_anneal", "da_anneal_async", "da_pt",
@@ -293,6 +297,26 @@ def da_diag_accept(x: np.ndarray, w: np.ndarray) -> np.ndarray:
     acc = np.empty(xs.size, np.uint8)
     _check(lib().da_diag_accept(_ptr(xs), _ptr(ws), _ptr(acc), xs.size))
     return acc
+
+
+def da_diag_fixed(w: np.ndarray, S: np.ndarray):
+    """(integer-path, intrinsic-path) round(w 2^S) as the kernels compute it."""
+    ws = np.ascontiguousarray(w, dtype=np.float32).ravel()
+    Ss = np.ascontiguousarray(np.broadcast_to(S, ws.shape), dtype=np.int32).ravel()
+    got = np.empty(ws.size, np.int64)
+    ref = np.empty(ws.size, np.int64)
+    _check(lib().da_diag_fixed(_ptr(ws), _ptr(Ss), _ptr(got), _ptr(ref), ws.size))
+    return got, ref
+
+
+def da_diag_scaled(v: np.ndarray, S: np.ndarray):
+    """(integer-path, intrinsic-path) fl32(v) 2^-S as the kernels compute it."""
+    vs = np.ascontiguousarray(v, dtype=np.int64).ravel()
+    Ss = np.ascontiguousarray(np.broadcast_to(S, vs.shape), dtype=np.int32).ravel()
+    got = np.empty(vs.size, np.float32)
+    ref = np.empty(vs.size, np.float32)
+    _check(lib().da_diag_scaled(_ptr(vs), _ptr(Ss), _ptr(got), _ptr(ref), vs.size))
+    return got, ref
 
 
 def da_static_pitch(N: int) -> int:

@@ -410,7 +410,7 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
-    e = da::tc_operand_build(dtype == DA_INT8, c->W, n, ldw, c->S, &c->tc, c->stream);
+    e = da::tc_operand_build(dtype == DA_INT8, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -7,6 +7,7 @@
 
 #include "da.h"
 #include "da_device.cuh"
+#include "da_fixed.cuh"
 
 namespace {
 
@@ -41,6 +42,24 @@ __global__ void accept_kernel(const float* x, const uint32_t* w, uint8_t* acc, l
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < n) acc[i] = da::metropolis_accept(x[i], w[i]) ? 1 : 0;
+}
+
+// The recompute's fixed-point conversions in integer arithmetic, beside the
+// same conversions written with the 64-bit conversion instructions.
+__global__ void fixed_kernel(const float* w, const int32_t* S, long long* got, long long* ref, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    got[i] = da::fixed_of_f32(w[i], S[i]);
+    ref[i] = __float2ll_rn(ldexpf(w[i], S[i]));
+}
+
+__global__ void scaled_kernel(const long long* v, const int32_t* S, float* got, float* ref, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    got[i] = da::scaled_f32_of(v[i], S[i]);
+    ref[i] = ldexpf(__ll2float_rn(v[i]), -S[i]);
 }
 
 thread_local std::string g_diag_err;
@@ -113,4 +132,42 @@ extern "C" da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* 
         accept_kernel<<<(unsigned)((n + 255) / 256), 256>>>(xa, reinterpret_cast<const uint32_t*>(xa + n),
                                                             static_cast<uint8_t*>(b), n);
     });
+}
+
+extern "C" da_status da_diag_fixed(const float* w, const int32_t* S, int64_t* got, int64_t* ref, int64_t n)
+{
+    if (n < 0 || (n > 0 && (!w || !S || !got || !ref))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    std::vector<char> in((size_t)n * 8);
+    std::copy((const char*)w, (const char*)w + n * 4, in.begin());
+    std::copy((const char*)S, (const char*)S + n * 4, in.begin() + n * 4);
+    std::vector<long long> out((size_t)n * 2);
+    da_status s = run((size_t)n * 8, (size_t)n * 16, in.data(), out.data(), [&](void* a, void* b) {
+        const float* wa = static_cast<const float*>(a);
+        long long* o = static_cast<long long*>(b);
+        fixed_kernel<<<(unsigned)((n + 255) / 256), 256>>>(wa, reinterpret_cast<const int32_t*>(wa + n), o, o + n, n);
+    });
+    if (s != DA_OK) return s;
+    std::copy(out.begin(), out.begin() + n, got);
+    std::copy(out.begin() + n, out.end(), ref);
+    return DA_OK;
+}
+
+extern "C" da_status da_diag_scaled(const int64_t* v, const int32_t* S, float* got, float* ref, int64_t n)
+{
+    if (n < 0 || (n > 0 && (!v || !S || !got || !ref))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    std::vector<char> in((size_t)n * 12);
+    std::copy((const char*)v, (const char*)v + n * 8, in.begin());
+    std::copy((const char*)S, (const char*)S + n * 4, in.begin() + n * 8);
+    std::vector<float> out((size_t)n * 2);
+    da_status s = run((size_t)n * 12, (size_t)n * 8, in.data(), out.data(), [&](void* a, void* b) {
+        const long long* va = static_cast<const long long*>(a);
+        float* o = static_cast<float*>(b);
+        scaled_kernel<<<(unsigned)((n + 255) / 256), 256>>>(va, reinterpret_cast<const int32_t*>(va + n), o, o + n, n);
+    });
+    if (s != DA_OK) return s;
+    std::copy(out.begin(), out.begin() + n, got);
+    std::copy(out.begin() + n, out.end(), ref);
+    return DA_OK;
 }

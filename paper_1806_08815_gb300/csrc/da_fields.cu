@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "da_fixed.cuh"
 #include "da_internal.h"
 
 namespace da {
@@ -37,14 +38,14 @@ template <bool INT8>
 __device__ __forceinline__ long long fixed_of(const void* a, size_t idx, int S)
 {
     if constexpr (INT8) return (long long)static_cast<const int8_t*>(a)[idx];
-    else return __float2ll_rn(ldexpf(static_cast<const float*>(a)[idx], S));
+    else return fixed_of_f32(static_cast<const float*>(a)[idx], S);
 }
 
 template <bool INT8>
 __device__ __forceinline__ long long fixed_diag(const void* diag, int i, int S)
 {
     if constexpr (INT8) return (long long)static_cast<const int32_t*>(diag)[i];
-    else return __float2ll_rn(ldexpf(static_cast<const float*>(diag)[i], S));
+    else return fixed_of_f32(static_cast<const float*>(diag)[i], S);
 }
 
 struct I128 {
@@ -128,13 +129,13 @@ __global__ void __launch_bounds__(kWarps * 32) recompute_kernel(const void* __re
                 if constexpr (INT8)
                     static_cast<int32_t*>(hout)[(size_t)r * npad + ia] = ia < N ? (int32_t)acc[q][0] : 0;
                 else
-                    static_cast<float*>(hout)[(size_t)r * npad + ia] = ia < N ? ldexpf(__ll2float_rn(acc[q][0]), -S) : 0.f;
+                    static_cast<float*>(hout)[(size_t)r * npad + ia] = ia < N ? scaled_f32_of(acc[q][0], S) : 0.f;
             }
             if (ib < npad) {
                 if constexpr (INT8)
                     static_cast<int32_t*>(hout)[(size_t)r * npad + ib] = ib < N ? (int32_t)acc[q][1] : 0;
                 else
-                    static_cast<float*>(hout)[(size_t)r * npad + ib] = ib < N ? ldexpf(__ll2float_rn(acc[q][1]), -S) : 0.f;
+                    static_cast<float*>(hout)[(size_t)r * npad + ib] = ib < N ? scaled_f32_of(acc[q][1], S) : 0.f;
             }
         }
         if (part) {

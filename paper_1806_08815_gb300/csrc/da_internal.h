@@ -108,11 +108,13 @@ cudaError_t launch_energy_sum(bool is_int8, const long long* part, int tiles, in
 // gave up (the results of that call are then invalid).
 struct TcOperand {
     void* B = nullptr;
+    long long* dfix = nullptr;  // the diagonal on the same grid
     int* err = nullptr;
     int bits = 0, limbs = 0, kchunks = 0;
 };
 void tc_digits(bool is_int8, int N, int* bits, int* limbs);
-cudaError_t tc_operand_build(bool is_int8, const void* W, int N, int ldw, int S, TcOperand* op, cudaStream_t st);
+cudaError_t tc_operand_build(bool is_int8, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+                             cudaStream_t st);
 void tc_operand_free(TcOperand* op);
 // Workspace for R states expanded to f16 (state_ws of launch_recompute_tc).
 size_t tc_state_bytes(int N, int R);

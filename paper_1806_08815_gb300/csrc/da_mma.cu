@@ -30,6 +30,7 @@
 
 #include <algorithm>
 
+#include "da_fixed.cuh"
 #include "da_internal.h"
 #include "da_tc.cuh"
 
@@ -58,14 +59,22 @@ template <bool INT8>
 __device__ __forceinline__ long long fixed_w(const void* W, size_t idx, int S)
 {
     if constexpr (INT8) return (long long)static_cast<const int8_t*>(W)[idx];
-    else return __float2ll_rn(ldexpf(static_cast<const float*>(W)[idx], S));
+    else return fixed_of_f32(static_cast<const float*>(W)[idx], S);
 }
 
 template <bool INT8>
 __device__ __forceinline__ long long fixed_d(const void* diag, int i, int S)
 {
     if constexpr (INT8) return (long long)static_cast<const int32_t*>(diag)[i];
-    else return __float2ll_rn(ldexpf(static_cast<const float*>(diag)[i], S));
+    else return fixed_of_f32(static_cast<const float*>(diag)[i], S);
+}
+
+// The diagonal on the fixed-point grid, zero-padded to n entries.
+template <bool INT8>
+__global__ void build_dfix_kernel(const void* __restrict__ diag, int N, int S, long long* __restrict__ dfix, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dfix[i] = i < N ? fixed_d<INT8>(diag, i, S) : 0ll;
 }
 
 // Digit planes: one thread per (tile i, chunk j, row i, group of 8 j).
@@ -145,7 +154,7 @@ __device__ __forceinline__ void i128_add(I128& a, long long v)
 struct TcParams {
     const __half* A;        // [rtiles][kchunks] state tiles
     const __half* B;        // [ceil(N/64)][kchunks][limbs] digit-plane tiles
-    const void* diag;
+    const long long* dfix;  // [kchunks * 64] fixed-point diagonal, zero-padded
     const uint32_t* xs;     // [R][nw]
     void* hout;             // [R][npad] or null
     I128* part;             // [gridDim.x][R] or null
@@ -155,10 +164,10 @@ struct TcParams {
 };
 
 template <bool INT8>
-__device__ __forceinline__ void store_field(void* hout, size_t at, long long acc, int S)
+__device__ __forceinline__ uint32_t field_bits(long long acc, int S)
 {
-    if constexpr (INT8) static_cast<int32_t*>(hout)[at] = (int32_t)acc;
-    else static_cast<float*>(hout)[at] = ldexpf(__ll2float_rn(acc), -S);
+    if constexpr (INT8) return (uint32_t)(int32_t)acc;
+    else return __float_as_uint(scaled_f32_of(acc, S));
 }
 
 template <bool INT8>
@@ -175,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
         if (r < p.R) {
             if (p.hout)
                 for (int e = 0; e < kBN; ++e)
-                    if (i0 + e < p.npad) store_field<INT8>(p.hout, (size_t)r * p.npad + i0 + e, 0ll, 0);
+                    if (i0 + e < p.npad) static_cast<uint32_t*>(p.hout)[(size_t)r * p.npad + i0 + e] = 0u;
             if (p.part) p.part[(size_t)blockIdx.x * p.R + r] = I128{0ull, 0ll};
         }
         return;
@@ -263,13 +272,19 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
     const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
     I128 esum{0ull, 0ll};
     const bool live = r < p.R;
+    const bool vec = (p.npad & 3) == 0;
+    uint32_t* hrow = p.hout ? static_cast<uint32_t*>(p.hout) + (size_t)r * p.npad : nullptr;
 #pragma unroll 1
     for (int cg = 0; cg < kBN / 16; ++cg) {
         const int ib = i0 + cg * 16;
         __syncwarp();
         long long acc[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = ib + e < p.N ? fixed_d<INT8>(p.diag, ib + e, p.S) : 0ll;
+        for (int e = 0; e < 16; e += 2) {
+            const longlong2 d2 = *reinterpret_cast<const longlong2*>(p.dfix + ib + e);
+            acc[e] = d2.x;
+            acc[e + 1] = d2.y;
+        }
         for (int l = 0; l < p.limbs; ++l) {
             uint32_t v[16];
             tc::tmem_ld16(lane_addr + (uint32_t)(l * kBN + cg * 16), v);
@@ -277,20 +292,29 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
 #pragma unroll
             for (int e = 0; e < 16; ++e)
                 acc[e] = (long long)((unsigned long long)acc[e] +
-                                     ((unsigned long long)__float2ll_rn(__uint_as_float(v[e])) << sh));
+                                     ((unsigned long long)(long long)small_int_of(__uint_as_float(v[e])) << sh));
         }
         if (live) {
-            if (p.hout) {
+            if (hrow) {
+                uint32_t hb[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    if (ib + e < p.npad)
-                        store_field<INT8>(p.hout, (size_t)r * p.npad + ib + e, ib + e < p.N ? acc[e] : 0ll, p.S);
+                for (int e = 0; e < 16; ++e) hb[e] = field_bits<INT8>(acc[e], p.S);  // 0 for i >= N
+                if (vec && ib + 16 <= p.npad) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<uint4*>(hrow + ib + 4 * q) =
+                            make_uint4(hb[4 * q], hb[4 * q + 1], hb[4 * q + 2], hb[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        if (ib + e < p.npad) hrow[ib + e] = hb[e];
+                }
             }
             if (p.part && ib < p.N) {
                 const uint32_t xw = (p.xs[(size_t)r * p.nw + (ib >> 5)] >> (ib & 31)) & 0xFFFFu;
 #pragma unroll
                 for (int e = 0; e < 16; ++e)
-                    if (((xw >> e) & 1u) && ib + e < p.N) i128_add(esum, fixed_d<INT8>(p.diag, ib + e, p.S) + acc[e]);
+                    if ((xw >> e) & 1u) i128_add(esum, p.dfix[ib + e] + acc[e]);
             }
         }
     }
@@ -337,7 +361,8 @@ size_t tc_state_bytes(int N, int R)
     return rtiles * kchunks * kATile;
 }
 
-cudaError_t tc_operand_build(bool is_int8, const void* W, int N, int ldw, int S, TcOperand* op, cudaStream_t st)
+cudaError_t tc_operand_build(bool is_int8, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+                             cudaStream_t st)
 {
     tc_digits(is_int8, N, &op->bits, &op->limbs);
     op->kchunks = (N + kBK - 1) / kBK;
@@ -345,18 +370,23 @@ cudaError_t tc_operand_build(bool is_int8, const void* W, int N, int ldw, int S,
     const size_t bytes = (size_t)itiles * op->kchunks * op->limbs * kBTile;
     cudaError_t e = cudaMalloc(&op->B, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&op->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&op->dfix, (size_t)op->kchunks * kBK * sizeof(long long));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(op->err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const long long total = (long long)itiles * op->kchunks * kBN * 8;
     const int tb = 256;
     const unsigned blocks = (unsigned)((total + tb - 1) / tb);
-    if (is_int8)
+    const int nd = op->kchunks * kBK;
+    if (is_int8) {
         build_digits_kernel<true><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
                                                          static_cast<__half*>(op->B), total);
-    else
+        build_dfix_kernel<true><<<(nd + tb - 1) / tb, tb, 0, st>>>(diag, N, S, op->dfix, nd);
+    } else {
         build_digits_kernel<false><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
                                                           static_cast<__half*>(op->B), total);
+        build_dfix_kernel<false><<<(nd + tb - 1) / tb, tb, 0, st>>>(diag, N, S, op->dfix, nd);
+    }
     return cudaGetLastError();
 }
 
@@ -364,6 +394,7 @@ void tc_operand_free(TcOperand* op)
 {
     if (op->B) cudaFree(op->B);
     if (op->err) cudaFree(op->err);
+    if (op->dfix) cudaFree(op->dfix);
     *op = TcOperand{};
 }
 
@@ -401,7 +432,7 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
     TcParams p;
     p.A = A;
     p.B = static_cast<const __half*>(op.B);
-    p.diag = diag;
+    p.dfix = op.dfix;
     p.xs = xs;
     p.hout = hout;
     p.part = E ? reinterpret_cast<I128*>(scratch) : nullptr;

@@ -11,6 +11,7 @@
 // recompute in da_fields.cu, evaluated by the warp itself).
 #pragma once
 #include "da_device.cuh"
+#include "da_fixed.cuh"
 #include "da_internal.h"
 #include "da_step_common.cuh"
 
@@ -167,7 +168,7 @@ struct WarpReplica {
         long long acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            acc[v] = ((valid >> v) & 1u) ? __float2ll_rn(ldexpf(ldx<CG>(diag + base + v), S)) : 0ll;
+            acc[v] = ((valid >> v) & 1u) ? fixed_of_f32(ldx<CG>(diag + base + v), S) : 0ll;
         const uint32_t myword = word();
         const int nw = (N + 31) >> 5;
         for (int wi = 0; wi < nw; ++wi) {
@@ -180,7 +181,7 @@ struct WarpReplica {
                     Tw cv[V];
                     Row<Tw, V, CG>::load(W + (size_t)j * ldw + base, cv);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += __float2ll_rn(ldexpf(cv[v], S));
+                    for (int v = 0; v < V; ++v) acc[v] += fixed_of_f32(cv[v], S);
                 }
             }
         }
@@ -190,12 +191,12 @@ struct WarpReplica {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             if (((valid & xm) >> v) & 1u) {
-                const long long t = __float2ll_rn(ldexpf(ldx<CG>(diag + base + v), S)) + acc[v];
+                const long long t = fixed_of_f32(ldx<CG>(diag + base + v), S) + acc[v];
                 const unsigned long long nlo = lo + (unsigned long long)t;
                 hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
                 lo = nlo;
             }
-            if ((valid >> v) & 1u) h[v] = ldexpf(__ll2float_rn(acc[v]), -S);
+            if ((valid >> v) & 1u) h[v] = scaled_f32_of(acc[v], S);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

@@ -105,3 +105,45 @@ def test_int8(da, N, R):
     Q[1, 2:] = 127
     np.fill_diagonal(Q, rng.integers(-5000, 5000, N))
     _check_int8(da, Q, R, N, sample=None if N <= 1024 else 8)
+
+
+def test_fixed_point_conversion_matches_intrinsics(da):
+    """round(w 2^S), ties to even, in integer arithmetic (as the recompute
+    kernels evaluate it) against the 64-bit conversion instruction and an
+    exact host evaluation, over all exponents, subnormals, zeros and ties."""
+    rng = np.random.default_rng(11)
+    bits = rng.integers(0, 0x7F800000, 400_000, dtype=np.uint32)          # every finite magnitude
+    bits |= (rng.integers(0, 2, bits.size, dtype=np.uint32) << 31)
+    w = bits.view(np.float32)
+    ew = np.floor(np.log2(np.maximum(np.abs(w.astype(np.float64)), 2.0 ** -149))).astype(np.int64)
+    S = np.array([rng.integers(-170, 62 - e) for e in ew], np.int32)       # |w 2^S| < 2^62
+    # exact ties k + 1/2 and values just around them
+    k = rng.integers(0, 1 << 22, 20_000)
+    St = rng.integers(1, 40, k.size).astype(np.int32)
+    wt = np.ldexp((2 * k + 1).astype(np.float64), -St - 1).astype(np.float32)
+    w = np.concatenate([w, wt, np.nextafter(wt, np.float32(np.inf)), np.nextafter(wt, np.float32(-np.inf)),
+                        np.float32([0.0, -0.0, 1.5, 2.5, -2.5, 0.5, -0.5])])
+    S = np.concatenate([S, St, St, St, np.int32([0, 0, 0, 0, 0, 0, 0])])
+    got, ref = da.binding.da_diag_fixed(w, S)
+    assert np.array_equal(got, ref)
+    exact = np.rint(np.ldexp(w.astype(np.float64), S)).astype(np.int64)   # exact product, round half even
+    assert np.array_equal(got, exact)
+
+
+def test_scaled_float_conversion_matches_intrinsics(da):
+    """fl32(v) 2^-S (round to nearest even, then scale) in integer arithmetic
+    against __ll2float_rn + ldexpf, over every magnitude, ties, and results
+    that are subnormal or overflow."""
+    rng = np.random.default_rng(12)
+    mag = rng.integers(0, 63, 300_000)
+    v = (rng.integers(0, 1 << 62, mag.size, dtype=np.int64) >> (62 - mag)) * rng.choice([-1, 1], mag.size)
+    ties = np.array([(1 << 25) + 2, (1 << 25) + 6, (1 << 24) + 1, (1 << 24) + 3, (1 << 40) + (1 << 16),
+                     (1 << 40) + (3 << 16), (1 << 62), (1 << 62) - 1, 1, 0, -1], np.int64)
+    v = np.concatenate([v, ties, -ties])
+    S = rng.integers(-80, 200, v.size).astype(np.int32)
+    S[-2 * ties.size:] = rng.integers(-5, 60, 2 * ties.size)
+    got, ref = da.binding.da_diag_scaled(v, S)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    host = np.ldexp(v.astype(np.float32).astype(np.float64), -S.astype(np.int64))
+    normal = (np.abs(host) >= 2.0 ** -126) & (np.abs(host) < 2.0 ** 128)
+    assert np.array_equal(got[normal].astype(np.float64), host[normal])
