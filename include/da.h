@@ -134,6 +134,15 @@ da_status da_ctx_info(const da_ctx* ctx, int64_t* N, da_dtype* dtype);
  * step and replica).  Errors: DA_EINVAL. */
 da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);
 
+/* For shapes with G = 1 (the automatic choice up to N = 1024): on = 1 runs
+ * each replica as an annealer warp plus a producer warp that computes the
+ * acceptance draws of the coming steps (Philox words as log2 u) into shared
+ * memory, one replica per block, rpb ignored; on = 0 (the default) lets the
+ * annealer warp draw for itself while its row load is in flight.  Results
+ * are identical either way (each trial's decision equals the exact Metropolis
+ * test of Sec. II with the same u).  Errors: DA_EINVAL. */
+da_status da_set_draw_warp(da_ctx* ctx, int32_t on);
+
 /* Run the Digital Annealer (Algorithm 2) R times from x = 0 (all runs start
  * from one state, Sec. II) for `steps` iterations, blocking until done.
  *   beta_schedule  host, [steps] inverse temperature of every step (the
@@ -318,6 +327,14 @@ da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
  * u = ((w >> 8) + 1) 2^-24 with w[n] 32-bit Philox words. */
 da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n);
 da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n);
+/* The log-domain decision of the warp-specialised step (da_set_draw_warp):
+ * da_diag_log_uniform returns L[i] = log2 u (the hardware approximation the
+ * producer warp stores) for u = ((w[i] >> 8) + 1) 2^-24; da_diag_accept_log
+ * returns, per trial (delta[i], beta[i], w[i]), bit 0 = the kernel's accept
+ * decision and bit 1 = set when the trial fell in the band and was decided by
+ * the exact test delta <= 0 || u < exp_neg(-fl(beta delta)). */
+da_status da_diag_log_uniform(const uint32_t* w, float* L, int64_t n);
+da_status da_diag_accept_log(const float* delta, const float* beta, const uint32_t* w, uint8_t* out, int64_t n);
 /* The fixed-point conversions of the exact recompute (da_field_recompute) as
  * the kernels evaluate them, in integer arithmetic (got), beside the same
  * conversions through the 64-bit conversion instructions (ref):

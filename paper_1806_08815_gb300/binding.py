@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
     L.da_destroy.restype = None
     L.da_ctx_info.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int)]
     L.da_set_launch_shape.argtypes = [_P, i32, i32, i32]
+    L.da_set_draw_warp.argtypes = [_P, i32]
+    L.da_set_draw_warp.restype = ctypes.c_int
     L.da_anneal.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_result)]
     L.da_anneal_async.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_dev_result), _P]
     L.da_pt.argtypes = [_P, _P, i32, i64, i32, f32, u64, ctypes.POINTER(da_pt_result)]
@@ -112,6 +114,10 @@ def lib() -> ctypes.CDLL:
     L.da_diag_accept.argtypes = [_P, _P, _P, i64]
     L.da_diag_exp_band.restype = ctypes.c_int
     L.da_diag_accept.restype = ctypes.c_int
+    L.da_diag_log_uniform.argtypes = [_P, _P, i64]
+    L.da_diag_accept_log.argtypes = [_P, _P, _P, _P, i64]
+    L.da_diag_log_uniform.restype = ctypes.c_int
+    L.da_diag_accept_log.restype = ctypes.c_int
     L.da_diag_fixed.argtypes = [_P, _P, _P, _P, i64]
     L.da_diag_scaled.argtypes = [_P, _P, _P, _P, i64]
     L.da_diag_fixed.restype = ctypes.c_int
@@ -242,6 +248,10 @@ def da_pt(ctx: Context, betas: np.ndarray, sweeps: int, ladders: int, seed: int,
     return out
 
 
+def da_set_draw_warp(ctx: Context, on: bool) -> None:
+    _check(lib().da_set_draw_warp(ctx.handle, 1 if on else 0))
+
+
 def da_energy(ctx: Context, x: np.ndarray) -> np.ndarray:
     xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.uint32)
     E = np.zeros(xs.shape[0])
@@ -297,6 +307,23 @@ def da_diag_accept(x: np.ndarray, w: np.ndarray) -> np.ndarray:
     acc = np.empty(xs.size, np.uint8)
     _check(lib().da_diag_accept(_ptr(xs), _ptr(ws), _ptr(acc), xs.size))
     return acc
+
+
+def da_diag_log_uniform(w: np.ndarray) -> np.ndarray:
+    ws = np.ascontiguousarray(w, dtype=np.uint32).ravel()
+    L = np.empty(ws.size, np.float32)
+    _check(lib().da_diag_log_uniform(_ptr(ws), _ptr(L), ws.size))
+    return L
+
+
+def da_diag_accept_log(delta: np.ndarray, beta: np.ndarray, w: np.ndarray):
+    """(decision, in_band) of the warp-specialised step for each trial."""
+    d = np.ascontiguousarray(delta, dtype=np.float32).ravel()
+    b = np.ascontiguousarray(np.broadcast_to(beta, d.shape), dtype=np.float32).ravel()
+    ws = np.ascontiguousarray(w, dtype=np.uint32).ravel()
+    out = np.empty(d.size, np.uint8)
+    _check(lib().da_diag_accept_log(_ptr(d), _ptr(b), _ptr(ws), _ptr(out), d.size))
+    return (out & 1).astype(bool), (out & 2).astype(bool)
 
 
 def da_diag_fixed(w: np.ndarray, S: np.ndarray):

@@ -58,6 +58,7 @@ struct da_ctx {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     StepShape forced;  // V = 0: automatic
+    bool draw_warp = false;  // G = 1 shapes: a producer warp computes the acceptance draws
     // optional per-launch timing of the step kernel (da_profile_*)
     bool prof = false;
     std::vector<cudaEvent_t> prof_ev;  // pairs around step launches
@@ -89,8 +90,9 @@ StepShape auto_shape(int N)
 
 StepShape shape_for(const da_ctx* c)
 {
-    if (c->forced.V > 0) return c->forced;
-    return auto_shape(c->N);
+    StepShape s = c->forced.V > 0 ? c->forced : auto_shape(c->N);
+    s.ws = s.G == 1 && c->draw_warp;
+    return s;
 }
 
 da_status ensure_ws(da_ctx* c, size_t bytes)
@@ -184,6 +186,7 @@ StepParams base_params(const da_ctx* c, const RunBuffers& b)
     p.x = b.x();
     p.bestx = b.bestx();
     p.sc = b.sc();
+    p.err = c->tc.err;
     return p;
 }
 
@@ -205,15 +208,17 @@ da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
     return DA_OK;
 }
 
-// After a call's stream work has completed: a bounded wait inside the
-// tensor-core recompute that gave up invalidates the call's results.
+// After a call's stream work has completed: a bounded wait inside a kernel
+// (the tensor-core recompute's pipeline, the step's producer/annealer
+// handshake) that gave up invalidates the call's results.
 da_status check_tc(da_ctx* c)
 {
     int flag = 0;
     DA_CU(cudaMemcpy(&flag, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         DA_CU(cudaMemset(c->tc.err, 0, sizeof(int)));
-        return fail(DA_ETIMEOUT, "tensor-core recompute: a bounded wait on a pipeline barrier gave up");
+        return fail(DA_ETIMEOUT, flag == 2 ? "step kernel: a bounded wait on the draw ring gave up"
+                                           : "tensor-core recompute: a bounded wait on a pipeline barrier gave up");
     }
     return DA_OK;
 }
@@ -441,6 +446,14 @@ da_status da_ctx_info(const da_ctx* c, int64_t* N, da_dtype* dtype)
     if (da_status s = check_ctx(c)) return s;
     if (N) *N = c->N;
     if (dtype) *dtype = c->dtype;
+    return DA_OK;
+}
+
+da_status da_set_draw_warp(da_ctx* c, int32_t on)
+{
+    if (da_status s = check_ctx(c)) return s;
+    if (on != 0 && on != 1) return fail(DA_EINVAL, "on must be 0 or 1");
+    c->draw_warp = on != 0;
     return DA_OK;
 }
 

@@ -6,7 +6,7 @@
 // independently):
 //   Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed_lo, seed_hi).
 //   acceptance draw of trial i at step t of replica r:
-//       counter (32*(i/128) + i%32, t, r, 0), output lane (i%128)/32
+//       counter (i/4, t, r, 0), output lane i%4
 //   uniform choice of step t:   counter (0, t & ~3, r, 1), output lane t%4
 //   replica exchange after sweep s, pair p, ladder l:  counter (p, s, l, 2), lane 0
 //   u = ((word >> 8) + 1) * 2^-24, uniform on (0, 1] with 24-bit resolution.
@@ -128,6 +128,25 @@ __device__ __forceinline__ bool metropolis_accept(float x, uint32_t w)
     if (U < __fmul_rn(est, kBandLo)) return true;
     if (!(U < __fmul_rn(est, kBandHi))) return false;
     return __fmul_rn(U, 5.9604644775390625e-08f) < exp_neg(x);
+}
+
+// The same decision in the log domain, as the warp-specialised step makes it:
+// a producer warp stores L = log2 u (hardware approximation, lg2_uniform) for
+// every trial, and the annealer forms s = delta beta log2(e) + L with one
+// fused multiply-add.  u < exp(-beta delta) is s < 0 up to the error of L,
+// of exp_neg and of the roundings of beta log2(e) and of s, together far
+// below kLogBand for every argument (the tests bound each term); so
+// s < -kLogBand accepts, s >= kLogBand rejects, and only trials in between
+// (and delta <= 0 trials whose s falls there) take the exact test
+// delta <= 0 || u < exp_neg(x).
+constexpr float kLog2e = 1.44269504088896341f;
+constexpr float kLogBand = 3.0517578125e-05f;   // 2^-15
+
+__device__ __forceinline__ float lg2_uniform(uint32_t w)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(uniform01(w)));
+    return y;
 }
 
 // Arguments at or below this give exp_neg(x) <= 2^-24, which no u in (0, 1]

@@ -44,6 +44,27 @@ __global__ void accept_kernel(const float* x, const uint32_t* w, uint8_t* acc, l
     if (i < n) acc[i] = da::metropolis_accept(x[i], w[i]) ? 1 : 0;
 }
 
+__global__ void log_uniform_kernel(const uint32_t* w, float* L, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) L[i] = da::lg2_uniform(w[i]);
+}
+
+// The warp-specialised step's decision for one trial, as WarpReplica::step_log
+// makes it: bit 0 the decision, bit 1 set when it came from the exact test
+// (the trial's s fell in the band).
+__global__ void accept_log_kernel(const float* delta, const float* beta, const uint32_t* w, uint8_t* out, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float c = __fmul_rn(beta[i], da::kLog2e);
+    const float sv = __fmaf_rn(delta[i], c, da::lg2_uniform(w[i]));
+    bool acc = sv < -da::kLogBand;
+    const bool band = sv >= -da::kLogBand && sv < da::kLogBand;
+    if (band) acc = delta[i] <= 0.0f || da::uniform01(w[i]) < da::exp_neg(-__fmul_rn(beta[i], delta[i]));
+    out[i] = (uint8_t)((acc ? 1 : 0) | (band ? 2 : 0));
+}
+
 // The recompute's fixed-point conversions in integer arithmetic, beside the
 // same conversions written with the 64-bit conversion instructions.
 __global__ void fixed_kernel(const float* w, const int32_t* S, long long* got, long long* ref, long long n)
@@ -170,4 +191,29 @@ extern "C" da_status da_diag_scaled(const int64_t* v, const int32_t* S, float* g
     std::copy(out.begin(), out.begin() + n, got);
     std::copy(out.begin() + n, out.end(), ref);
     return DA_OK;
+}
+
+extern "C" da_status da_diag_log_uniform(const uint32_t* w, float* L, int64_t n)
+{
+    if (n < 0 || (n > 0 && (!w || !L))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    return run((size_t)n * 4, (size_t)n * 4, w, L, [&](void* a, void* b) {
+        log_uniform_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<const uint32_t*>(a), static_cast<float*>(b), n);
+    });
+}
+
+extern "C" da_status da_diag_accept_log(const float* delta, const float* beta, const uint32_t* w, uint8_t* out,
+                                        int64_t n)
+{
+    if (n < 0 || (n > 0 && (!delta || !beta || !w || !out))) return DA_EINVAL;
+    if (n == 0) return DA_OK;
+    std::vector<char> in((size_t)n * 12);
+    std::copy((const char*)delta, (const char*)delta + n * 4, in.begin());
+    std::copy((const char*)beta, (const char*)beta + n * 4, in.begin() + n * 4);
+    std::copy((const char*)w, (const char*)w + n * 4, in.begin() + n * 8);
+    return run((size_t)n * 12, (size_t)n, in.data(), out, [&](void* a, void* b) {
+        const float* da_ = static_cast<const float*>(a);
+        accept_log_kernel<<<(unsigned)((n + 255) / 256), 256>>>(da_, da_ + n, reinterpret_cast<const uint32_t*>(da_ + 2 * n),
+                                                                static_cast<uint8_t*>(b), n);
+    });
 }

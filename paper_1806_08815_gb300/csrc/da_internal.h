@@ -28,6 +28,7 @@ struct StepShape {
     int V = 0;
     int G = 0;
     int rpb = 0;  // replicas (groups) per block
+    bool ws = false;  // G = 1 only: one replica per block, with a producer warp for its draws
     int npad() const { return 32 * V * G; }
     int nwords() const { return V * G; }
 };
@@ -53,6 +54,7 @@ struct StepParams {
     long long t0 = 0, t1 = 0;     // steps [t0, t1)
     int* trace = nullptr;         // optional [R][trace_T]
     long long trace_T = 0;
+    int* err = nullptr;           // device flag, set to 2 when a bounded wait gives up
 };
 
 // Philox4x32-10 round keys k + r * Weyl (r = 0..9) of a seed.

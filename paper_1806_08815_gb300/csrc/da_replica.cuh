@@ -118,6 +118,50 @@ struct WarpReplica {
                 }
             }
         }
+        return choose_and_flip<FULL>(t, accm, keys, [&] {
+            if (draw_next) draw((uint32_t)(t + 1), keys);
+        });
+    }
+
+    // One step t whose acceptance draws arrive as L[v] = log2 u of this lane's
+    // trials (lg2_uniform, computed by a producer warp): s = delta beta log2(e) + L
+    // decides every trial outside the band |s| < kLogBand; inside it the exact
+    // test recomputes the trial's Philox word.  `overlap` runs while row k is
+    // in flight.
+    template <bool FULL, class Keys, class Overlap>
+    __device__ __forceinline__ int step_log(long long t, float beta, float inc, const float (&L)[V], const Keys& keys,
+                                            Overlap&& overlap)
+    {
+        const float Eoff = __fmul_rn(__uint2float_rn(m), inc);
+        const float c = __fmul_rn(beta, kLog2e);
+        uint32_t accm = 0, band = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
+            const float sv = __fmaf_rn(delta, c, L[v]);
+            accm |= (uint32_t)(sv < -kLogBand) << v;
+            band |= (uint32_t)(sv >= -kLogBand && sv < kLogBand) << v;
+        }
+        if (__any_sync(0xffffffffu, band != 0u)) {
+            while (band) {
+                const int v = __ffs(band) - 1;
+                band &= band - 1;
+                const float delta = A::delta(A::signed_field(select_slot<H, V>(h, v), (xm >> v) & 1u), Eoff);
+                const float ax = -__fmul_rn(beta, delta);
+                const uint32_t wd = pick(philox4x32_10((uint32_t)((base + v) >> 2), (uint32_t)t, rep, 0u, keys), v & 3);
+                accm |= (uint32_t)(delta <= 0.0f || uniform01(wd) < exp_neg(ax)) << v;
+            }
+        }
+        return choose_and_flip<FULL>(t, accm, keys, overlap);
+    }
+
+    // (c) of a step with acceptance mask accm: the best-state test left by the
+    // previous step, the uniform choice among the accepted trials, the flip
+    // and the field update; `overlap` runs while row k is in flight (or at
+    // once when nothing flips).  Returns the flipped index or -1.
+    template <bool FULL, class Keys, class Overlap>
+    __device__ __forceinline__ int choose_and_flip(long long t, uint32_t accm, const Keys& keys, Overlap&& overlap)
+    {
         if constexpr (!FULL) accm &= valid;
         flush_best();
 
@@ -126,7 +170,7 @@ struct WarpReplica {
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total == 0) {
             m += 1;
-            if (draw_next) draw((uint32_t)(t + 1), keys);
+            overlap();
             return -1;
         }
         const long long blk = t >> 2;
@@ -144,7 +188,7 @@ struct WarpReplica {
         const int k = own * V + vk;
         Tw cv[V];
         if (FULL || base < N) Row<Tw, V, CG>::load(W + (size_t)k * ldw + base, cv);
-        if (draw_next) draw((uint32_t)(t + 1), keys);
+        overlap();
         if (FULL || base < N) {
             const typename A::Sign sg = A::sign(xold);
 #pragma unroll

@@ -34,6 +34,7 @@
 #include "da_internal.h"
 #include "da_replica.cuh"
 #include "da_step_common.cuh"
+#include "da_tc.cuh"
 
 namespace da {
 namespace step_detail {
@@ -318,6 +319,124 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
     }
 }
 
+// G = 1 with warp specialisation: block = one replica = an annealer warp
+// (WarpReplica::step_log) and a producer warp that computes the acceptance
+// draws of the coming steps, L = log2 u for every trial, into a ring of
+// kWsRing shared-memory buffers.  The producer depends on nothing the
+// annealer computes, so it runs up to kWsRing steps ahead; the annealer reads
+// the next step's buffer while its row load is in flight.  Full/empty
+// handshakes are mbarriers whose waits are bounded (a wait that gives up
+// sets *p.err and ends the launch; the replica's results are then invalid,
+// and later launches that see the flag leave at once).
+constexpr int kWsRing = 4;
+constexpr uint32_t kWsWaitPolls = 1u << 26;
+constexpr uint64_t kWsWaitNs = 2000000000ull;
+
+template <typename Tw, int V, bool FULL, bool TRACE>
+__global__ void __launch_bounds__(64, 7) step_kernel_ws(const __grid_constant__ StepParams p)
+{
+    using R_ = WarpReplica<Tw, V>;
+    using H = typename R_::H;
+    constexpr int NQ = V / 4;
+    __shared__ float4 ring[kWsRing][NQ][32];
+    __shared__ uint64_t full[kWsRing], empty[kWsRing];
+    __shared__ int failed;
+    const int r = blockIdx.x;
+    if (r >= p.R) return;   // whole block
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kWsRing; ++b) {
+            tc::mbar_init(&full[b], 32);
+            tc::mbar_init(&empty[b], 32);
+        }
+        failed = p.err ? *reinterpret_cast<volatile int*>(p.err) : 0;
+    }
+    __syncthreads();
+    if (failed) return;     // whole block
+    const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
+    const uint32_t rep = p.rep_base + (uint32_t)r;
+    const long long n = p.t1 - p.t0;
+
+    if (warp == 1) {   // producer: draws of steps t0 .. t1 - 1, in order
+        const uint32_t q0 = (uint32_t)(lane * V) >> 2;
+        for (long long i = 0; i < n; ++i) {
+            const int b = (int)(i % kWsRing);
+            const uint32_t ph = (uint32_t)(i / kWsRing);
+            if (ph > 0 && !tc::mbar_wait(&empty[b], (ph - 1) & 1u, kWsWaitPolls, kWsWaitNs)) {
+                if (p.err) atomicExch(p.err, 2);
+                break;
+            }
+            const uint32_t tt = (uint32_t)(p.t0 + i);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const u32x4 w = philox4x32_10(q0 + q, tt, rep, 0u, keys);
+                ring[b][q][lane] = make_float4(lg2_uniform(w.x), lg2_uniform(w.y), lg2_uniform(w.z), lg2_uniform(w.w));
+            }
+            tc::mbar_arrive(&full[b]);
+        }
+        return;
+    }
+
+    R_ rp;
+    rp.init(static_cast<const Tw*>(p.W), p.N, p.ldw, rep, p.bestx + (size_t)r * p.nw);
+    H* hg = static_cast<H*>(p.h) + (size_t)r * p.npad + rp.base;
+    uint32_t* xg = p.x + (size_t)r * p.nw;
+#pragma unroll
+    for (int v = 0; v < V; ++v) rp.h[v] = hg[v];
+    rp.xm = (xg[rp.base >> 5] >> (rp.base & 31)) & R_::VMASK;
+    ReplicaScalars sc = p.sc[r];
+    rp.Ecur = Arith<Tw>::load_e(sc.E);
+    rp.Ebest = Arith<Tw>::load_e(sc.best);
+    rp.flips = sc.flips;
+    rp.m = sc.m;
+    rp.chk = sc.check != 0;
+    const bool per_rep = p.betas != nullptr;
+    const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
+
+    float L[V];
+    bool ok = true;
+    auto fetch = [&](long long i) {   // the draws of step t0 + i, then release the buffer
+        const int b = (int)(i % kWsRing);
+        if (!tc::mbar_wait(&full[b], (uint32_t)(i / kWsRing) & 1u, kWsWaitPolls, kWsWaitNs)) {
+            ok = false;
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float4 f = ring[b][q][lane];
+            L[4 * q] = f.x; L[4 * q + 1] = f.y; L[4 * q + 2] = f.z; L[4 * q + 3] = f.w;
+        }
+        tc::mbar_arrive(&empty[b]);
+    };
+    if (n > 0) fetch(0);
+    float beta_next = (!per_rep && n > 0) ? p.beta[p.t0] : beta_rep;
+    for (long long i = 0; i < n && __all_sync(0xffffffffu, ok); ++i) {
+        const long long t = p.t0 + i;
+        const float beta = beta_next;
+        if (!per_rep && i + 1 < n) beta_next = p.beta[t + 1];
+        const int k = rp.template step_log<FULL>(t, beta, p.inc, L, keys, [&] {
+            if (i + 1 < n) fetch(i + 1);
+        });
+        if constexpr (TRACE) {
+            if (lane == 0) p.trace[(size_t)r * p.trace_T + t] = k;
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0 && p.err) atomicExch(p.err, 2);
+#pragma unroll
+    for (int v = 0; v < V; ++v) hg[v] = rp.h[v];
+    const uint32_t word = rp.word();
+    if (lane % R_::P == 0) xg[rp.base >> 5] = word;
+    if (lane == 0) {
+        sc.E = Arith<Tw>::store_e(rp.Ecur);
+        sc.best = Arith<Tw>::store_e(rp.Ebest);
+        sc.flips = rp.flips;
+        sc.m = rp.m;
+        sc.check = rp.chk ? 1u : 0u;
+        p.sc[r] = sc;
+    }
+}
+
 template <typename Tw, int V, int G>
 cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)
 {
@@ -327,6 +446,16 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
     if (blocks == 0) return cudaSuccess;
     const bool full = p.N == 32 * V * G;
     if constexpr (G == 1) {
+        if (s.ws) {
+            if (full) {
+                if (trace) step_kernel_ws<Tw, V, true, true><<<p.R, 64, 0, st>>>(p);
+                else step_kernel_ws<Tw, V, true, false><<<p.R, 64, 0, st>>>(p);
+            } else {
+                if (trace) step_kernel_ws<Tw, V, false, true><<<p.R, 64, 0, st>>>(p);
+                else step_kernel_ws<Tw, V, false, false><<<p.R, 64, 0, st>>>(p);
+            }
+            return cudaGetLastError();
+        }
         if (full) {
             if (trace) step_kernel_g1<Tw, V, true, true><<<blocks, threads, 0, st>>>(p);
             else step_kernel_g1<Tw, V, true, false><<<blocks, threads, 0, st>>>(p);

@@ -121,6 +121,50 @@ def test_accept_decision_matches_definition(da):
     assert np.array_equal(got, ref)
 
 
+def test_log_uniform_error_bound(da):
+    """L = log2 u as the producer warp stores it, for every one of the 2^24 values
+    of u: its error against log2 u in fp64 (about one fp32 ulp of L, at most
+    2^-19 near L = -24) is far inside the decision band 2^-15."""
+    U = np.arange(1, 2 ** 24 + 1, dtype=np.int64)
+    w = ((U - 1) << 8).astype(np.uint32)
+    L = da.binding.da_diag_log_uniform(w)
+    err = np.abs(L.astype(np.float64) - (np.log2(U.astype(np.float64)) - 24.0))
+    assert err.max() < 2.0 ** -18
+    assert L[-1] == 0.0
+
+
+def test_log_domain_decision_matches_exact_test(da):
+    """The warp-specialised step decides s = delta beta log2(e) + log2 u against
+    the band 2^-15 and falls back to the exact test inside it: for trials placed
+    right at the acceptance boundary (relative offsets 2^-30 .. 2^-8 either side),
+    random trials, delta <= 0, beta = 0 and u = 1 its decision equals
+    delta <= 0 || u < exp_neg(-fl(beta delta))."""
+    import oracle
+    rng = np.random.default_rng(7)
+    n = 1 << 22
+    U = rng.integers(1, 2 ** 24 + 1, n)
+    beta = np.exp(rng.uniform(np.log(0.01), np.log(50.0), n)).astype(np.float32)
+    rho = rng.choice([-1.0, 1.0], n) * 2.0 ** -rng.uniform(8, 30, n)
+    delta = (-np.log(U * 2.0 ** -24) / beta.astype(np.float64) * (1 + rho)).astype(np.float32)
+    m = 1 << 20
+    U2 = rng.integers(1, 2 ** 24 + 1, m)
+    b2 = rng.uniform(0, 20, m).astype(np.float32)
+    b2[:1000] = 0.0
+    d2 = rng.normal(0, 3, m).astype(np.float32)
+    d2[1000:2000] = 0.0
+    d2[2000:3000] = -0.0
+    U2[3000:4000] = 2 ** 24
+    U = np.concatenate([U, U2])
+    beta = np.concatenate([beta, b2])
+    delta = np.concatenate([delta, d2])
+    w = (((U - 1) << 8) | rng.integers(0, 256, U.size)).astype(np.uint32)
+    got, band = da.binding.da_diag_accept_log(delta, beta, w)
+    x = np.minimum(-(beta * delta), np.float32(0.0)).astype(np.float32)    # fp32 product
+    exact = (delta <= 0) | (U * 2.0 ** -24 < oracle.expf(x).astype(np.float64))
+    assert np.array_equal(got, exact)
+    assert band[n:].mean() < 1e-3        # typical trials rarely need the exact test
+
+
 def test_device_philox_matches_oracle(da):
     import oracle
     rng = np.random.default_rng(1)
@@ -163,6 +207,21 @@ def test_int8_ragged_sizes_all_shapes(da, inst, N, shape):
     got = da.da_anneal(ctx, beta, 0.5, 13, 7, trace=True)
     ref = oracle.da_anneal(q.Q, beta, R=13, seed=7, inc=0.5, trace=True, nthreads=NT)
     _compare_anneal(got, ref, q.Q, True)
+
+
+@pytest.mark.parametrize("N,dtype", [(33, "i8"), (100, "i8"), (700, "i8"), (1024, "f32"), (200, "f32")])
+def test_draw_warp_on_and_off(da, inst, N, dtype):
+    """The G = 1 step with and without its producer warp: both reproduce the oracle."""
+    import oracle
+    q = inst.sk_bimodal(N, N) if dtype == "i8" else inst.sk_gaussian(N, N)
+    beta = inst.beta_linear(0.05, 4.0 if dtype == "i8" else 9.0, 1500)
+    rec = 0 if dtype == "i8" else 512
+    ref = oracle.da_anneal(q.Q, beta, R=9, seed=4, inc=0.5, recompute_every=rec, trace=True, nthreads=NT)
+    for on in (True, False):
+        ctx = da.da_create(q.Q)
+        da.binding.da_set_draw_warp(ctx, on)
+        got = da.da_anneal(ctx, beta, 0.5, 9, 4, recompute_every=rec, trace=True)
+        _compare_anneal(got, ref, q.Q, dtype == "i8")
 
 
 @pytest.mark.parametrize("N,shape", [(300, (0, 0, 0)), (300, (16, 1, 2)), (1000, (0, 0, 0)), (1000, (8, 4, 1)),
