@@ -327,9 +327,9 @@ da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
  * u = ((w >> 8) + 1) 2^-24 with w[n] 32-bit Philox words. */
 da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n);
 da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n);
-/* The log-domain decision of the warp-specialised step (da_set_draw_warp):
- * da_diag_log_uniform returns L[i] = log2 u (the hardware approximation the
- * producer warp stores) for u = ((w[i] >> 8) + 1) 2^-24; da_diag_accept_log
+/* The log-domain decision of the step kernels: da_diag_log_uniform returns
+ * L[i] = log2 U (the hardware approximation the kernels keep for every draw)
+ * for U = (w[i] >> 8) + 1, i.e. u = U 2^-24; da_diag_accept_log
  * returns, per trial (delta[i], beta[i], w[i]), bit 0 = the kernel's accept
  * decision and bit 1 = set when the trial fell in the band and was decided by
  * the exact test delta <= 0 || u < exp_neg(-fl(beta delta)). */

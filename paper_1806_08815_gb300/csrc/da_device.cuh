@@ -130,22 +130,23 @@ __device__ __forceinline__ bool metropolis_accept(float x, uint32_t w)
     return __fmul_rn(U, 5.9604644775390625e-08f) < exp_neg(x);
 }
 
-// The same decision in the log domain, as the warp-specialised step makes it:
-// a producer warp stores L = log2 u (hardware approximation, lg2_uniform) for
-// every trial, and the annealer forms s = delta beta log2(e) + L with one
-// fused multiply-add.  u < exp(-beta delta) is s < 0 up to the error of L,
-// of exp_neg and of the roundings of beta log2(e) and of s, together far
-// below kLogBand for every argument (the tests bound each term); so
-// s < -kLogBand accepts, s >= kLogBand rejects, and only trials in between
-// (and delta <= 0 trials whose s falls there) take the exact test
+// The same decision in the log domain, as the step kernels make it: every
+// trial's draw is kept as Lg = log2 U (hardware approximation, lg2_draw),
+// U = (w >> 8) + 1 in [1, 2^24], and the annealer forms s = delta beta log2(e)
+// + Lg with one fused multiply-add.  u < exp(-beta delta) is s < 24 up to the
+// error of Lg, of exp_neg and of the roundings of beta log2(e) and of s,
+// together far below 2^-15 for every argument (the tests bound each term); so
+// s < kLogLo accepts, s >= kLogHi rejects, and only trials in between (and
+// delta <= 0 trials whose s falls there) take the exact test
 // delta <= 0 || u < exp_neg(x).
 constexpr float kLog2e = 1.44269504088896341f;
-constexpr float kLogBand = 3.0517578125e-05f;   // 2^-15
+constexpr float kLogLo = 24.0f - 3.0517578125e-05f;   // 24 -+ 2^-15 (exact in fp32)
+constexpr float kLogHi = 24.0f + 3.0517578125e-05f;
 
-__device__ __forceinline__ float lg2_uniform(uint32_t w)
+__device__ __forceinline__ float lg2_draw(uint32_t w)
 {
     float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(uniform01(w)));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__uint2float_rn((w >> 8) + 1u)));
     return y;
 }
 

@@ -47,7 +47,7 @@ __global__ void accept_kernel(const float* x, const uint32_t* w, uint8_t* acc, l
 __global__ void log_uniform_kernel(const uint32_t* w, float* L, long long n)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) L[i] = da::lg2_uniform(w[i]);
+    if (i < n) L[i] = da::lg2_draw(w[i]);
 }
 
 // The warp-specialised step's decision for one trial, as WarpReplica::step_log
@@ -58,9 +58,9 @@ __global__ void accept_log_kernel(const float* delta, const float* beta, const u
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float c = __fmul_rn(beta[i], da::kLog2e);
-    const float sv = __fmaf_rn(delta[i], c, da::lg2_uniform(w[i]));
-    bool acc = sv < -da::kLogBand;
-    const bool band = sv >= -da::kLogBand && sv < da::kLogBand;
+    const float sv = __fmaf_rn(delta[i], c, da::lg2_draw(w[i]));
+    bool acc = sv < da::kLogLo;
+    const bool band = sv >= da::kLogLo && sv < da::kLogHi;
     if (band) acc = delta[i] <= 0.0f || da::uniform01(w[i]) < da::exp_neg(-__fmul_rn(beta[i], delta[i]));
     out[i] = (uint8_t)((acc ? 1 : 0) | (band ? 2 : 0));
 }

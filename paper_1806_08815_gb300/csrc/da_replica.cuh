@@ -29,7 +29,7 @@ struct WarpReplica {
     static constexpr int P = 32 / V;
 
     H h[V];
-    u32x4 rr[NQ];
+    float lg[V];      // log2 U of this lane's draws for the current step (lg2_draw)
     u32x4 cr;
     long long cr_blk;
     uint32_t xm, valid, m;
@@ -83,51 +83,30 @@ struct WarpReplica {
     __device__ __forceinline__ void draw(uint32_t tt, const Keys& keys)
     {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) rr[q] = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+        for (int q = 0; q < NQ; ++q) {
+            const u32x4 w = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+            lg[4 * q] = lg2_draw(w.x);
+            lg[4 * q + 1] = lg2_draw(w.y);
+            lg[4 * q + 2] = lg2_draw(w.z);
+            lg[4 * q + 3] = lg2_draw(w.w);
+        }
     }
 
-    // One step t (the draws of t are in rr).  If draw_next, the draws of t + 1
+    // One step t (the draws of t are in lg).  If draw_next, the draws of t + 1
     // are computed while row k is in flight.  Returns the flipped index or -1.
     template <bool FULL, class Keys>
     __device__ __forceinline__ int step(long long t, bool draw_next, float beta, float inc, const Keys& keys)
     {
-        const float Eoff = __fmul_rn(__uint2float_rn(m), inc);
-        uint32_t accm = 0, band = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const H dE = A::signed_field(h[v], (xm >> v) & 1u);
-            const float delta = A::delta(dE, Eoff);
-            const float ax = -__fmul_rn(beta, delta);
-            const uint32_t wd = pick(rr[v >> 2], v & 3);
-            const float est = exp_estimate(ax);
-            const float U = __uint2float_rn((wd >> 8) + 1u);
-            const bool le0 = delta <= 0.0f;
-            // below kExpCut the band lies under U >= 1, so no cut test is needed
-            const bool sure = U < __fmul_rn(est, kBandLo);
-            const bool maybe = U < __fmul_rn(est, kBandHi);
-            accm |= (uint32_t)(le0 || sure) << v;
-            band |= (uint32_t)(!le0 && !sure && maybe) << v;
-        }
-        if (__any_sync(0xffffffffu, band != 0u)) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if ((band >> v) & 1u) {
-                    const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
-                    const float ax = -__fmul_rn(beta, delta);
-                    accm |= (uint32_t)(uniform01(pick(rr[v >> 2], v & 3)) < exp_neg(ax)) << v;
-                }
-            }
-        }
-        return choose_and_flip<FULL>(t, accm, keys, [&] {
+        return step_log<FULL>(t, beta, inc, lg, keys, [&] {
             if (draw_next) draw((uint32_t)(t + 1), keys);
         });
     }
 
-    // One step t whose acceptance draws arrive as L[v] = log2 u of this lane's
-    // trials (lg2_uniform, computed by a producer warp): s = delta beta log2(e) + L
-    // decides every trial outside the band |s| < kLogBand; inside it the exact
-    // test recomputes the trial's Philox word.  `overlap` runs while row k is
-    // in flight.
+    // One step t whose acceptance draws are L[v] = log2 U of this lane's trials
+    // (lg2_draw; from draw() or from a producer warp): s = delta beta log2(e) + L
+    // decides every trial outside the band [kLogLo, kLogHi); inside it the
+    // exact test recomputes the trial's Philox word.  `overlap` runs while row
+    // k is in flight.
     template <bool FULL, class Keys, class Overlap>
     __device__ __forceinline__ int step_log(long long t, float beta, float inc, const float (&L)[V], const Keys& keys,
                                             Overlap&& overlap)
@@ -139,8 +118,8 @@ struct WarpReplica {
         for (int v = 0; v < V; ++v) {
             const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
             const float sv = __fmaf_rn(delta, c, L[v]);
-            accm |= (uint32_t)(sv < -kLogBand) << v;
-            band |= (uint32_t)(sv >= -kLogBand && sv < kLogBand) << v;
+            accm |= (uint32_t)(sv < kLogLo) << v;
+            band |= (uint32_t)(sv >= kLogLo && sv < kLogHi) << v;
         }
         if (__any_sync(0xffffffffu, band != 0u)) {
             while (band) {

@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
 
 // G = 1 with warp specialisation: block = one replica = an annealer warp
 // (WarpReplica::step_log) and a producer warp that computes the acceptance
-// draws of the coming steps, L = log2 u for every trial, into a ring of
+// draws of the coming steps, L = log2 U for every trial, into a ring of
 // kWsRing shared-memory buffers.  The producer depends on nothing the
 // annealer computes, so it runs up to kWsRing steps ahead; the annealer reads
 // the next step's buffer while its row load is in flight.  Full/empty
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(64, 7) step_kernel_ws(const __grid_constant__ 
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const u32x4 w = philox4x32_10(q0 + q, tt, rep, 0u, keys);
-                ring[b][q][lane] = make_float4(lg2_uniform(w.x), lg2_uniform(w.y), lg2_uniform(w.z), lg2_uniform(w.w));
+                ring[b][q][lane] = make_float4(lg2_draw(w.x), lg2_draw(w.y), lg2_draw(w.z), lg2_draw(w.w));
             }
             tc::mbar_arrive(&full[b]);
         }

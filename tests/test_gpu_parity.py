@@ -122,20 +122,20 @@ def test_accept_decision_matches_definition(da):
 
 
 def test_log_uniform_error_bound(da):
-    """L = log2 u as the producer warp stores it, for every one of the 2^24 values
-    of u: its error against log2 u in fp64 (about one fp32 ulp of L, at most
-    2^-19 near L = -24) is far inside the decision band 2^-15."""
+    """log2 U as the step kernels keep it for every draw, for each of the 2^24
+    values of U = (w >> 8) + 1: its error against log2 U in fp64 (about one fp32
+    ulp, at most 2^-19 near 24) is far inside the decision band 2^-15."""
     U = np.arange(1, 2 ** 24 + 1, dtype=np.int64)
     w = ((U - 1) << 8).astype(np.uint32)
     L = da.binding.da_diag_log_uniform(w)
-    err = np.abs(L.astype(np.float64) - (np.log2(U.astype(np.float64)) - 24.0))
+    err = np.abs(L.astype(np.float64) - np.log2(U.astype(np.float64)))
     assert err.max() < 2.0 ** -18
-    assert L[-1] == 0.0
+    assert L[0] == 0.0 and L[-1] == 24.0
 
 
 def test_log_domain_decision_matches_exact_test(da):
-    """The warp-specialised step decides s = delta beta log2(e) + log2 u against
-    the band 2^-15 and falls back to the exact test inside it: for trials placed
+    """The step kernels decide s = delta beta log2(e) + log2 U against 24 -+ 2^-15
+    and fall back to the exact test inside that band: for trials placed
     right at the acceptance boundary (relative offsets 2^-30 .. 2^-8 either side),
     random trials, delta <= 0, beta = 0 and u = 1 its decision equals
     delta <= 0 || u < exp_neg(-fl(beta delta))."""
