@@ -96,13 +96,20 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
         const uint32_t word = gather_word<V>(xm, lane);
         if (lane % P == 0) bestg[word_of_lane] = word;
     };
-    // Acceptance draws of one step: block q covers variables base + 4q .. + 3.
-    auto draw_step = [&](u32x4 (&rr)[NQ], uint32_t tt) {
+    // Acceptance draws of one step as log2 U (lg2_draw): Philox block q covers
+    // variables base + 4q .. + 3.
+    auto draw_step = [&](float (&lg)[V], uint32_t tt) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) rr[q] = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+        for (int q = 0; q < NQ; ++q) {
+            const u32x4 w4 = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+            lg[4 * q] = lg2_draw(w4.x);
+            lg[4 * q + 1] = lg2_draw(w4.y);
+            lg[4 * q + 2] = lg2_draw(w4.z);
+            lg[4 * q + 3] = lg2_draw(w4.w);
+        }
     };
-    u32x4 rr[NQ];
-    if (p.t0 < p.t1) draw_step(rr, (uint32_t)p.t0);
+    float lg[V];
+    if (p.t0 < p.t1) draw_step(lg, (uint32_t)p.t0);
 
     float beta_next = (!per_rep && p.t0 < p.t1) ? p.beta[p.t0] : beta_rep;
     for (long long t = p.t0; t < p.t1; ++t) {
@@ -110,33 +117,26 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
         if (!per_rep && t + 1 < p.t1) beta_next = p.beta[t + 1];
         const float Eoff = __fmul_rn(__uint2float_rn(m), p.inc);
 
-        // (a) + (b): every trial of this lane, branch-free except for the rare
-        // draws that fall inside the band of the exp estimate.
+        // (a) + (b): every trial of this lane in the log domain (lg2_draw),
+        // branch-free except for the rare trials inside the band, which take the
+        // exact test with their Philox word recomputed.
+        const float c = __fmul_rn(beta, kLog2e);
         uint32_t accm = 0, band = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const H dE = A::signed_field(h[v], (xm >> v) & 1u);
-            const float delta = A::delta(dE, Eoff);
-            const float ax = -__fmul_rn(beta, delta);
-            const uint32_t wd = pick(rr[v >> 2], v & 3);
-            const float est = exp_estimate(ax);
-            const float U = __uint2float_rn((wd >> 8) + 1u);
-            const bool le0 = delta <= 0.0f;
-            const bool need = !le0 && ax > kExpCut;
-            const bool sure = U < __fmul_rn(est, kBandLo);
-            const bool maybe = U < __fmul_rn(est, kBandHi);
-            accm |= (uint32_t)(le0 || (need && sure)) << v;
-            band |= (uint32_t)(need && !sure && maybe) << v;
+            const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
+            const float sv = __fmaf_rn(delta, c, lg[v]);
+            accm |= (uint32_t)(sv < kLogLo) << v;
+            band |= (uint32_t)(sv >= kLogLo && sv < kLogHi) << v;
         }
         if (__any_sync(0xffffffffu, band != 0u)) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if ((band >> v) & 1u) {
-                    const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
-                    const float ax = -__fmul_rn(beta, delta);
-                    const float u = uniform01(pick(rr[v >> 2], v & 3));
-                    accm |= (uint32_t)(u < exp_neg(ax)) << v;
-                }
+            while (band) {
+                const int v = __ffs(band) - 1;
+                band &= band - 1;
+                const float delta = A::delta(A::signed_field(select_slot<H, V>(h, v), (xm >> v) & 1u), Eoff);
+                const float ax = -__fmul_rn(beta, delta);
+                const uint32_t wd = pick(philox4x32_10((uint32_t)((base + v) >> 2), (uint32_t)t, rep, 0u, keys), v & 3);
+                accm |= (uint32_t)(delta <= 0.0f || uniform01(wd) < exp_neg(ax)) << v;
             }
         }
         if constexpr (!FULL) accm &= valid;
@@ -215,10 +215,7 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
 
         if (k >= 0) {
             // Delta E_k from the owner's registers
-            H gk = h[0];
-#pragma unroll
-            for (int v = 1; v < V; ++v)
-                if (v == vk) gk = h[v];
+            const H gk = select_slot<H, V>(h, vk);
             H dEk = 0;
             if constexpr (G == 1) {
                 dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own_lane);
@@ -229,10 +226,11 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
             if (FULL || base < p.N) Row<Tw, V>::load(Wm + (size_t)k * p.ldw + base, cv);
             // the next step's draws do not depend on row k: compute them while
             // its loads are in flight
-            if (t + 1 < p.t1) draw_step(rr, (uint32_t)(t + 1));
+            if (t + 1 < p.t1) draw_step(lg, (uint32_t)(t + 1));
             if (FULL || base < p.N) {
+                const typename A::Sign sg = A::sign(xold);
 #pragma unroll
-                for (int v = 0; v < V; ++v) h[v] = A::apply(h[v], cv[v], xold != 0u);
+                for (int v = 0; v < V; ++v) h[v] = A::apply_signed(h[v], cv[v], sg);
             }
             if (w == own_warp && lane == own_lane) xm ^= 1u << vk;
             ++flips;
@@ -241,7 +239,7 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
                 if (Ecur < Ebest) { Ebest = Ecur; snapshot(); }
             }
         } else if (t + 1 < p.t1) {
-            draw_step(rr, (uint32_t)(t + 1));
+            draw_step(lg, (uint32_t)(t + 1));
         }
         if constexpr (G > 1) pending = k >= 0;
         if constexpr (TRACE) {
