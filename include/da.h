@@ -321,12 +321,6 @@ int64_t da_static_pitch(int64_t N);
  * implementations.  Errors: DA_EINVAL, DA_ECUDA. */
 da_status da_diag_expf(const float* x, float* y, int64_t n);
 da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
-/* The kernels decide u < exp(x) first against a band around a fast hardware
- * estimate of 2^24 exp(x): da_diag_exp_band returns the band edges lo[n],
- * hi[n] for x[n]; da_diag_accept returns the full decision acc[n] (0/1) for
- * u = ((w >> 8) + 1) 2^-24 with w[n] 32-bit Philox words. */
-da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n);
-da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n);
 /* The log-domain decision of the step kernels: da_diag_log_uniform returns
  * L[i] = log2 U (the hardware approximation the kernels keep for every draw)
  * for U = (w[i] >> 8) + 1, i.e. u = U 2^-24; da_diag_accept_log

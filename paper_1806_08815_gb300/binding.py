@@ -110,10 +110,6 @@ def lib() -> ctypes.CDLL:
     L.da_anneal_static.restype = ctypes.c_int
     L.da_static_pitch.argtypes = [i64]
     L.da_static_pitch.restype = i64
-    L.da_diag_exp_band.argtypes = [_P, _P, _P, i64]
-    L.da_diag_accept.argtypes = [_P, _P, _P, i64]
-    L.da_diag_exp_band.restype = ctypes.c_int
-    L.da_diag_accept.restype = ctypes.c_int
     L.da_diag_log_uniform.argtypes = [_P, _P, i64]
     L.da_diag_accept_log.argtypes = [_P, _P, _P, _P, i64]
     L.da_diag_log_uniform.restype = ctypes.c_int
@@ -291,22 +287,6 @@ def da_profile_read(ctx: Context):
     ms = ctypes.c_double()
     _check(lib().da_profile_read(ctx.handle, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
-
-
-def da_diag_exp_band(x: np.ndarray):
-    xs = np.ascontiguousarray(x, dtype=np.float32).ravel()
-    lo = np.empty_like(xs)
-    hi = np.empty_like(xs)
-    _check(lib().da_diag_exp_band(_ptr(xs), _ptr(lo), _ptr(hi), xs.size))
-    return lo, hi
-
-
-def da_diag_accept(x: np.ndarray, w: np.ndarray) -> np.ndarray:
-    xs = np.ascontiguousarray(x, dtype=np.float32).ravel()
-    ws = np.ascontiguousarray(w, dtype=np.uint32).ravel()
-    acc = np.empty(xs.size, np.uint8)
-    _check(lib().da_diag_accept(_ptr(xs), _ptr(ws), _ptr(acc), xs.size))
-    return acc
 
 
 def da_diag_log_uniform(w: np.ndarray) -> np.ndarray:

@@ -100,37 +100,8 @@ __device__ __forceinline__ float exp_neg(float x)
     return __fmul_rn(p, scale);
 }
 
-// exp(x) from the hardware 2^x approximation: an estimate whose relative
-// error against exp_neg is far below 2^-16 over (kExpCut, 0] (verified for
-// every fp32 argument there by the tests).
-__device__ __forceinline__ float exp_estimate(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fmul_rn(x, 1.44269504088896341f)));
-    return y;
-}
-
-// 2^24 (1 -+ 2^-16): the band around the estimate outside which the
-// comparison with u = U 2^-24 is already decided.
-constexpr float kBandLo = 16776960.0f;
-constexpr float kBandHi = 16777472.0f;
-
-// The Metropolis test u < exp_neg(x) for u = ((w >> 8) + 1) 2^-24 and
-// kExpCut < x <= 0, decided exactly: with U = (w >> 8) + 1 (exact in fp32),
-// U < est 2^24 (1 - 2^-16) <= exp_neg(x) 2^24 means accept, and
-// U >= est 2^24 (1 + 2^-16) >= exp_neg(x) 2^24 means reject; only the rare U
-// inside the band evaluates exp_neg.  Same result as
-// uniform01(w) < exp_neg(x) for every input.
-__device__ __forceinline__ bool metropolis_accept(float x, uint32_t w)
-{
-    const float est = exp_estimate(x);
-    const float U = __uint2float_rn((w >> 8) + 1u);
-    if (U < __fmul_rn(est, kBandLo)) return true;
-    if (!(U < __fmul_rn(est, kBandHi))) return false;
-    return __fmul_rn(U, 5.9604644775390625e-08f) < exp_neg(x);
-}
-
-// The same decision in the log domain, as the step kernels make it: every
+// The Metropolis test u < exp_neg(x), x = -beta delta, as the step kernels
+// make it, in the log domain: every
 // trial's draw is kept as Lg = log2 U (hardware approximation, lg2_draw),
 // U = (w >> 8) + 1 in [1, 2^24], and the annealer forms s = delta beta log2(e)
 // + Lg with one fused multiply-add.  u < exp(-beta delta) is s < 24 up to the

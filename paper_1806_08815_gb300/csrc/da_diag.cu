@@ -29,21 +29,6 @@ __global__ void philox_kernel(const uint32_t* in, uint32_t* out, long long n)
     out[4 * i + 3] = r.w;
 }
 
-__global__ void band_kernel(const float* x, float* lo, float* hi, long long n)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float est = da::exp_estimate(x[i]);
-    lo[i] = __fmul_rn(est, da::kBandLo);
-    hi[i] = __fmul_rn(est, da::kBandHi);
-}
-
-__global__ void accept_kernel(const float* x, const uint32_t* w, uint8_t* acc, long long n)
-{
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < n) acc[i] = da::metropolis_accept(x[i], w[i]) ? 1 : 0;
-}
-
 __global__ void log_uniform_kernel(const uint32_t* w, float* L, long long n)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -123,35 +108,6 @@ extern "C" da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int6
     if (n == 0) return DA_OK;
     return run((size_t)n * 24, (size_t)n * 16, ctr_key, out, [&](void* a, void* b) {
         philox_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<const uint32_t*>(a), static_cast<uint32_t*>(b), n);
-    });
-}
-
-extern "C" da_status da_diag_exp_band(const float* x, float* lo, float* hi, int64_t n)
-{
-    if (n < 0 || (n > 0 && (!x || !lo || !hi))) return DA_EINVAL;
-    if (n == 0) return DA_OK;
-    std::vector<float> out((size_t)n * 2);
-    da_status s = run((size_t)n * 4, (size_t)n * 8, x, out.data(), [&](void* a, void* b) {
-        float* o = static_cast<float*>(b);
-        band_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<const float*>(a), o, o + n, n);
-    });
-    if (s != DA_OK) return s;
-    std::copy(out.begin(), out.begin() + n, lo);
-    std::copy(out.begin() + n, out.end(), hi);
-    return DA_OK;
-}
-
-extern "C" da_status da_diag_accept(const float* x, const uint32_t* w, uint8_t* acc, int64_t n)
-{
-    if (n < 0 || (n > 0 && (!x || !w || !acc))) return DA_EINVAL;
-    if (n == 0) return DA_OK;
-    std::vector<char> in((size_t)n * 8);
-    std::copy((const char*)x, (const char*)x + n * 4, in.begin());
-    std::copy((const char*)w, (const char*)w + n * 4, in.begin() + n * 4);
-    return run((size_t)n * 8, (size_t)n, in.data(), acc, [&](void* a, void* b) {
-        const float* xa = static_cast<const float*>(a);
-        accept_kernel<<<(unsigned)((n + 255) / 256), 256>>>(xa, reinterpret_cast<const uint32_t*>(xa + n),
-                                                            static_cast<uint8_t*>(b), n);
     });
 }
 

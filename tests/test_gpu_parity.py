@@ -67,60 +67,6 @@ def test_device_exp_matches_oracle_exhaustively(da):
     assert np.array_equal(da.binding.da_diag_expf(x).view(np.uint32), oracle.expf(x).view(np.uint32))
 
 
-def test_fast_exp_band_contains_exact_exp(da):
-    """For every fp32 x in (-16.7, 0] the kernel's band [lo, hi] around its fast
-    estimate contains 2^24 exp(x) of the exact exponential, so deciding u < exp(x)
-    outside the band gives the exact decision."""
-    import oracle
-    lo_bits = np.float32(-0.0).view(np.uint32)
-    hi_bits = np.float32(-16.7).view(np.uint32)
-    step = 1 << 25
-    worst = 0.0
-    for start in range(int(lo_bits), int(hi_bits), step):
-        x = np.arange(start, min(start + step, int(hi_bits)), dtype=np.uint32).view(np.float32)
-        lo, hi = da.binding.da_diag_exp_band(x)
-        P = oracle.expf(x).astype(np.float64) * 2.0 ** 24
-        assert np.all(lo.astype(np.float64) <= P) and np.all(hi.astype(np.float64) >= P)
-        worst = max(worst, float(np.max(np.minimum(P - lo, hi - P) / P)))
-    x = np.array([0.0], np.float32)
-    lo, hi = da.binding.da_diag_exp_band(x)
-    assert lo[0] <= 2.0 ** 24 <= hi[0]
-    # below the cut the band's lower edge stays under U >= 1, so the fast path never
-    # accepts there (the kernels make no separate cut test): every fp32 x in
-    # [-30, -16.7], and a sample down to -1e30
-    a = np.float32(-16.7).view(np.uint32)
-    b = np.float32(-30.0).view(np.uint32)
-    x = np.arange(int(a), int(b) + 1, dtype=np.uint32).view(np.float32)
-    x = np.concatenate([x, -np.exp(np.random.default_rng(3).uniform(np.log(30), np.log(1e30), 1 << 20)).astype(np.float32),
-                        np.array([-np.inf], np.float32)])
-    lo, _ = da.binding.da_diag_exp_band(x)
-    assert lo.max() < 1.0
-    # for x >= 0 (delta <= 0) the band's upper edge lies above every U <= 2^24, so
-    # such a trial is surely accepted or decided by the exact rule: every fp32 x in
-    # [0, 2^-8] and a dense grid up to 100
-    x = np.arange(0, int(np.float32(2.0 ** -8).view(np.uint32)) + 1, dtype=np.uint32).view(np.float32)
-    x = np.concatenate([x, np.linspace(0, 100, 1 << 20, dtype=np.float32), np.array([-0.0, np.inf], np.float32)])
-    _, hi = da.binding.da_diag_exp_band(x)
-    assert hi.min() > 2.0 ** 24
-
-
-def test_accept_decision_matches_definition(da):
-    import oracle
-    rng = np.random.default_rng(5)
-    n = 1 << 22
-    x = -(rng.random(n) * 16.7).astype(np.float32)
-    p = oracle.expf(x)
-    # words whose u falls right at, just below and just above p, plus random ones
-    P = np.floor(p.astype(np.float64) * 2 ** 24).astype(np.int64)
-    U = np.concatenate([P - 1, P, P + 1, rng.integers(1, 2 ** 24 + 1, n)])
-    U = np.clip(U, 1, 2 ** 24)
-    xs = np.concatenate([x, x, x, x])
-    w = ((U - 1).astype(np.uint64) << 8).astype(np.uint32) | rng.integers(0, 256, xs.size).astype(np.uint32)
-    got = da.binding.da_diag_accept(xs, w)
-    ref = (U.astype(np.float64) * 2.0 ** -24 < oracle.expf(xs).astype(np.float64)).astype(np.uint8)
-    assert np.array_equal(got, ref)
-
-
 def test_log_uniform_error_bound(da):
     """log2 U as the step kernels keep it for every draw, for each of the 2^24
     values of U = (w >> 8) + 1: its error against log2 U in fp64 (about one fp32
