@@ -41,7 +41,7 @@ constexpr int kBM = 128;   // states per tile (TMEM lanes)
 constexpr int kBN = 64;    // variables per tile (TMEM columns per digit plane)
 constexpr int kBK = 64;    // couplings per pipeline stage
 constexpr int kStages = 3;
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;   // 16 warps: warp w reads TMEM lanes 32 (w % 4).., columns 16 (w / 4)..
 constexpr uint32_t kATile = kBM * kBK * 2;   // bytes of one state tile (16 KB)
 constexpr uint32_t kBTile = kBN * kBK * 2;   // bytes of one digit-plane tile (8 KB)
 constexpr uint32_t kWaitLimit = 1u << 26;    // polls of one mbarrier before giving up ...
@@ -175,13 +175,16 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_fail;
+    __shared__ I128 s_part[kThreads / kBM][kBM];   // partial energies of the 4 column groups
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int i0 = blockIdx.x * kBN;
-    const int r = blockIdx.y * kBM + threadIdx.x;   // TMEM lane threadIdx.x holds state r
+    const int m = (warp & 3) * 32 + lane;           // TMEM lane = state of the tile
+    const int cg = warp >> 2;                       // 16-column group of the epilogue
+    const int r = blockIdx.y * kBM + m;
 
     if (i0 >= p.N) {   // padding beyond N (whole block): zero fields and partial sums
-        if (r < p.R) {
+        if (cg == 0 && r < p.R) {
             if (p.hout)
                 for (int e = 0; e < kBN; ++e)
                     if (i0 + e < p.npad) static_cast<uint32_t*>(p.hout)[(size_t)r * p.npad + i0 + e] = 0u;
@@ -265,19 +268,17 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
         __syncwarp();
     }
 
-    // epilogue: state r = TMEM lane threadIdx.x, variables i0 .. i0 + 63
+    // epilogue: state r = TMEM lane m, variables i0 + 16 cg .. + 15
     if (!tc::mbar_wait(done, 0, kWaitLimit, kWaitNs)) s_fail = 1;
     __syncwarp();
     tc::fence_after_sync();
-    const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_addr = tbase + ((uint32_t)((warp & 3) * 32) << 16);
     I128 esum{0ull, 0ll};
     const bool live = r < p.R;
     const bool vec = (p.npad & 3) == 0;
     uint32_t* hrow = p.hout ? static_cast<uint32_t*>(p.hout) + (size_t)r * p.npad : nullptr;
-#pragma unroll 1
-    for (int cg = 0; cg < kBN / 16; ++cg) {
+    {
         const int ib = i0 + cg * 16;
-        __syncwarp();
         long long acc[16];
 #pragma unroll
         for (int e = 0; e < 16; e += 2) {
@@ -318,13 +319,24 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
             }
         }
     }
-    if (live && p.part) p.part[(size_t)blockIdx.x * p.R + r] = esum;
+    s_part[cg][m] = esum;
 
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tbase, p.ncols);
+    }
+    if (threadIdx.x < kBM && p.part && blockIdx.y * kBM + threadIdx.x < p.R) {
+        I128 t = s_part[0][threadIdx.x];
+#pragma unroll
+        for (int g = 1; g < kThreads / kBM; ++g) {
+            const I128 u = s_part[g][threadIdx.x];
+            const unsigned long long lo = t.lo + u.lo;
+            t.hi += u.hi + (lo < t.lo ? 1ll : 0ll);
+            t.lo = lo;
+        }
+        p.part[(size_t)blockIdx.x * p.R + blockIdx.y * kBM + threadIdx.x] = t;
     }
     if (threadIdx.x == 0 && s_fail) atomicExch(p.err, 1);
 }
