@@ -206,11 +206,54 @@ def run_ptda(da, instances, L=32, K=32, sweeps=100):
     r = da.da_pt(ctx, betas, sweeps, L, 1)
     trials = L * K * sweeps * q.N * q.N
     acc = r["swaps"].sum(axis=0) / (L * sweeps)
+    # the adaptive ladder (ends fixed, gaps moved towards equal exchange rates) over the first
+    # half of the sweeps; acceptance measured over the second half
+    ra = da.da_pt(ctx, betas, sweeps, L, 1, swap_trace=True, adapt_every=5, adapt_sweeps=sweeps // 2)
+    acc_a = ra["swap_trace"][:, sweeps // 2:, :].mean(axis=(0, 1))
     return {"workload": f"SK bimodal N=512, {K} geometric betas 0.2-5.0, {L} ladders, {sweeps} sweeps, "
                         "device-side exchange after every sweep",
             "value": trials / r["elapsed_s"], "unit": UNIT, "seconds": r["elapsed_s"],
             "exchange_acceptance_min": float(acc.min()), "exchange_acceptance_mean": float(acc.mean()),
-            "best_E": float(r["best_E"].min())}
+            "best_E": float(r["best_E"].min()),
+            "adaptive": {"value": trials / ra["elapsed_s"], "unit": UNIT,
+                         "basis": "ladder adapted every 5 sweeps over the first half, rates over the second",
+                         "exchange_acceptance_min": float(acc_a.min()),
+                         "exchange_acceptance_max": float(acc_a.max()),
+                         "best_E": float(ra["best_E"].min())}}
+
+
+# DA temperatures (T_h, T_l) per density of the Erdos-Renyi study (appendix table of the
+# density experiment), in the units of the Ising Hamiltonian.
+DENSITY_TEMPS = {0.1: (20, 2.0), 0.2: (50, 2.0), 0.3: (60, 2.0), 0.4: (65, 2.5), 0.5: (75, 3.0),
+                 0.6: (75, 3.0), 0.7: (60, 3.5), 0.8: (65, 3.5), 0.9: (70, 4.0)}
+
+
+def run_density(da, instances, per_density=8, R=100, T=100_000):
+    """Density sweep: Erdos-Renyi graphs with bimodal couplings, N = 1024, zero biases, nine
+    densities 10..90 %, 100 runs per instance from x = 0, beta linear 1/T_h -> 1/T_l (the
+    study's temperatures), offset off; one batched launch per density.  The step's cost does
+    not depend on the density (every row of W is dense in HBM), which the per-density
+    throughputs show; TTS99 per instance against the best energy over its runs."""
+    out = {}
+    N = 1024
+    for d, (Th, Tl) in DENSITY_TEMPS.items():
+        beta = instances.beta_linear(1.0 / Th, 1.0 / Tl, T)
+        jobs = []
+        for k in range(per_density):
+            q = instances.erdos_renyi_bimodal(N, d, k)
+            jobs.append(dict(ctx=da.da_create(q.Q), beta=beta, offset_inc=0.0, replicas=R, seed=k,
+                             recompute_every=0))
+        da.da_batch_anneal(jobs[:1])
+        outs, el = da.da_batch_anneal(jobs)
+        tau = el / (per_density * R)
+        tts = [_tts_from_best(o["best_E"], tau) for o in outs]
+        out[f"{int(round(d * 100))}%"] = {
+            "value": per_density * R * T * N / el, "unit": UNIT, "seconds": el,
+            "tts99_median_s": float(np.median([t["tts99_s"] for t in tts])),
+            "hit_fraction_mean": float(np.mean([t["hits"] / t["runs"] for t in tts]))}
+    return {"workload": f"Erdos-Renyi bimodal N={N}, densities 10..90 %, {per_density} instances x {R} runs "
+                        f"per density, {T} steps, beta linear 1/T_h -> 1/T_l per density, offset off",
+            "per_density": out}
 
 
 def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30):
@@ -462,6 +505,7 @@ def main():
         line["batched"] = run_batched(da, instances)
         line["ptda"] = run_ptda(da, instances)
         line["served"] = run_served(da, instances)
+        line["density"] = run_density(da, instances)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

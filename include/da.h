@@ -267,6 +267,21 @@ void da_server_destroy(da_server* srv);
 da_status da_pt(da_ctx* ctx, const float* betas, int32_t K, int64_t sweeps, int32_t ladders,
                 float offset_inc, uint64_t seed, da_pt_result* out);
 
+/* PTDA with the adaptive ladder (Sec. II: the temperatures follow an
+ * adaptive scheme in which the highest and lowest temperatures are fixed and
+ * the intermediate ones are adjusted towards equal exchange probabilities of
+ * neighbouring pairs).  As da_pt, and after every adapt_every sweeps up to
+ * sweep adapt_sweeps the ladder is updated from the exchanges accepted in that
+ * window over all ladders: each gap beta_{p+1} - beta_p is multiplied by
+ * w_p^(1/8), w_p = (a_p + 1) / (L adapt_every + 2) the pair's smoothed
+ * acceptance, and the gaps are rescaled to the fixed span beta_{K-1} - beta_0
+ * (fp64, rounded to fp32); the updated ladder applies from the next sweep.  betas[K] (host, ascending) is
+ * the initial ladder on entry and the final ladder on return.
+ * Errors: DA_EINVAL (adapt_every < 1, as da_pt otherwise), DA_ENOMEM, DA_ECUDA. */
+da_status da_pt_adaptive(da_ctx* ctx, float* betas, int32_t K, int64_t sweeps, int32_t ladders,
+                         float offset_inc, uint64_t seed, int64_t adapt_every, int64_t adapt_sweeps,
+                         da_pt_result* out);
+
 /* Exact energies of R bit-packed host states x[R * da_words(N)] into E[R]
  * (host).  Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
 da_status da_energy(da_ctx* ctx, const uint32_t* x, int32_t R, double* E);

@@ -70,6 +70,10 @@ def lib():
         L.orc_sa_anneal.argtypes = [i64, P, P, i64, i32, u64, P, P, ctypes.c_int]
         L.orc_ptda.argtypes = [i64, ctypes.c_int, P, P, i32, i64, f32, i32, u64,
                                P, P, P, P, P, P, ctypes.c_int]
+        L.orc_ptda_adaptive.argtypes = [i64, ctypes.c_int, P, P, i32, i64, f32, i32, u64, i64, i64, P,
+                                        P, P, P, P, P, P, ctypes.c_int]
+        L.orc_pt_adapt.argtypes = [i32, P, P, i64, P]
+        L.orc_pt_adapt.restype = None
         _lib = L
     return _lib
 
@@ -250,7 +254,18 @@ def sa_anneal(Q, beta, R, seed, nthreads=1):
     return dict(E_best=E, x_best=xb)
 
 
-def ptda(Q, betas, sweeps, L, seed, inc=0.0, mode=None, nthreads=1):
+def pt_adapt(betas, accepted, proposals):
+    """One update of the adaptive PTDA ladder (ends fixed, gaps towards equal acceptance)."""
+    b = np.ascontiguousarray(betas, dtype=np.float32)
+    a = np.ascontiguousarray(accepted, dtype=np.int64)
+    out = np.zeros_like(b)
+    lib().orc_pt_adapt(int(b.size), _p(b), _p(a), int(proposals), _p(out))
+    return out
+
+
+def ptda(Q, betas, sweeps, L, seed, inc=0.0, mode=None, nthreads=1, adapt_every=0, adapt_sweeps=0):
+    """PTDA; with adapt_every > 0 the ladder adapts every adapt_every sweeps up to sweep
+    adapt_sweeps, and out["betas"] is the final ladder."""
     N = Q.shape[0]
     if mode is None:
         mode = MODE_INT if Q.dtype == np.int32 else MODE_F32
@@ -261,8 +276,10 @@ def ptda(Q, betas, sweeps, L, seed, inc=0.0, mode=None, nthreads=1):
                x_best=np.zeros((L, K, words(N)), np.uint32), temp_of=np.zeros((L, K), np.int32),
                swaps=np.zeros((L, max(K - 1, 0)), np.int64),
                swap_trace=np.zeros((L, sweeps, max(K - 1, 0)), np.uint8))
-    rc = lib().orc_ptda(N, mode, _p(Qc), _p(b), K, int(sweeps), float(inc), L, int(seed),
-                        _p(out["E_final"]), _p(out["E_best"]), _p(out["x_best"]), _p(out["temp_of"]),
-                        _p(out["swaps"]), _p(out["swap_trace"]), int(nthreads))
+    out["betas"] = b.copy()
+    rc = lib().orc_ptda_adaptive(N, mode, _p(Qc), _p(b), K, int(sweeps), float(inc), L, int(seed),
+                                 int(adapt_every), int(adapt_sweeps), _p(out["betas"]),
+                                 _p(out["E_final"]), _p(out["E_best"]), _p(out["x_best"]), _p(out["temp_of"]),
+                                 _p(out["swaps"]), _p(out["swap_trace"]), int(nthreads))
     _check(rc, "ptda")
     return out

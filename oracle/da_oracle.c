@@ -658,76 +658,154 @@ int orc_sa_anneal(int64_t N, const float* Q, const float* beta, int64_t T, int32
 /* PTDA: the DA step inside every replica, replica exchange between
  * neighbouring temperatures after every sweep of N steps (Sec. II, PTDA;
  * the exchange rule is the Metropolis swap of Algorithm 4). */
+/* Adaptive ladder of the PTDA (Sec. II: the temperatures follow the adaptive
+ * scheme of Hukushima et al.; the highest and lowest are fixed and the
+ * intermediate ones are moved so that every neighbouring pair is exchanged with
+ * the same probability).  The paper gives the objective, not an update rule;
+ * this one is a damped proportional feedback on the gaps: with a_p the
+ * accepted and n the proposed exchanges of pair (p, p+1) over the last window,
+ * each gap beta_{p+1} - beta_p is multiplied by w_p^(1/8), w_p = (a_p + 1) /
+ * (n + 2) the pair's smoothed acceptance (the eighth root taken as three
+ * square roots), and the gaps are rescaled to the fixed span
+ * beta_{K-1} - beta_0.  Pairs accepted more often than the others are pulled
+ * apart, pairs accepted less often are pushed together, equal acceptances
+ * leave the ladder unchanged; the damping keeps the iteration stable for
+ * acceptances down to about 1e-3, where an undamped update overshoots.
+ * fp64 arithmetic in this order, rounded to fp32. */
+static double gap_weight(int64_t accepted, int64_t proposals)
+{
+    const double w = ((double)accepted + 1.0) / ((double)proposals + 2.0);
+    return sqrt(sqrt(sqrt(w)));
+}
+
+void orc_pt_adapt(int32_t K, const float* betas, const int64_t* accepted, int64_t proposals, float* out)
+{
+    for (int32_t k = 0; k < K; ++k) out[k] = betas[k];
+    if (K < 3 || proposals < 1) return;
+    double total = 0.0;
+    for (int32_t p = 0; p + 1 < K; ++p) {
+        const double gap = (double)betas[p + 1] - (double)betas[p];
+        total = total + gap * gap_weight(accepted[p], proposals);
+    }
+    if (!(total > 0.0)) return;
+    const double span = (double)betas[K - 1] - (double)betas[0];
+    double b = (double)betas[0];
+    for (int32_t p = 0; p + 2 < K; ++p) {
+        const double gap = (double)betas[p + 1] - (double)betas[p];
+        b = b + (gap * gap_weight(accepted[p], proposals)) * span / total;
+        out[p + 1] = (float)b;
+    }
+}
+
+/* One ladder of the PTDA for sweeps [s0, s1) at the ladder `b`. */
+static void ptda_window(const inst_t* I, rep_t* reps, uint8_t* best, double* Ebest, int32_t* tof, int32_t* at,
+                        int64_t* cnt, const float* b, int32_t K, int32_t l, int64_t s0, int64_t s1, int64_t sweeps,
+                        float inc, uint64_t seed, uint8_t* swap_trace)
+{
+    const int64_t N = I->N;
+    for (int64_t sw = s0; sw < s1; ++sw) {
+        for (int32_t k = 0; k < K; ++k) {
+            const float beta = b[tof[k]];
+            const uint32_t rep = (uint32_t)(l * K + k);
+            for (int64_t q = 0; q < N; ++q) {
+                const uint32_t t = (uint32_t)(sw * N + q);
+                da_step(I, &reps[k], beta, inc, seed, t, rep, NULL);
+                double E = tracked_energy(I, &reps[k]);
+                if (E < Ebest[k]) { Ebest[k] = E; memcpy(best + (int64_t)k * N, reps[k].x, (size_t)N); }
+            }
+        }
+        for (int32_t p = 0; p + 1 < K; ++p) {
+            const int32_t a = at[p], c = at[p + 1];
+            const double arg = ((double)b[p] - (double)b[p + 1]) *
+                               (tracked_energy(I, &reps[a]) - tracked_energy(I, &reps[c]));
+            int acc = arg >= 0.0;
+            if (!acc) {
+                uint32_t rw = philox_word(seed, (uint32_t)p, (uint32_t)sw, (uint32_t)l, 2u, 0);
+                acc = orc_uniform(rw) < orc_expf((float)arg);
+            }
+            if (swap_trace) swap_trace[((int64_t)l * sweeps + sw) * (K - 1) + p] = (uint8_t)acc;
+            if (acc) {
+                at[p] = c; at[p + 1] = a;
+                tof[a] = p + 1; tof[c] = p;
+                cnt[p]++;
+            }
+        }
+    }
+}
+
+int orc_ptda_adaptive(int64_t N, int mode, const void* Q, const float* betas_in, int32_t K,
+                      int64_t sweeps, float inc, int32_t L, uint64_t seed, int64_t adapt_every,
+                      int64_t adapt_sweeps, float* betas_out,
+                      double* E_final, double* E_best, uint32_t* x_best, int32_t* temp_of,
+                      int64_t* swaps, uint8_t* swap_trace, int nthreads)
+{
+    if (N < 1 || K < 1 || sweeps < 0 || L < 0 || !Q || !betas_in || adapt_every < 0) return -1;
+    if (mode != ORC_MODE_INT && mode != ORC_MODE_F32) return -1;
+    inst_t I;
+    if (inst_make(&I, N, mode, Q)) return -2;
+    const int64_t words = (N + 31) / 32;
+    const int64_t LK = (int64_t)L * K;
+    const int32_t P = K > 1 ? K - 1 : 0;
+    rep_t* reps = (rep_t*)calloc((size_t)(LK > 0 ? LK : 1), sizeof(rep_t));
+    uint8_t* best = (uint8_t*)calloc((size_t)(LK * N > 0 ? LK * N : 1), 1);
+    double* Ebest = (double*)calloc((size_t)(LK > 0 ? LK : 1), sizeof(double));
+    int32_t* tof = (int32_t*)malloc((size_t)(LK > 0 ? LK : 1) * sizeof(int32_t));
+    int32_t* at = (int32_t*)malloc((size_t)(LK > 0 ? LK : 1) * sizeof(int32_t));
+    int64_t* cnt = (int64_t*)calloc((size_t)((int64_t)L * P > 0 ? (int64_t)L * P : 1), sizeof(int64_t));
+    int64_t* seen = (int64_t*)calloc((size_t)(P > 0 ? P : 1), sizeof(int64_t));
+    int64_t* win = (int64_t*)calloc((size_t)(P > 0 ? P : 1), sizeof(int64_t));
+    float* b = (float*)malloc((size_t)K * sizeof(float));
+    float* nb = (float*)malloc((size_t)K * sizeof(float));
+    int err = (!reps || !best || !Ebest || !tof || !at || !cnt || !seen || !win || !b || !nb) ? -2 : 0;
+    for (int64_t r = 0; r < LK && !err; ++r) err = rep_init(&reps[r], &I) != 0 ? -2 : 0;
+    if (!err) {
+        for (int32_t k = 0; k < K; ++k) b[k] = betas_in[k];
+        for (int64_t r = 0; r < LK; ++r) { tof[r] = (int32_t)(r % K); at[r] = (int32_t)(r % K); }
+        int64_t sw = 0;
+        while (sw < sweeps) {
+            const int adapting = adapt_every > 0 && sw < adapt_sweeps;
+            int64_t end = sweeps;
+            if (adapting && (sw / adapt_every + 1) * adapt_every < end) end = (sw / adapt_every + 1) * adapt_every;
+#ifdef _OPENMP
+            if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+            for (int32_t l = 0; l < L; ++l)
+                ptda_window(&I, reps + (int64_t)l * K, best + (int64_t)l * K * N, Ebest + (int64_t)l * K,
+                            tof + (int64_t)l * K, at + (int64_t)l * K, cnt + (int64_t)l * P, b, K, l, sw, end,
+                            sweeps, inc, seed, swap_trace);
+            if (adapting && end % adapt_every == 0 && end <= adapt_sweeps) {
+                for (int32_t p = 0; p < P; ++p) {
+                    int64_t tot = 0;
+                    for (int32_t l = 0; l < L; ++l) tot += cnt[(int64_t)l * P + p];
+                    win[p] = tot - seen[p];
+                    seen[p] = tot;
+                }
+                orc_pt_adapt(K, b, win, (int64_t)L * adapt_every, nb);
+                for (int32_t k = 0; k < K; ++k) b[k] = nb[k];
+            }
+            sw = end;
+        }
+        for (int64_t o = 0; o < LK; ++o) {
+            if (E_final) E_final[o] = tracked_energy(&I, &reps[o]);
+            if (E_best) E_best[o] = Ebest[o];
+            if (x_best) pack_bits(best + o * N, N, x_best + o * words);
+            if (temp_of) temp_of[o] = tof[o];
+        }
+        if (swaps) for (int64_t o = 0; o < (int64_t)L * P; ++o) swaps[o] = cnt[o];
+        if (betas_out) for (int32_t k = 0; k < K; ++k) betas_out[k] = b[k];
+    }
+    if (reps) for (int64_t r = 0; r < LK; ++r) rep_free(&reps[r]);
+    free(reps); free(best); free(Ebest); free(tof); free(at); free(cnt); free(seen); free(win); free(b); free(nb);
+    inst_free(&I);
+    return err;
+}
+
 int orc_ptda(int64_t N, int mode, const void* Q, const float* betas, int32_t K,
              int64_t sweeps, float inc, int32_t L, uint64_t seed,
              double* E_final, double* E_best, uint32_t* x_best, int32_t* temp_of,
              int64_t* swaps, uint8_t* swap_trace, int nthreads)
 {
-    if (N < 1 || K < 1 || sweeps < 0 || L < 0 || !Q || !betas) return -1;
-    if (mode != ORC_MODE_INT && mode != ORC_MODE_F32) return -1;
-    inst_t I;
-    if (inst_make(&I, N, mode, Q)) return -2;
-    const int64_t words = (N + 31) / 32;
-    int err = 0;
-#ifdef _OPENMP
-    if (nthreads < 1) nthreads = 1;
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
-#endif
-    for (int32_t l = 0; l < L; ++l) {
-        rep_t* reps = (rep_t*)calloc((size_t)K, sizeof(rep_t));
-        uint8_t* best = (uint8_t*)calloc((size_t)(K * N), 1);
-        double* Ebest = (double*)calloc((size_t)K, sizeof(double));
-        int32_t* tof = (int32_t*)malloc((size_t)K * sizeof(int32_t));
-        int32_t* at = (int32_t*)malloc((size_t)K * sizeof(int32_t));
-        int bad = !reps || !best || !Ebest || !tof || !at;
-        for (int32_t k = 0; k < K && !bad; ++k) bad = rep_init(&reps[k], &I) != 0;
-        if (bad) {
-#ifdef _OPENMP
-#pragma omp atomic write
-#endif
-            err = -2;
-        } else {
-            for (int32_t k = 0; k < K; ++k) { tof[k] = k; at[k] = k; }
-            if (swaps) for (int32_t p = 0; p + 1 < K; ++p) swaps[(int64_t)l * (K - 1) + p] = 0;
-            for (int64_t sw = 0; sw < sweeps; ++sw) {
-                for (int32_t k = 0; k < K; ++k) {
-                    const float b = betas[tof[k]];
-                    const uint32_t rep = (uint32_t)(l * K + k);
-                    for (int64_t q = 0; q < N; ++q) {
-                        const uint32_t t = (uint32_t)(sw * N + q);
-                        da_step(&I, &reps[k], b, inc, seed, t, rep, NULL);
-                        double E = tracked_energy(&I, &reps[k]);
-                        if (E < Ebest[k]) { Ebest[k] = E; memcpy(best + (int64_t)k * N, reps[k].x, (size_t)N); }
-                    }
-                }
-                for (int32_t p = 0; p + 1 < K; ++p) {
-                    const int32_t a = at[p], c = at[p + 1];
-                    const double arg = ((double)betas[p] - (double)betas[p + 1]) *
-                                       (tracked_energy(&I, &reps[a]) - tracked_energy(&I, &reps[c]));
-                    int acc = arg >= 0.0;
-                    if (!acc) {
-                        uint32_t rw = philox_word(seed, (uint32_t)p, (uint32_t)sw, (uint32_t)l, 2u, 0);
-                        acc = orc_uniform(rw) < orc_expf((float)arg);
-                    }
-                    if (swap_trace) swap_trace[((int64_t)l * sweeps + sw) * (K - 1) + p] = (uint8_t)acc;
-                    if (acc) {
-                        at[p] = c; at[p + 1] = a;
-                        tof[a] = p + 1; tof[c] = p;
-                        if (swaps) swaps[(int64_t)l * (K - 1) + p]++;
-                    }
-                }
-            }
-            for (int32_t k = 0; k < K; ++k) {
-                const int64_t o = (int64_t)l * K + k;
-                if (E_final) E_final[o] = tracked_energy(&I, &reps[k]);
-                if (E_best) E_best[o] = Ebest[k];
-                if (x_best) pack_bits(best + (int64_t)k * N, N, x_best + o * words);
-                if (temp_of) temp_of[o] = tof[k];
-            }
-        }
-        if (reps) for (int32_t k = 0; k < K; ++k) rep_free(&reps[k]);
-        free(reps); free(best); free(Ebest); free(tof); free(at);
-    }
-    inst_free(&I);
-    return err;
+    return orc_ptda_adaptive(N, mode, Q, betas, K, sweeps, inc, L, seed, 0, 0, NULL, E_final, E_best, x_best,
+                             temp_of, swaps, swap_trace, nthreads);
 }

@@ -121,6 +121,22 @@ int orc_ptda(int64_t N, int mode, const void* Q, const float* betas, int32_t K,
              double* E_final, double* E_best, uint32_t* x_best, int32_t* temp_of,
              int64_t* swaps, uint8_t* swap_trace, int nthreads);
 
+/* The PTDA with its adaptive ladder: as orc_ptda, and after every
+ * adapt_every sweeps up to sweep adapt_sweeps the ladder is updated by
+ * orc_pt_adapt from the exchanges accepted in that window over all ladders
+ * (proposals = L * adapt_every per pair); betas_out[K] (may be NULL) gets the
+ * final ladder.  adapt_every = 0 is orc_ptda. */
+int orc_ptda_adaptive(int64_t N, int mode, const void* Q, const float* betas_in, int32_t K,
+                      int64_t sweeps, float inc, int32_t L, uint64_t seed, int64_t adapt_every,
+                      int64_t adapt_sweeps, float* betas_out,
+                      double* E_final, double* E_best, uint32_t* x_best, int32_t* temp_of,
+                      int64_t* swaps, uint8_t* swap_trace, int nthreads);
+
+/* The adaptive ladder update (proportional feedback on the gaps towards equal
+ * exchange acceptance, ends fixed): out[K] from betas[K], accepted[K-1]
+ * exchanges of each pair out of `proposals`. */
+void orc_pt_adapt(int32_t K, const float* betas, const int64_t* accepted, int64_t proposals, float* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
     L.da_anneal.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_result)]
     L.da_anneal_async.argtypes = [_P, _P, i64, f32, i32, u64, i64, ctypes.POINTER(da_dev_result), _P]
     L.da_pt.argtypes = [_P, _P, i32, i64, i32, f32, u64, ctypes.POINTER(da_pt_result)]
+    L.da_pt_adaptive.argtypes = [_P, _P, i32, i64, i32, f32, u64, i64, i64, ctypes.POINTER(da_pt_result)]
+    L.da_pt_adaptive.restype = ctypes.c_int
     L.da_energy.argtypes = [_P, _P, i32, _P]
     L.da_field_recompute.argtypes = [_P, _P, i32, _P]
     L.da_profile_enable.argtypes = [_P, i32]
@@ -229,8 +231,10 @@ def da_anneal_async(ctx: Context, beta_dev, steps: int, offset_inc: float, repli
 
 
 def da_pt(ctx: Context, betas: np.ndarray, sweeps: int, ladders: int, seed: int, offset_inc: float = 0.0,
-          swap_trace: bool = False) -> dict:
-    b = np.ascontiguousarray(betas, dtype=np.float32)
+          swap_trace: bool = False, adapt_every: int = 0, adapt_sweeps: int = 0) -> dict:
+    """PTDA; with adapt_every > 0 the ladder adapts (da_pt_adaptive) and out["betas"] is
+    the final ladder."""
+    b = np.array(betas, dtype=np.float32)
     K, L, W = b.size, int(ladders), da_words(ctx.N)
     out = dict(final_E=np.zeros((L, K)), best_E=np.zeros((L, K)), best_x=np.zeros((L, K, W), np.uint32),
                temp_of=np.zeros((L, K), np.int32), swaps=np.zeros((L, max(K - 1, 0)), np.int64))
@@ -238,8 +242,14 @@ def da_pt(ctx: Context, betas: np.ndarray, sweeps: int, ladders: int, seed: int,
         out["swap_trace"] = np.zeros((L, sweeps, max(K - 1, 0)), np.uint8)
     res = da_pt_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "best_x", "temp_of", "swaps",
                                                      "swap_trace")), 0.0)
-    _check(lib().da_pt(ctx.handle, _ptr(b), K, int(sweeps), L, float(offset_inc), int(seed) & (2 ** 64 - 1),
-                       ctypes.byref(res)))
+    if adapt_every:
+        _check(lib().da_pt_adaptive(ctx.handle, _ptr(b), K, int(sweeps), L, float(offset_inc),
+                                    int(seed) & (2 ** 64 - 1), int(adapt_every), int(adapt_sweeps),
+                                    ctypes.byref(res)))
+    else:
+        _check(lib().da_pt(ctx.handle, _ptr(b), K, int(sweeps), L, float(offset_inc), int(seed) & (2 ** 64 - 1),
+                           ctypes.byref(res)))
+    out["betas"] = b
     out["elapsed_s"] = res.elapsed_s
     return out
 

@@ -575,11 +575,11 @@ da_status da_anneal_async(da_ctx* c, const float* beta_dev, int64_t steps, float
     return DA_OK;
 }
 
-da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_t L, float inc, uint64_t seed,
-                da_pt_result* out)
+static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, int32_t K, int64_t sweeps, int32_t L,
+                           float inc, uint64_t seed, int64_t adapt_every, int64_t adapt_sweeps, da_pt_result* out)
 {
-    g_err.clear();
     if (da_status s = check_ctx(c)) return s;
+    if (adapt_every < 0 || adapt_sweeps < 0) return fail(DA_EINVAL, "adapt_every and adapt_sweeps must be >= 0");
     if (!betas || K < 1 || K > 4096) return fail(DA_EINVAL, "need 1 <= K <= 4096 and betas");
     if (L < 1 || sweeps < 0) return fail(DA_EINVAL, "need ladders >= 1 and sweeps >= 0");
     if ((long long)L * K > (1 << 24)) return fail(DA_EINVAL, "too many replicas");
@@ -597,7 +597,8 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     const bool want_trace = out && out->swap_trace && K > 1;
     const size_t n_sw = (size_t)L * std::max(K - 1, 0);
     const size_t pt_bytes = align_up((size_t)K * 4, 256) + align_up((size_t)R * 4, 256) * 2 +
-                            align_up(n_sw * 8, 256) + (want_trace ? n_sw * (size_t)sweeps : 0);
+                            align_up(n_sw * 8, 256) + align_up((size_t)K * 8, 256) +
+                            (want_trace ? n_sw * (size_t)sweeps : 0);
     const Layout Ly = plan(c, s, R, 0, false, false, pt_bytes);
     if (da_status e = ensure_ws(c, Ly.total)) return e;
     RunBuffers b{static_cast<char*>(c->ws), Ly, s, R};
@@ -606,7 +607,8 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     int* temp_of = reinterpret_cast<int*>(pb + align_up((size_t)K * 4, 256));
     int* rep_at = temp_of + align_up((size_t)R * 4, 256) / 4;
     long long* swaps = reinterpret_cast<long long*>(reinterpret_cast<char*>(rep_at) + align_up((size_t)R * 4, 256));
-    uint8_t* strace = want_trace ? reinterpret_cast<uint8_t*>(swaps) + align_up(n_sw * 8, 256) : nullptr;
+    long long* seen = reinterpret_cast<long long*>(reinterpret_cast<char*>(swaps) + align_up(n_sw * 8, 256));
+    uint8_t* strace = want_trace ? reinterpret_cast<uint8_t*>(seen) + align_up((size_t)K * 8, 256) : nullptr;
     std::vector<int> init((size_t)R);
     for (int l = 0; l < L; ++l)
         for (int k = 0; k < K; ++k) init[(size_t)l * K + k] = k;
@@ -615,6 +617,7 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     DA_CU(cudaMemcpyAsync(temp_of, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
     DA_CU(cudaMemcpyAsync(rep_at, init.data(), (size_t)R * 4, cudaMemcpyHostToDevice, st));
     if (n_sw) DA_CU(cudaMemsetAsync(swaps, 0, n_sw * 8, st));
+    DA_CU(cudaMemsetAsync(seen, 0, (size_t)K * 8, st));
     if (da_status e = reset_state(c, b, st)) return e;
     StepParams p = base_params(c, b);
     p.betas = betas_dev;
@@ -627,6 +630,8 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
         DA_CU(da::launch_step(is_int8(c), s, p, false, st));
         DA_CU(da::launch_pt_exchange(is_int8(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
                                      seed, st));
+        if (adapt_every > 0 && (sw + 1) % adapt_every == 0 && sw + 1 <= adapt_sweeps)
+            DA_CU(da::launch_pt_adapt(betas_dev, K, L, swaps, seen, (long long)L * adapt_every, st));
     }
     DA_CU(da::launch_best_fixup(R, b.sc(), is_int8(c), b.x(), b.bestx(), s.nwords(), st));
     if (da_status e = evaluate(c, b, st)) return e;
@@ -640,6 +645,7 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
     if (out && out->temp_of) DA_CU(cudaMemcpyAsync(out->temp_of, temp_of, (size_t)R * 4, cudaMemcpyDeviceToHost, st));
     if (out && out->swaps && n_sw)
         DA_CU(cudaMemcpyAsync(out->swaps, swaps, n_sw * 8, cudaMemcpyDeviceToHost, st));
+    if (betas_final) DA_CU(cudaMemcpyAsync(betas_final, betas_dev, (size_t)K * 4, cudaMemcpyDeviceToHost, st));
     if (want_trace && sweeps > 0)
         DA_CU(cudaMemcpyAsync(out->swap_trace, strace, n_sw * (size_t)sweeps, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
@@ -655,6 +661,21 @@ da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_
         if (out->best_E) out->best_E[r] = eb;
     }
     return DA_OK;
+}
+
+da_status da_pt(da_ctx* c, const float* betas, int32_t K, int64_t sweeps, int32_t L, float inc, uint64_t seed,
+                da_pt_result* out)
+{
+    g_err.clear();
+    return pt_common(c, betas, nullptr, K, sweeps, L, inc, seed, 0, 0, out);
+}
+
+da_status da_pt_adaptive(da_ctx* c, float* betas, int32_t K, int64_t sweeps, int32_t L, float inc, uint64_t seed,
+                         int64_t adapt_every, int64_t adapt_sweeps, da_pt_result* out)
+{
+    g_err.clear();
+    if (adapt_every < 1) return fail(DA_EINVAL, "adapt_every must be >= 1");
+    return pt_common(c, betas, betas, K, sweeps, L, inc, seed, adapt_every, adapt_sweeps, out);
 }
 
 static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h, double* E)

@@ -131,6 +131,12 @@ cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                long long* swaps, uint8_t* swap_trace, long long sweep, long long sweeps,
                                uint64_t seed, cudaStream_t st);
 
+// Adaptive PTDA ladder update (da_pt.cu): betas[K] (device) from the exchange
+// counts swaps[L][K-1] accumulated since the counts in seen[K-1] (updated),
+// with `proposals` proposals per pair in the window.
+cudaError_t launch_pt_adapt(float* betas, int K, int L, const long long* swaps, long long* seen, long long proposals,
+                            cudaStream_t st);
+
 // The plain one-launch-per-step form of the DA step (da_plain.cu), N <= 1024:
 // ws holds plain_workspace_bytes(N, R); words_out [2R][ceil(N/32)] receives the
 // final and best states, eex [2R] their exact energies (part: recompute

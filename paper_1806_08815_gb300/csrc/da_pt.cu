@@ -51,7 +51,62 @@ __global__ void pt_exchange_kernel(const float* __restrict__ betas, int K, int L
     }
 }
 
+// The adaptive ladder (Sec. II: highest and lowest temperature fixed, the
+// others moved towards equal exchange acceptance of neighbouring pairs):
+// win[p] = exchanges of pair p accepted over all ladders since the last
+// update, out of `proposals`; each gap beta_{p+1} - beta_p is multiplied by
+// w^(1/8), w = (win[p] + 1) / (proposals + 2) (three correctly rounded square
+// roots; the damping keeps the feedback stable down to acceptances near
+// 1e-3), and the gaps are rescaled to the fixed span.  One block: the counts
+// are summed over ladders in parallel, the ladder is updated by one thread in
+// fp64 in pair order (the same operations, in the same order, as the CPU
+// reference), then rounded to fp32.
+__device__ __forceinline__ double gap_weight(long long accepted, long long proposals)
+{
+    const double w = __ddiv_rn(__dadd_rn((double)accepted, 1.0), __dadd_rn((double)proposals, 2.0));
+    return __dsqrt_rn(__dsqrt_rn(__dsqrt_rn(w)));
+}
+
+__global__ void pt_adapt_kernel(float* betas, int K, int L, const long long* __restrict__ swaps, long long* seen,
+                                long long proposals)
+{
+    extern __shared__ long long win[];
+    const int P = K - 1;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        long long tot = 0;
+        for (int l = 0; l < L; ++l) tot += swaps[(size_t)l * P + p];
+        win[p] = tot - seen[p];
+        seen[p] = tot;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0 || K < 3 || proposals < 1) return;
+    double total = 0.0;
+    for (int p = 0; p < P; ++p) {
+        const double gap = __dsub_rn((double)betas[p + 1], (double)betas[p]);
+        total = __dadd_rn(total, __dmul_rn(gap, gap_weight(win[p], proposals)));
+    }
+    if (!(total > 0.0)) return;
+    const double span = __dsub_rn((double)betas[K - 1], (double)betas[0]);
+    double b = (double)betas[0];
+    float prev = betas[0];   // betas[p] before its update, for the gap of pair p
+    for (int p = 0; p + 2 < K; ++p) {
+        const float next = betas[p + 1];
+        const double gap = __dsub_rn((double)next, (double)prev);
+        b = __dadd_rn(b, __ddiv_rn(__dmul_rn(__dmul_rn(gap, gap_weight(win[p], proposals)), span), total));
+        betas[p + 1] = __double2float_rn(b);
+        prev = next;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pt_adapt(float* betas, int K, int L, const long long* swaps, long long* seen, long long proposals,
+                            cudaStream_t st)
+{
+    if (K < 2 || L < 1) return cudaSuccess;
+    pt_adapt_kernel<<<1, 256, (size_t)(K - 1) * sizeof(long long), st>>>(betas, K, L, swaps, seen, proposals);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                const ReplicaScalars* sc, int* temp_of, int* rep_at,

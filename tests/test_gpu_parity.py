@@ -155,6 +155,30 @@ def test_int8_ragged_sizes_all_shapes(da, inst, N, shape):
     _compare_anneal(got, ref, q.Q, True)
 
 
+@pytest.mark.parametrize("density", [0.1, 0.5, 0.9])
+def test_erdos_renyi_density_instances(da, inst, density):
+    """Bimodal couplings on G(N, p) graphs (the density study), beta linear 1/T_h -> 1/T_l
+    from its temperature table, offset off: bit-exact trajectories at N = 256, and at the
+    study's N = 1024 on sampled replicas of a 100-run launch."""
+    import oracle
+    from bench import DENSITY_TEMPS
+    Th, Tl = DENSITY_TEMPS[density]
+    q = inst.erdos_renyi_bimodal(256, density, 1)
+    beta = inst.beta_linear(1.0 / Th, 1.0 / Tl, 2000)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, 0.0, 10, 3, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=10, seed=3, inc=0.0, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, True)
+    q = inst.erdos_renyi_bimodal(1024, density, 2)
+    beta = inst.beta_linear(1.0 / Th, 1.0 / Tl, 3000)
+    ctx = da.da_create(q.Q)
+    got = da.da_anneal(ctx, beta, 0.0, 100, 5)
+    for r in (0, 63, 99):
+        ref = oracle.da_anneal(q.Q, beta, R=1, seed=5, inc=0.0, replica_base=r)
+        assert np.array_equal(got["best_x"][r], ref["x_best"][0])
+        assert got["best_E"][r] == ref["E_best"][0]
+
+
 @pytest.mark.parametrize("N,dtype", [(33, "i8"), (100, "i8"), (700, "i8"), (1024, "f32"), (200, "f32")])
 def test_draw_warp_on_and_off(da, inst, N, dtype):
     """The G = 1 step with and without its producer warp: both reproduce the oracle."""
@@ -341,6 +365,26 @@ def test_ptda_matches_oracle(da, inst, dtype):
         assert np.array_equal(got["final_E"], ref["E_final"])
     else:
         assert np.allclose(got["best_E"], Eb, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_adaptive_ptda_matches_oracle(da, inst, dtype):
+    """PTDA with the adaptive ladder: every exchange decision, the final ladder, the
+    replicas' temperatures and best states agree with the oracle bit for bit."""
+    import oracle
+    q = inst.sk_bimodal(64, 9) if dtype == "i8" else inst.sk_gaussian(64, 9)
+    b0 = inst.beta_geometric(0.05, 2.0 if dtype == "i8" else 4.0, 8)
+    ref = oracle.ptda(q.Q, b0, 120, 6, 3, nthreads=NT, adapt_every=10, adapt_sweeps=80)
+    ctx = da.da_create(q.Q)
+    got = da.da_pt(ctx, b0, 120, 6, 3, swap_trace=True, adapt_every=10, adapt_sweeps=80)
+    assert np.array_equal(got["betas"].view(np.uint32), ref["betas"].view(np.uint32))
+    assert not np.array_equal(got["betas"], b0)
+    assert np.array_equal(got["swap_trace"], ref["swap_trace"])
+    assert np.array_equal(got["swaps"], ref["swaps"])
+    assert np.array_equal(got["temp_of"], ref["temp_of"])
+    assert np.array_equal(got["best_x"], ref["x_best"])
+    with pytest.raises(da.DAError):
+        da.da_pt(ctx, b0, 10, 2, 3, adapt_every=-1)
 
 
 def test_ptda_c4b_shape(da, inst):

@@ -219,3 +219,59 @@ def test_ptda_finds_ground_state(orc):
     assert np.all(pt["E_best"].min(axis=1) == Emin)
     assert np.array_equal(pt["E_best"].astype(np.int64).ravel(),
                           orc.energy(inst.Q, pt["x_best"].reshape(-1, 1)).astype(np.int64))
+
+
+def test_pt_adapt_fixed_point_ends_and_direction(orc):
+    """The adaptive ladder keeps the end temperatures exactly, leaves a ladder whose
+    pairs are all accepted equally often unchanged, and widens the gap of a pair
+    accepted more often than the others (narrowing one accepted less often)."""
+    b = np.array([0.1, 0.2, 0.45, 0.7, 1.3, 2.0, 3.5], np.float32)
+    same = orc.pt_adapt(b, np.full(6, 40), 100)
+    assert same[0] == b[0] and same[-1] == b[-1]
+    assert np.allclose(same, b, rtol=1e-6, atol=0)
+    acc = np.full(6, 40)
+    acc[2] = 90
+    acc[4] = 5
+    nb = orc.pt_adapt(b, acc, 100)
+    assert nb[0] == b[0] and nb[-1] == b[-1] and np.all(np.diff(nb) > 0)
+    g, ng = np.diff(b.astype(np.float64)), np.diff(nb.astype(np.float64))
+    assert ng[2] / ng.sum() > g[2] / g.sum()
+    assert ng[4] / ng.sum() < g[4] / g.sum()
+    assert np.array_equal(orc.pt_adapt(b[:2], np.array([3]), 10), b[:2])
+
+
+def test_pt_adapt_equalises_a_known_acceptance_law(orc):
+    """Against a ladder whose pair acceptance is a known function of its gap
+    (exp(-gap^2 c_p) with a different c_p per pair, as for Gaussian energy
+    fluctuations), the iterated update drives the acceptances to one value
+    while the ends stay fixed."""
+    K = 12
+    c = np.linspace(2.0, 40.0, K - 1)
+    b = np.geomspace(0.1, 3.0, K).astype(np.float32)
+    n = 10 ** 6
+    def accept(bb):
+        return np.exp(-np.diff(bb.astype(np.float64)) ** 2 * c)
+    spread0 = np.ptp(accept(b))
+    for _ in range(400):
+        b = orc.pt_adapt(b, np.rint(accept(b) * n).astype(np.int64), n)
+    a = accept(b)
+    assert b[0] == np.float32(0.1) and b[-1] == np.float32(3.0)
+    assert np.ptp(a) < 0.01 * spread0 and np.ptp(a) < 0.01
+
+
+def test_adaptive_ptda_evens_out_exchange_rates(orc):
+    """On an SK instance the adaptive ladder gives neighbouring pairs more even
+    exchange rates than the geometric ladder it starts from (the paper's
+    objective for the PTDA's temperatures)."""
+    from paper_1806_08815_gb300 import instances
+    q = instances.sk_bimodal(48, 2)
+    b0 = instances.beta_geometric(0.05, 2.0, 8)
+    sweeps, L = 400, 16
+    fixed = orc.ptda(q.Q, b0, sweeps, L, 1, nthreads=8)
+    adapt = orc.ptda(q.Q, b0, sweeps, L, 1, nthreads=8, adapt_every=10, adapt_sweeps=200)
+    late = lambda r: r["swap_trace"][:, 200:, :].mean(axis=(0, 1))
+    rf, ra = late(fixed), late(adapt)
+    assert np.ptp(ra) < 0.6 * np.ptp(rf)
+    assert adapt["betas"][0] == b0[0] and adapt["betas"][-1] == b0[-1]
+    assert np.all(np.diff(adapt["betas"]) > 0)
+    assert not np.array_equal(adapt["betas"], b0)
