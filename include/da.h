@@ -282,6 +282,16 @@ da_status da_pt_adaptive(da_ctx* ctx, float* betas, int32_t K, int64_t sweeps, i
                          float offset_inc, uint64_t seed, int64_t adapt_every, int64_t adapt_sweeps,
                          da_pt_result* out);
 
+/* The temperature grid's input (appendix, "Parameters": the low and high
+ * temperatures are searched near the 5th-10th and 80th-85th percentiles of
+ * the distribution of the energy changes of proposed moves): over the R host
+ * states x[R * da_words(N)], every single-flip move that raises the energy,
+ * Delta E_i = (1 - 2 x_i) g_i > 0 with the exactly recomputed fields; out[k] =
+ * q[k]-th percentile (0..100) of those Delta E.  Errors: DA_EINVAL (no move
+ * raises the energy, q outside [0, 100]), DA_ENOMEM, DA_ECUDA. */
+da_status da_move_energy_percentiles(da_ctx* ctx, const uint32_t* x, int32_t R, const double* q, int32_t nq,
+                                     double* out);
+
 /* Exact energies of R bit-packed host states x[R * da_words(N)] into E[R]
  * (host).  Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
 da_status da_energy(da_ctx* ctx, const uint32_t* x, int32_t R, double* E);
@@ -336,6 +346,23 @@ int64_t da_static_pitch(int64_t N);
  * implementations.  Errors: DA_EINVAL, DA_ECUDA. */
 da_status da_diag_expf(const float* x, float* y, int64_t n);
 da_status da_diag_philox(const uint32_t* ctr_key, uint32_t* out, int64_t n);
+/* Time to solution over a set of instances (Sec. IV, Algorithm 3), host
+ * computation: B bootstrap resamples of the I instances (with replacement);
+ * for each sampled instance a success probability p from its posterior
+ * Beta(0.5 + hits, 0.5 + runs - hits) (Jeffreys prior), R99 = log(0.01) /
+ * log(1 - p) (at least one run); tts_q[b] = tau times the q-th percentile
+ * (0..100, linear interpolation between order statistics) of the R99 values
+ * of resample b.  tau: time per run.  Random numbers: Philox4x32-10 of seed,
+ * block (b, j, k, 6) for sampled instance j; Gamma draws by Marsaglia & Tsang,
+ * normals by Box-Muller.  hits[I], runs[I], tts_q[B] host arrays.
+ * Errors: DA_EINVAL (I < 1, B < 1, q outside [0, 100], hits > runs, ...). */
+da_status da_tts_bootstrap(const int64_t* hits, const int64_t* runs, int32_t I, double tau, double q,
+                           int32_t B, uint64_t seed, double* tts_q);
+
+/* out[k] = q[k]-th percentile (0..100) of v[n], linear interpolation between
+ * order statistics at position (n - 1) q / 100.  Host.  Errors: DA_EINVAL. */
+da_status da_percentiles(const double* v, int64_t n, const double* q, int32_t nq, double* out);
+
 /* The log-domain decision of the step kernels: da_diag_log_uniform returns
  * L[i] = log2 U (the hardware approximation the kernels keep for every draw)
  * for U = (w[i] >> 8) + 1, i.e. u = U 2^-24; da_diag_accept_log

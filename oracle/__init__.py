@@ -74,6 +74,11 @@ def lib():
                                         P, P, P, P, P, P, ctypes.c_int]
         L.orc_pt_adapt.argtypes = [i32, P, P, i64, P]
         L.orc_pt_adapt.restype = None
+        L.orc_tts_bootstrap.argtypes = [P, P, i32, ctypes.c_double, ctypes.c_double, i32, u64, P]
+        L.orc_beta_samples.argtypes = [ctypes.c_double, ctypes.c_double, i64, u64, P]
+        L.orc_beta_samples.restype = None
+        L.orc_percentile.argtypes = [P, i64, ctypes.c_double]
+        L.orc_percentile.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -283,3 +288,24 @@ def ptda(Q, betas, sweeps, L, seed, inc=0.0, mode=None, nthreads=1, adapt_every=
                                  _p(out["swaps"]), _p(out["swap_trace"]), int(nthreads))
     _check(rc, "ptda")
     return out
+
+
+def tts_bootstrap(hits, runs, tau, q, B, seed):
+    """Algorithm 3: B bootstrap samples of the q-th percentile of the TTS over instances."""
+    y = np.ascontiguousarray(hits, dtype=np.int64)
+    r = np.ascontiguousarray(runs, dtype=np.int64)
+    out = np.zeros(int(B))
+    _check(lib().orc_tts_bootstrap(_p(y), _p(r), int(y.size), float(tau), float(q), int(B), int(seed), _p(out)),
+           "tts_bootstrap")
+    return out
+
+
+def beta_samples(a, b, n, seed):
+    out = np.zeros(int(n))
+    lib().orc_beta_samples(float(a), float(b), int(n), int(seed), _p(out))
+    return out
+
+
+def percentile(v, q):
+    w = np.array(v, dtype=np.float64)
+    return lib().orc_percentile(_p(w), int(w.size), float(q))

@@ -809,3 +809,112 @@ int orc_ptda(int64_t N, int mode, const void* Q, const float* betas, int32_t K,
     return orc_ptda_adaptive(N, mode, Q, betas, K, sweeps, inc, L, seed, 0, 0, NULL, E_final, E_best, x_best,
                              temp_of, swaps, swap_trace, nthreads);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Time to solution over a set of instances (Sec. IV, Algorithm 3).  Random
+ * numbers: Philox blocks (b, j, k, 6) of the seed for resample b, sampled
+ * instance j, k-th block of that pair; uniforms in (0, 1) from 53 bits of two
+ * consecutive words; normals by Box-Muller (first variate); Gamma(a) by
+ * Marsaglia & Tsang for a >= 1 and Gamma(a + 1) u^(1/a) for a < 1; Beta(a, b)
+ * = X / (X + Y) from two Gamma draws; the posterior of an instance with y hits
+ * in r runs is Beta(0.5 + y, 0.5 + r - y) (Jeffreys prior). */
+typedef struct { uint64_t seed; uint32_t b, j, k; uint32_t w[4]; int used; } ustream_t;
+
+static uint32_t us_word(ustream_t* s)
+{
+    if (s->used == 4) {
+        const uint32_t ctr[4] = {s->b, s->j, s->k++, 6u};
+        const uint32_t key[2] = {(uint32_t)s->seed, (uint32_t)(s->seed >> 32)};
+        orc_philox4x32_10(ctr, key, s->w);
+        s->used = 0;
+    }
+    return s->w[s->used++];
+}
+
+static double us_uniform(ustream_t* s)
+{
+    const uint64_t hi = us_word(s) >> 5;
+    const uint64_t lo = us_word(s) >> 6;
+    return ((double)((hi << 26) | lo) + 0.5) * 0x1.0p-53;
+}
+
+static double us_normal(ustream_t* s)
+{
+    const double u1 = us_uniform(s);
+    const double u2 = us_uniform(s);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+static double us_gamma(ustream_t* s, double a)
+{
+    if (a < 1.0) {
+        const double g = us_gamma(s, a + 1.0);
+        const double u = us_uniform(s);
+        return g * exp(log(u) / a);
+    }
+    const double d = a - 1.0 / 3.0;
+    const double c = 1.0 / sqrt(9.0 * d);
+    double v = 1.0;
+    for (int it = 0; it < 1000; ++it) {
+        const double x = us_normal(s);
+        const double t = 1.0 + c * x;
+        if (t <= 0.0) continue;
+        v = t * t * t;
+        const double u = us_uniform(s);
+        if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) return d * v;
+    }
+    return d * v;
+}
+
+void orc_beta_samples(double a, double b, int64_t n, uint64_t seed, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        ustream_t s = {seed, (uint32_t)(i >> 32), (uint32_t)i, 0u, {0, 0, 0, 0}, 4};
+        const double x = us_gamma(&s, a);
+        const double y = us_gamma(&s, b);
+        out[i] = x / (x + y);
+    }
+}
+
+static int cmp_double(const void* a, const void* b)
+{
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* q-th percentile (0..100), linear interpolation at position (n - 1) q / 100 of
+ * the sorted values (sorts v). */
+double orc_percentile(double* v, int64_t n, double q)
+{
+    qsort(v, (size_t)n, sizeof(double), cmp_double);
+    const double pos = (double)(n - 1) * q / 100.0;
+    int64_t lo = (int64_t)floor(pos);
+    int64_t hi = lo + 1 < n ? lo + 1 : n - 1;
+    const double f = pos - (double)lo;
+    return v[lo] + f * (v[hi] - v[lo]);
+}
+
+int orc_tts_bootstrap(const int64_t* hits, const int64_t* runs, int32_t I, double tau, double q, int32_t B,
+                      uint64_t seed, double* tts_q)
+{
+    if (I < 1 || B < 1) return -1;
+    double* r99 = (double*)malloc((size_t)I * sizeof(double));
+    if (!r99) return -2;
+    const double log_miss = log(1.0 - 0.99);
+    for (int32_t b = 0; b < B; ++b) {
+        for (int32_t j = 0; j < I; ++j) {
+            ustream_t s = {seed, (uint32_t)b, (uint32_t)j, 0u, {0, 0, 0, 0}, 4};
+            int64_t idx = (int64_t)(us_uniform(&s) * (double)I);
+            if (idx >= I) idx = I - 1;
+            const double x = us_gamma(&s, 0.5 + (double)hits[idx]);
+            const double y = us_gamma(&s, 0.5 + (double)(runs[idx] - hits[idx]));
+            const double p = x / (x + y);
+            double r = p >= 1.0 ? 1.0 : log_miss / log(1.0 - p);
+            if (!(r >= 1.0)) r = 1.0;
+            r99[j] = r;
+        }
+        tts_q[b] = tau * orc_percentile(r99, I, q);
+    }
+    free(r99);
+    return 0;
+}

@@ -137,6 +137,19 @@ int orc_ptda_adaptive(int64_t N, int mode, const void* Q, const float* betas_in,
  * exchanges of each pair out of `proposals`. */
 void orc_pt_adapt(int32_t K, const float* betas, const int64_t* accepted, int64_t proposals, float* out);
 
+/* Time to solution over instances (Sec. IV, Algorithm 3): B bootstrap
+ * resamples of the I instances (with replacement); for each sampled instance a
+ * success probability from its posterior Beta(0.5 + y, 0.5 + r - y) (hits y of
+ * runs r), R99 = log(0.01) / log(1 - p) (at least 1); tts_q[b] = tau times the
+ * q-th percentile of the R99 values of resample b. */
+int orc_tts_bootstrap(const int64_t* hits, const int64_t* runs, int32_t I, double tau, double q, int32_t B,
+                      uint64_t seed, double* tts_q);
+/* n draws of Beta(a, b) from the sampler of orc_tts_bootstrap (draw i uses the
+ * Philox stream (i >> 32, i & 0xffffffff, k, 6)). */
+void orc_beta_samples(double a, double b, int64_t n, uint64_t seed, double* out);
+/* q-th percentile by linear interpolation of the sorted values (sorts v). */
+double orc_percentile(double* v, int64_t n, double q);
+
 #ifdef __cplusplus
 }
 #endif

@@ -112,6 +112,12 @@ def lib() -> ctypes.CDLL:
     L.da_anneal_static.restype = ctypes.c_int
     L.da_static_pitch.argtypes = [i64]
     L.da_static_pitch.restype = i64
+    L.da_tts_bootstrap.argtypes = [_P, _P, i32, ctypes.c_double, ctypes.c_double, i32, u64, _P]
+    L.da_tts_bootstrap.restype = ctypes.c_int
+    L.da_move_energy_percentiles.argtypes = [_P, _P, i32, _P, i32, _P]
+    L.da_move_energy_percentiles.restype = ctypes.c_int
+    L.da_percentiles.argtypes = [_P, i64, _P, i32, _P]
+    L.da_percentiles.restype = ctypes.c_int
     L.da_diag_log_uniform.argtypes = [_P, _P, i64]
     L.da_diag_accept_log.argtypes = [_P, _P, _P, _P, i64]
     L.da_diag_log_uniform.restype = ctypes.c_int
@@ -297,6 +303,33 @@ def da_profile_read(ctx: Context):
     ms = ctypes.c_double()
     _check(lib().da_profile_read(ctx.handle, ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def da_tts_bootstrap(hits, runs, tau: float, q: float, B: int, seed: int) -> np.ndarray:
+    """Algorithm 3: B bootstrap samples of TTS_q over the instances (hits/runs per instance)."""
+    y = np.ascontiguousarray(hits, dtype=np.int64)
+    r = np.ascontiguousarray(runs, dtype=np.int64)
+    out = np.zeros(int(B))
+    _check(lib().da_tts_bootstrap(_ptr(y), _ptr(r), int(y.size), float(tau), float(q), int(B),
+                                  int(seed) & (2 ** 64 - 1), _ptr(out)))
+    return out
+
+
+def da_move_energy_percentiles(ctx: Context, x: np.ndarray, q) -> np.ndarray:
+    """Percentiles of the energy rises of all single-flip moves from the states x."""
+    xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.uint32)
+    qs = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(qs.size)
+    _check(lib().da_move_energy_percentiles(ctx.handle, _ptr(xs), xs.shape[0], _ptr(qs), qs.size, _ptr(out)))
+    return out
+
+
+def da_percentiles(v, q) -> np.ndarray:
+    vs = np.ascontiguousarray(v, dtype=np.float64)
+    qs = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros(qs.size)
+    _check(lib().da_percentiles(_ptr(vs), vs.size, _ptr(qs), qs.size, _ptr(out)))
+    return out
 
 
 def da_diag_log_uniform(w: np.ndarray) -> np.ndarray:

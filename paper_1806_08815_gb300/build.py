@@ -1,4 +1,4 @@
-"""Build the library's CUDA sources into libda.so (in-tree, sm_103a only).
+"""Build the library's CUDA and host sources into libda.so (in-tree, sm_103a only).
 
 nvcc compiles each translation unit in parallel with
 ``-gencode arch=compute_103a,code=sm_103a`` and links one shared library that
@@ -29,7 +29,7 @@ def nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def _deps():
@@ -53,7 +53,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc, *flags, "-c", src, "-o", obj]
+        # host statistics (.cpp) are compiled without floating-point contraction
+        host = ["-Xcompiler", "-ffp-contract=off"] if src.endswith(".cpp") else []
+        cmd = [cc, *flags, *host, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

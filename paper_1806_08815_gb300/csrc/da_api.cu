@@ -769,6 +769,30 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     return DA_OK;
 }
 
+da_status da_move_energy_percentiles(da_ctx* c, const uint32_t* x, int32_t R, const double* q, int32_t nq,
+                                     double* out)
+{
+    g_err.clear();
+    if (!q || !out || nq < 0) return fail(DA_EINVAL, "need q and out");
+    if (da_status s = check_ctx(c)) return s;
+    std::vector<char> h((size_t)std::max(R, 0) * c->N * 4);
+    if (da_status s = states_common(c, x, R, h.data(), nullptr)) return s;
+    const size_t words = (size_t)da_words(c->N);
+    std::vector<double> up;
+    up.reserve((size_t)R * c->N / 2);
+    for (int r = 0; r < R; ++r)
+        for (int i = 0; i < c->N; ++i) {
+            const size_t at = (size_t)r * c->N + i;
+            const double g = is_int8(c) ? (double)reinterpret_cast<const int32_t*>(h.data())[at]
+                                        : (double)reinterpret_cast<const float*>(h.data())[at];
+            const bool xi = (x[(size_t)r * words + (i >> 5)] >> (i & 31)) & 1u;
+            const double dE = xi ? -g : g;
+            if (dE > 0.0) up.push_back(dE);
+        }
+    if (up.empty()) return fail(DA_EINVAL, "no proposed move raises the energy in these states");
+    return da_percentiles(up.data(), (int64_t)up.size(), q, nq, out);
+}
+
 da_status da_profile_enable(da_ctx* c, int32_t on)
 {
     g_err.clear();

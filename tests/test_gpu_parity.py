@@ -444,3 +444,33 @@ def test_batched_launch_matches_single_instances(da, inst):
     ref = oracle.da_anneal(inst.sk_gaussian(128, 1).Q, j["beta"], R=j["replicas"], seed=j["seed"], inc=0.5,
                            recompute_every=128, trace=True, nthreads=NT)
     assert np.array_equal(outs[1]["trace"], ref["trace"])
+
+
+@pytest.mark.parametrize("dtype", ["i8", "f32"])
+def test_move_energy_percentiles_match_brute_force(da, inst, dtype):
+    """The temperature grid's input: percentiles of the energy rises of all single-flip
+    moves, against E(x xor e_i) - E(x) from the oracle's energy of every neighbour."""
+    import oracle
+    from paper_1806_08815_gb300 import tuning
+    q = inst.sk_bimodal(40, 4) if dtype == "i8" else inst.sk_gaussian(40, 4)
+    ctx = da.da_create(q.Q)
+    rng = np.random.default_rng(2)
+    X = rng.integers(0, 2, (6, q.N))
+    up = []
+    for x in X:
+        E0 = oracle.energy(q.Q, oracle.pack(x[None]))[0]
+        for i in range(q.N):
+            y = x.copy()
+            y[i] ^= 1
+            d = oracle.energy(q.Q, oracle.pack(y[None]))[0] - E0
+            if d > 0:
+                up.append(d)
+    qs = [0, 5, 10, 50, 80, 85, 100]
+    got = da.binding.da_move_energy_percentiles(ctx, oracle.pack(X), qs)
+    ref = np.percentile(np.array(up, dtype=np.float64), qs)
+    if dtype == "i8":
+        assert np.array_equal(got, ref)
+    else:
+        assert np.allclose(got, ref, rtol=1e-6, atol=1e-6)
+    grid = tuning.temperature_grid(ctx, n_states=16)
+    assert 0 < grid["T_low"][0] <= grid["T_low"][1] <= grid["T_high"][0] <= grid["T_high"][1]
