@@ -247,9 +247,13 @@ def run_density(da, instances, per_density=8, R=100, T=100_000):
         outs, el = da.da_batch_anneal(jobs)
         tau = el / (per_density * R)
         tts = [_tts_from_best(o["best_E"], tau) for o in outs]
+        # Algorithm 3: bootstrap distribution of the median TTS over the instances
+        boot = da.da_tts_bootstrap([t["hits"] for t in tts], [t["runs"] for t in tts], tau, 50, 2000, 0)
+        p5, p95 = da.da_percentiles(boot, [5, 95])
         out[f"{int(round(d * 100))}%"] = {
             "value": per_density * R * T * N / el, "unit": UNIT, "seconds": el,
             "tts99_median_s": float(np.median([t["tts99_s"] for t in tts])),
+            "tts50_bootstrap_s": {"mean": float(boot.mean()), "p5": float(p5), "p95": float(p95)},
             "hit_fraction_mean": float(np.mean([t["hits"] / t["runs"] for t in tts]))}
     return {"workload": f"Erdos-Renyi bimodal N={N}, densities 10..90 %, {per_density} instances x {R} runs "
                         f"per density, {T} steps, beta linear 1/T_h -> 1/T_l per density, offset off",
