@@ -41,8 +41,11 @@ extern "C" {
 typedef struct da_ctx da_ctx;
 
 typedef enum da_dtype {
-    DA_INT8 = 0, /* integer couplings (e.g. bimodal +-1 -> +-4): int8 W, int32 fields, exact */
-    DA_FP32 = 1  /* real couplings (e.g. Gaussian): fp32 W and fields, fp64 energies */
+    DA_INT8 = 0,  /* integer couplings (e.g. bimodal +-1 -> +-4): int8 W, int32 fields, exact */
+    DA_FP32 = 1,  /* real couplings (e.g. Gaussian): fp32 W and fields, fp64 energies */
+    DA_INT16 = 2  /* the DA's fixed-point precision (Sec. III "Benchmarking Problems": 16-bit
+                     couplers, 26-bit biases): int16 W, int32 fields, exact integer energies
+                     (real couplings enter through da_quantize) */
 } da_dtype;
 
 typedef enum da_status {
@@ -108,15 +111,37 @@ int64_t da_words(int64_t N);
 const char* da_last_error(void);
 
 /* Create a context holding one QUBO instance on the current CUDA device.
- *   Q      host, N x N row-major (int32_t for DA_INT8, float for DA_FP32);
- *          the upper triangle is read and copied, the caller keeps Q.
+ *   Q      host, N x N row-major (int32_t for DA_INT8 and DA_INT16, float for
+ *          DA_FP32); the upper triangle is read and copied, the caller keeps Q.
  *   N      1 <= N <= 8192 (the next-generation DA size named in Sec. II).
  *   dtype  DA_INT8 requires every coupling in [-128, 127] and every
  *          |Q_ii| + sum_j |Q_ij| < 2^24 (so that every Delta E is exact in
- *          fp32); DA_FP32 requires finite values.
+ *          fp32); DA_INT16 requires every coupling in [-32767, 32767] and every
+ *          |Q_ii| + sum_j |Q_ij| < 2^31 (fields and energies stay exact; a
+ *          Delta E beyond 2^24 enters the acceptance test rounded to fp32, as
+ *          every Delta E does); DA_FP32 requires finite values.
+ *          DA_INT16 contexts serve da_anneal, da_anneal_async, da_pt,
+ *          da_pt_adaptive, da_energy, da_field_recompute and
+ *          da_move_energy_percentiles (not the batched, plain, allocation-free
+ *          or request-loop forms).
  * The library stores W (symmetric, zero diagonal) and diag(Q) in device
  * memory.  Errors: DA_EINVAL (bad N, dtype, range), DA_ENOMEM, DA_ECUDA. */
 da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out);
+
+/* The DA's scaling of real coefficients to its fixed-point precision (Sec. III,
+ * "Benchmarking Problems": the coefficients are scaled up to the hardware's
+ * limits, 2^15 - 1 for the quadratic and 2^25 - 1 for the linear ones, and
+ * rounded to the nearest integers).  One factor for the whole instance:
+ * scale = min(coupler_max / max_{i<j} |Q_ij|, bias_max / max_i |Q_ii|) (a
+ * term whose maximum is 0 is left out; scale = 1 for Q = 0);
+ * Qint[i][j] = round(scale Q[i][j]) to nearest, ties to even, upper triangle
+ * with diagonal (the lower triangle is set to 0).  Q, Qint: host N x N
+ * row-major.  The quantized problem's energies are scale times the original
+ * ones up to the rounding; a DA_INT16 context takes Qint with the anneal's
+ * beta divided by scale.  Errors: DA_EINVAL (non-finite entries, N < 1, limits
+ * < 1 or above 2^30). */
+da_status da_quantize(const float* Q, int64_t N, int32_t coupler_max, int32_t bias_max, int32_t* Qint,
+                      double* scale);
 
 /* Release a context and its device memory (NULL is ignored). */
 void da_destroy(da_ctx* ctx);

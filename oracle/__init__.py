@@ -77,6 +77,7 @@ def lib():
         L.orc_tts_bootstrap.argtypes = [P, P, i32, ctypes.c_double, ctypes.c_double, i32, u64, P]
         L.orc_beta_samples.argtypes = [ctypes.c_double, ctypes.c_double, i64, u64, P]
         L.orc_beta_samples.restype = None
+        L.orc_quantize.argtypes = [i64, P, i32, i32, P, P]
         L.orc_percentile.argtypes = [P, i64, ctypes.c_double]
         L.orc_percentile.restype = ctypes.c_double
         _lib = L
@@ -309,3 +310,13 @@ def beta_samples(a, b, n, seed):
 def percentile(v, q):
     w = np.array(v, dtype=np.float64)
     return lib().orc_percentile(_p(w), int(w.size), float(q))
+
+
+def quantize(Q, coupler_max=2 ** 15 - 1, bias_max=2 ** 25 - 1):
+    """The DA's fixed-point scaling: (Qint int32, scale)."""
+    Qc = np.ascontiguousarray(Q, dtype=np.float32)
+    N = Qc.shape[0]
+    out = np.zeros((N, N), np.int32)
+    sc = np.zeros(1)
+    _check(lib().orc_quantize(N, _p(Qc), int(coupler_max), int(bias_max), _p(out), _p(sc)), "quantize")
+    return out, float(sc[0])

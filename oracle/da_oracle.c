@@ -918,3 +918,30 @@ int orc_tts_bootstrap(const int64_t* hits, const int64_t* runs, int32_t I, doubl
     free(r99);
     return 0;
 }
+
+/* The DA's fixed-point scaling (Sec. III, "Benchmarking Problems"): one factor
+ * s = min(coupler_max / max_{i<j} |Q_ij|, bias_max / max_i |Q_ii|) (terms with
+ * a zero maximum left out, s = 1 for Q = 0), Qint = nearest integer to s Q
+ * (ties to even) on and above the diagonal, 0 below. */
+int orc_quantize(int64_t N, const float* Q, int32_t coupler_max, int32_t bias_max, int32_t* Qint, double* scale)
+{
+    double qmax = 0.0, dmax = 0.0;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i; j < N; ++j) {
+            const double v = fabs((double)Q[i * N + j]);
+            if (i == j) { if (v > dmax) dmax = v; }
+            else if (v > qmax) qmax = v;
+        }
+    double s = 0.0;
+    if (qmax > 0.0) s = (double)coupler_max / qmax;
+    if (dmax > 0.0) {
+        const double sd = (double)bias_max / dmax;
+        if (!(s > 0.0) || sd < s) s = sd;
+    }
+    if (!(s > 0.0)) s = 1.0;
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = 0; j < N; ++j)
+            Qint[i * N + j] = j < i ? 0 : (int32_t)nearbyint(s * (double)Q[i * N + j]);
+    *scale = s;
+    return 0;
+}

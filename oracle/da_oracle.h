@@ -150,6 +150,11 @@ void orc_beta_samples(double a, double b, int64_t n, uint64_t seed, double* out)
 /* q-th percentile by linear interpolation of the sorted values (sorts v). */
 double orc_percentile(double* v, int64_t n, double q);
 
+/* The DA's fixed-point scaling of a real QUBO: one factor
+ * s = min(coupler_max / max_{i<j} |Q_ij|, bias_max / max_i |Q_ii|), Qint the
+ * nearest integers (ties to even) to s Q on and above the diagonal. */
+int orc_quantize(int64_t N, const float* Q, int32_t coupler_max, int32_t bias_max, int32_t* Qint, double* scale);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libda.so")
 
-DA_INT8, DA_FP32 = 0, 1
+DA_INT8, DA_FP32, DA_INT16 = 0, 1, 2
 STATUS = {0: "DA_OK", 1: "DA_EINVAL", 2: "DA_ENOMEM", 3: "DA_EBUDGET", 4: "DA_EBUSY",
           5: "DA_ETIMEOUT", 6: "DA_ECUDA", 7: "DA_ENOTREADY"}
 
@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
     L.da_tts_bootstrap.restype = ctypes.c_int
     L.da_move_energy_percentiles.argtypes = [_P, _P, i32, _P, i32, _P]
     L.da_move_energy_percentiles.restype = ctypes.c_int
+    L.da_quantize.argtypes = [_P, i64, i32, i32, _P, ctypes.POINTER(ctypes.c_double)]
+    L.da_quantize.restype = ctypes.c_int
     L.da_percentiles.argtypes = [_P, i64, _P, i32, _P]
     L.da_percentiles.restype = ctypes.c_int
     L.da_diag_log_uniform.argtypes = [_P, _P, i64]
@@ -167,14 +169,16 @@ class Context:
             pass
 
 
-def da_create(Q: np.ndarray) -> Context:
-    """Q: N x N upper-triangular QUBO, int32 (-> DA_INT8) or float32 (-> DA_FP32)."""
+def da_create(Q: np.ndarray, dtype: int | None = None) -> Context:
+    """Q: N x N upper-triangular QUBO, integer (-> DA_INT8, or DA_INT16 when asked) or
+    float32 (-> DA_FP32)."""
     Q = np.asarray(Q)
     N = Q.shape[0]
     if Q.ndim != 2 or Q.shape[1] != N:
         raise ValueError("Q must be N x N")
-    dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
-    Qc = np.ascontiguousarray(Q, dtype=np.int32 if dtype == DA_INT8 else np.float32)
+    if dtype is None:
+        dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
+    Qc = np.ascontiguousarray(Q, dtype=np.float32 if dtype == DA_FP32 else np.int32)
     h = _P()
     _check(lib().da_create(_ptr(Qc), N, dtype, ctypes.byref(h)))
     return Context(h, N, dtype)
@@ -322,6 +326,16 @@ def da_move_energy_percentiles(ctx: Context, x: np.ndarray, q) -> np.ndarray:
     out = np.zeros(qs.size)
     _check(lib().da_move_energy_percentiles(ctx.handle, _ptr(xs), xs.shape[0], _ptr(qs), qs.size, _ptr(out)))
     return out
+
+
+def da_quantize(Q: np.ndarray, coupler_max: int = 2 ** 15 - 1, bias_max: int = 2 ** 25 - 1):
+    """The DA's fixed-point scaling: (Qint int32 N x N upper triangle, scale)."""
+    Qc = np.ascontiguousarray(Q, dtype=np.float32)
+    N = Qc.shape[0]
+    out = np.zeros((N, N), np.int32)
+    sc = ctypes.c_double()
+    _check(lib().da_quantize(_ptr(Qc), N, int(coupler_max), int(bias_max), _ptr(out), ctypes.byref(sc)))
+    return out, sc.value
 
 
 def da_percentiles(v, q) -> np.ndarray:

@@ -68,7 +68,8 @@ struct da_ctx {
 
 namespace {
 
-bool is_int8(const da_ctx* c) { return c->dtype == DA_INT8; }
+// Integer couplings (DA_INT8, DA_INT16): int32 fields, exact int64 energies.
+bool is_int(const da_ctx* c) { return c->dtype != DA_FP32; }
 
 // Default launch shape: one warp per replica up to N = 1024 (V <= 32
 // variables per lane); beyond that 8 warps per replica, with shapes that keep
@@ -194,7 +195,7 @@ StepParams base_params(const da_ctx* c, const RunBuffers& b)
 // linear terms and E = 0 (all runs start from the same state, Sec. II).
 da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
-    DA_CU(da::launch_init_state(c->dtype == DA_INT8, c->diag, c->N, b.R, b.h(), b.s.npad(), st));
+    DA_CU(da::launch_init_state(is_int(c), c->diag, c->N, b.R, b.h(), b.s.npad(), st));
     DA_CU(cudaMemsetAsync(b.x(), 0, (size_t)2 * b.R * b.s.nwords() * 4, st));
     DA_CU(cudaMemsetAsync(b.sc(), 0, (size_t)b.R * sizeof(ReplicaScalars), st));
     return DA_OK;
@@ -203,7 +204,7 @@ da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 // Exact energies of the final and best states into eex[0..2R).
 da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
-    DA_CU(da::launch_recompute_tc(is_int8(c), c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
+    DA_CU(da::launch_recompute_tc(is_int(c), c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
                                   b.s.npad(), b.eex(), 1, st, b.sums(), b.tca()));
     return DA_OK;
 }
@@ -249,7 +250,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
     p.rep_base = 0;
     p.trace = trace_dev;
     p.trace_T = T;
-    const bool rec = !is_int8(c) && recompute_every > 0;
+    const bool rec = !is_int(c) && recompute_every > 0;
     for (long long t0 = 0; t0 < T; t0 = p.t1) {
         p.t0 = t0;
         p.t1 = std::min(T, t0 + (1ll << 14));
@@ -259,7 +260,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
             if (da_status e = prof_pair(c, &e0, &e1)) return e;
             DA_CU(cudaEventRecord(e0, st));
         }
-        DA_CU(da::launch_step(is_int8(c), b.s, p, trace_dev != nullptr, st));
+        DA_CU(da::launch_step((int)c->dtype, b.s, p, trace_dev != nullptr, st));
         if (e1) DA_CU(cudaEventRecord(e1, st));
         if (rec && p.t1 % recompute_every == 0) {
             DA_CU(da::launch_recompute_tc(false, c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), b.R, b.h(),
@@ -267,7 +268,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
                                           (int)(sizeof(ReplicaScalars) / 8), st, b.sums(), b.tca()));
         }
     }
-    DA_CU(da::launch_best_fixup(b.R, b.sc(), is_int8(c), b.x(), b.bestx(), b.s.nwords(), st));
+    DA_CU(da::launch_best_fixup(b.R, b.sc(), is_int(c), b.x(), b.bestx(), b.s.nwords(), st));
     return DA_OK;
 }
 
@@ -290,10 +291,43 @@ struct CtxLock {
 }  // namespace
 
 namespace da {
-bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::string& why)
+// Integer couplings into W of element type T (int8 or int16): range of every
+// coupling, and |Q_ii| + sum_j |Q_ij| below row_limit.
+template <typename T>
+static bool integer_instance(const int32_t* q, int n, int ldw, int32_t lo, int32_t hi, long long row_limit,
+                             const char* name, HostInstance& out, std::string& why)
+{
+    T* w = reinterpret_cast<T*>(out.W.data());
+    int32_t* d = reinterpret_cast<int32_t*>(out.diag.data());
+    std::vector<long long> rowabs(n, 0);
+    for (int i = 0; i < n; ++i) {
+        d[i] = q[(size_t)i * n + i];
+        rowabs[i] += std::llabs((long long)d[i]);
+        for (int j = i + 1; j < n; ++j) {
+            const int32_t v = q[(size_t)i * n + j];
+            if (v < lo || v > hi) {
+                why = std::string(name) + " coupling Q[" + std::to_string(i) + "][" + std::to_string(j) + "] = " +
+                      std::to_string(v) + " outside [" + std::to_string(lo) + ", " + std::to_string(hi) + "]";
+                return false;
+            }
+            w[(size_t)i * ldw + j] = (T)v;
+            w[(size_t)j * ldw + i] = (T)v;
+            rowabs[i] += std::abs(v);
+            rowabs[j] += std::abs(v);
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (rowabs[i] >= row_limit) {
+            why = std::string(name) + " row " + std::to_string(i) + ": |Q_ii| + sum |Q_ij| too large for exact fields";
+            return false;
+        }
+    return true;
+}
+
+bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why)
 {
     const int ldw = (int)align_up((size_t)n, 128);
-    const size_t esz = int8 ? 1 : 4;
+    const size_t esz = dtype == DA_INT8 ? 1 : dtype == DA_INT16 ? 2 : 4;
     out.ldw = ldw;
     out.S = 0;
     // 8192 zero entries after the last row: a lane whose slice straddles N
@@ -301,32 +335,14 @@ bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::str
     out.W.assign(((size_t)n * ldw + 8192) * esz, 0);
     out.diag.assign((size_t)n * 4, 0);
     float amax = 0.f;
-    if (int8) {
-        const int32_t* q = static_cast<const int32_t*>(Q);
-        int8_t* w = reinterpret_cast<int8_t*>(out.W.data());
-        int32_t* d = reinterpret_cast<int32_t*>(out.diag.data());
-        std::vector<long long> rowabs(n, 0);
-        for (int i = 0; i < n; ++i) {
-            d[i] = q[(size_t)i * n + i];
-            rowabs[i] += std::llabs((long long)d[i]);
-            for (int j = i + 1; j < n; ++j) {
-                const int32_t v = q[(size_t)i * n + j];
-                if (v < -128 || v > 127) {
-                    why = "DA_INT8 coupling Q[" + std::to_string(i) + "][" + std::to_string(j) + "] = " +
-                          std::to_string(v) + " outside [-128, 127]";
-                    return false;
-                }
-                w[(size_t)i * ldw + j] = (int8_t)v;
-                w[(size_t)j * ldw + i] = (int8_t)v;
-                rowabs[i] += std::abs(v);
-                rowabs[j] += std::abs(v);
-            }
-        }
-        for (int i = 0; i < n; ++i)
-            if (rowabs[i] >= (1ll << 24)) {
-                why = "DA_INT8 row " + std::to_string(i) + ": |Q_ii| + sum |Q_ij| >= 2^24";
-                return false;
-            }
+    if (dtype == DA_INT8) {
+        if (!integer_instance<int8_t>(static_cast<const int32_t*>(Q), n, ldw, -128, 127, 1ll << 24, "DA_INT8", out,
+                                      why))
+            return false;
+    } else if (dtype == DA_INT16) {
+        if (!integer_instance<int16_t>(static_cast<const int32_t*>(Q), n, ldw, -32767, 32767, 1ll << 31, "DA_INT16",
+                                       out, why))
+            return false;
     } else {
         const float* q = static_cast<const float*>(Q);
         float* w = reinterpret_cast<float*>(out.W.data());
@@ -381,11 +397,11 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     *out = nullptr;
     if (!Q) return fail(DA_EINVAL, "Q is null");
     if (N < 1 || N > 8192) return fail(DA_EINVAL, "N must be in [1, 8192]");
-    if (dtype != DA_INT8 && dtype != DA_FP32) return fail(DA_EINVAL, "unknown dtype");
+    if (dtype != DA_INT8 && dtype != DA_FP32 && dtype != DA_INT16) return fail(DA_EINVAL, "unknown dtype");
     const int n = (int)N;
     da::HostInstance hin;
     std::string why;
-    if (!da::build_instance(Q, n, dtype == DA_INT8, hin, why)) return fail(DA_EINVAL, why);
+    if (!da::build_instance(Q, n, (int)dtype, hin, why)) return fail(DA_EINVAL, why);
     const int ldw = hin.ldw;
     std::vector<char>& Wh = hin.W;
     std::vector<char>& dh = hin.diag;
@@ -415,7 +431,7 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
-    e = da::tc_operand_build(dtype == DA_INT8, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
+    e = da::tc_operand_build((int)dtype, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -423,6 +439,32 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
                     std::string("tensor-core operand: ") + cudaGetErrorString(e));
     }
     *out = c;
+    return DA_OK;
+}
+
+da_status da_quantize(const float* Q, int64_t N, int32_t coupler_max, int32_t bias_max, int32_t* Qint,
+                      double* scale)
+{
+    g_err.clear();
+    if (!Q || !Qint || !scale || N < 1) return fail(DA_EINVAL, "need Q, Qint, scale and N >= 1");
+    if (coupler_max < 1 || bias_max < 1 || coupler_max > (1 << 30) || bias_max > (1 << 30))
+        return fail(DA_EINVAL, "limits must be in [1, 2^30]");
+    const int64_t n = N;
+    double qmax = 0.0, dmax = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i; j < n; ++j) {
+            const double v = Q[i * n + j];
+            if (!std::isfinite(v)) return fail(DA_EINVAL, "non-finite Q entry");
+            if (i == j) dmax = std::max(dmax, std::fabs(v));
+            else qmax = std::max(qmax, std::fabs(v));
+        }
+    double s = 0.0;
+    if (qmax > 0.0) s = (double)coupler_max / qmax;
+    if (dmax > 0.0) s = s > 0.0 ? std::min(s, (double)bias_max / dmax) : (double)bias_max / dmax;
+    if (!(s > 0.0)) s = 1.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) Qint[i * n + j] = j < i ? 0 : (int32_t)std::nearbyint(s * (double)Q[i * n + j]);
+    *scale = s;
     return DA_OK;
 }
 
@@ -515,7 +557,7 @@ da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int3
     RunBuffers b{};
     if (da_status e = anneal_common(c, beta, true, steps, inc, R, seed, recompute_every, want_trace, st, &b)) return e;
     double* res = reinterpret_cast<double*>(b.base + b.L.res);
-    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int8(c), R, b.sc(), b.eex(), res, res + R, res + 2 * R,
+    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int(c), R, b.sc(), b.eex(), res, res + R, res + 2 * R,
                                                      reinterpret_cast<int64_t*>(res + 3 * R));
     DA_CU(cudaGetLastError());
     DA_CU(cudaEventRecord(c->ev1, st));
@@ -560,7 +602,7 @@ da_status da_anneal_async(da_ctx* c, const float* beta_dev, int64_t steps, float
     if (da_status e = anneal_common(c, beta_dev, false, steps, inc, R, seed, recompute_every, want_trace, st, &b))
         return e;
     if (!out) return DA_OK;
-    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int8(c), R, b.sc(), b.eex(), out->final_E, out->best_E,
+    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int(c), R, b.sc(), b.eex(), out->final_E, out->best_E,
                                                      out->max_drift, out->flips);
     DA_CU(cudaGetLastError());
     const size_t words = (size_t)da_words(c->N);
@@ -627,13 +669,13 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     for (long long sw = 0; sw < sweeps; ++sw) {
         p.t0 = sw * c->N;
         p.t1 = p.t0 + c->N;
-        DA_CU(da::launch_step(is_int8(c), s, p, false, st));
-        DA_CU(da::launch_pt_exchange(is_int8(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
+        DA_CU(da::launch_step((int)c->dtype, s, p, false, st));
+        DA_CU(da::launch_pt_exchange(is_int(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
                                      seed, st));
         if (adapt_every > 0 && (sw + 1) % adapt_every == 0 && sw + 1 <= adapt_sweeps)
             DA_CU(da::launch_pt_adapt(betas_dev, K, L, swaps, seen, (long long)L * adapt_every, st));
     }
-    DA_CU(da::launch_best_fixup(R, b.sc(), is_int8(c), b.x(), b.bestx(), s.nwords(), st));
+    DA_CU(da::launch_best_fixup(R, b.sc(), is_int(c), b.x(), b.bestx(), s.nwords(), st));
     if (da_status e = evaluate(c, b, st)) return e;
     DA_CU(cudaEventRecord(c->ev1, st));
     std::vector<long long> eex((size_t)2 * R);
@@ -655,8 +697,8 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out->elapsed_s = ms * 1e-3;
     for (int r = 0; r < R; ++r) {
-        const double ef = is_int8(c) ? (double)eex[r] : reinterpret_cast<const double*>(eex.data())[r];
-        const double eb = is_int8(c) ? (double)eex[R + r] : reinterpret_cast<const double*>(eex.data())[R + r];
+        const double ef = is_int(c) ? (double)eex[r] : reinterpret_cast<const double*>(eex.data())[r];
+        const double eb = is_int(c) ? (double)eex[R + r] : reinterpret_cast<const double*>(eex.data())[R + r];
         if (out->final_E) out->final_E[r] = ef;
         if (out->best_E) out->best_E[r] = eb;
     }
@@ -697,7 +739,7 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     long long* sums = reinterpret_cast<long long*>(base + xb + hb);
     long long* ed = reinterpret_cast<long long*>(base + xb + hb + sb);
     DA_CU(cudaMemcpyAsync(xd, x, (size_t)R * words * 4, cudaMemcpyHostToDevice, st));
-    DA_CU(da::launch_recompute_tc(is_int8(c), c->tc, c->diag, c->N, c->S, xd, (int)words, R, h ? hd : nullptr, c->N,
+    DA_CU(da::launch_recompute_tc(is_int(c), c->tc, c->diag, c->N, c->S, xd, (int)words, R, h ? hd : nullptr, c->N,
                                   E ? ed : nullptr, 1, st, sums, base + xb + hb + sb + eb));
     std::vector<long long> eh(E ? (size_t)R : 0);
     if (h) DA_CU(cudaMemcpyAsync(h, hd, (size_t)R * c->N * 4, cudaMemcpyDeviceToHost, st));
@@ -706,7 +748,7 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     if (da_status e = check_tc(c)) return e;
     if (E)
         for (int r = 0; r < R; ++r)
-            E[r] = is_int8(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
+            E[r] = is_int(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
     return DA_OK;
 }
 
@@ -716,6 +758,7 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     g_err.clear();
     if (da_status s = check_ctx(c)) return s;
     if (c->N > 1024) return fail(DA_EINVAL, "the plain form supports N <= 1024");
+    if (c->dtype == DA_INT16) return fail(DA_EINVAL, "the plain form takes DA_INT8 or DA_FP32 contexts");
     if (steps < 0 || (steps > 0 && !beta)) return fail(DA_EINVAL, "bad schedule");
     if (!da::schedule_ok(beta, steps)) return fail(DA_EINVAL, "beta must be finite and >= 0");
     if (R < 1) return fail(DA_EINVAL, "replicas < 1");
@@ -740,7 +783,7 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     if (steps > 0) DA_CU(cudaMemcpyAsync(base + o_beta, beta, (size_t)steps * 4, cudaMemcpyHostToDevice, st));
     uint32_t* words = reinterpret_cast<uint32_t*>(base + o_words);
     long long* eex = reinterpret_cast<long long*>(base + o_eex);
-    DA_CU(da::plain_anneal(c->W, c->diag, is_int8(c), c->N, c->ldw, c->S, reinterpret_cast<const float*>(base + o_beta),
+    DA_CU(da::plain_anneal(c->W, c->diag, is_int(c), c->N, c->ldw, c->S, reinterpret_cast<const float*>(base + o_beta),
                            steps, inc, R, seed, base + o_ws, want_trace ? reinterpret_cast<int*>(base + o_trace) : nullptr,
                            words, eex, reinterpret_cast<long long*>(base + o_part), tracked.data(), flips.data(), st));
     DA_CU(cudaEventRecord(c->ev1, st));
@@ -759,8 +802,8 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out->elapsed_s = ms * 1e-3;
     for (int r = 0; r < R; ++r) {
-        const double ef = is_int8(c) ? (double)e[r] : reinterpret_cast<const double*>(e.data())[r];
-        const double eb = is_int8(c) ? (double)e[R + r] : reinterpret_cast<const double*>(e.data())[R + r];
+        const double ef = is_int(c) ? (double)e[r] : reinterpret_cast<const double*>(e.data())[r];
+        const double eb = is_int(c) ? (double)e[R + r] : reinterpret_cast<const double*>(e.data())[R + r];
         if (out->final_E) out->final_E[r] = ef;
         if (out->best_E) out->best_E[r] = eb;
         if (out->max_drift) out->max_drift[r] = std::fabs(tracked[r] - ef);
@@ -783,7 +826,7 @@ da_status da_move_energy_percentiles(da_ctx* c, const uint32_t* x, int32_t R, co
     for (int r = 0; r < R; ++r)
         for (int i = 0; i < c->N; ++i) {
             const size_t at = (size_t)r * c->N + i;
-            const double g = is_int8(c) ? (double)reinterpret_cast<const int32_t*>(h.data())[at]
+            const double g = is_int(c) ? (double)reinterpret_cast<const int32_t*>(h.data())[at]
                                         : (double)reinterpret_cast<const float*>(h.data())[at];
             const bool xi = (x[(size_t)r * words + (i >> 5)] >> (i & 31)) & 1u;
             const double dE = xi ? -g : g;

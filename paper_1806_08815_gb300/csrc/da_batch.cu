@@ -257,6 +257,8 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         da_dtype dt;
         if (!it.ctx || da_ctx_info(it.ctx, &N, &dt) != DA_OK) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad context");
         if (N > 1024) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes N <= 1024");
+        if (dt != DA_INT8 && dt != DA_FP32)
+            return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes DA_INT8 or DA_FP32");
         if (it.replicas < 1 || it.steps < 0 || it.steps >= (1ll << 32) || (it.steps > 0 && !it.beta))
             return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad replicas/steps/schedule");
         if (it.steps > 0 && !da::schedule_ok(it.beta, it.steps))

@@ -11,6 +11,9 @@ struct da_ctx;
 
 namespace da {
 
+// Coupling types, with the values of da_dtype in include/da.h.
+constexpr int kWInt8 = 0, kWFp32 = 1, kWInt16 = 2;
+
 // Per-replica scalars kept in global memory between kernel launches.
 // E and best hold int64 energies (int8 instances) or fp64 bit patterns (fp32).
 struct alignas(32) ReplicaScalars {
@@ -81,7 +84,8 @@ cudaError_t launch_best_fixup(int R, ReplicaScalars* sc, bool is_int8, const uin
                               cudaStream_t st);
 
 // Step kernel launcher (da_step.cu).  is_int8 selects int8 W / int32 fields.
-cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
+// wtype: the da_dtype of W (DA_INT8, DA_FP32, DA_INT16).
+cudaError_t launch_step(int wtype, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 bool step_shape_supported(const StepShape& s);
 
 // Field recompute and energies (da_fields.cu).
@@ -114,13 +118,14 @@ struct TcOperand {
     int* err = nullptr;
     int bits = 0, limbs = 0, kchunks = 0;
 };
-void tc_digits(bool is_int8, int N, int* bits, int* limbs);
-cudaError_t tc_operand_build(bool is_int8, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+void tc_digits(int wtype, int N, int* bits, int* limbs);
+cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
                              cudaStream_t st);
 void tc_operand_free(TcOperand* op);
 // Workspace for R states expanded to f16 (state_ws of launch_recompute_tc).
 size_t tc_state_bytes(int N, int R);
-// Arguments as launch_recompute; scratch must hold 16 * ceil(max(npad, N) / 64) * R bytes.
+// Arguments as launch_recompute (is_int8: integer couplings of either width,
+// int32 fields); scratch must hold 16 * ceil(max(npad, N) / 64) * R bytes.
 cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
                                 const uint32_t* xs, int nw, int R, void* hout, int npad, long long* E, int Estride,
                                 cudaStream_t st, long long* scratch, void* state_ws);
@@ -147,13 +152,14 @@ cudaError_t plain_anneal(const void* W, const void* diag, bool int8, int N, int 
 size_t plain_workspace_bytes(int N, int R);
 
 // An instance in the library's device layout, built on the host from the
-// upper triangle of Q (da_api.cu): W symmetric with zero diagonal, row pitch
-// ldw, 8192 zero entries of slack; diag; fixed-point scale S (fp32).
+// upper triangle of Q (da_api.cu): W symmetric with zero diagonal (element
+// type of the da_dtype `dtype`), row pitch ldw, 8192 zero entries of slack;
+// diag; fixed-point scale S (fp32).
 struct HostInstance {
     std::vector<char> W, diag;
     int ldw = 0, S = 0;
 };
-bool build_instance(const void* Q, int n, bool int8, HostInstance& out, std::string& why);
+bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why);
 
 // The default launch shape of the step kernel for N variables.
 StepShape default_shape(int N);

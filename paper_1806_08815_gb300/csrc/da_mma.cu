@@ -55,11 +55,11 @@ __device__ __forceinline__ size_t core_offset(int rows, int row, int k)
     return (size_t)((k >> 3) * (rows >> 3) + (row >> 3)) * 64 + (row & 7) * 8 + (k & 7);
 }
 
-template <bool INT8>
+template <typename Tw>
 __device__ __forceinline__ long long fixed_w(const void* W, size_t idx, int S)
 {
-    if constexpr (INT8) return (long long)static_cast<const int8_t*>(W)[idx];
-    else return fixed_of_f32(static_cast<const float*>(W)[idx], S);
+    if constexpr (sizeof(Tw) == 4) return fixed_of_f32(static_cast<const float*>(W)[idx], S);
+    else return (long long)static_cast<const Tw*>(W)[idx];   // integer couplings are their own grid
 }
 
 template <bool INT8>
@@ -78,7 +78,7 @@ __global__ void build_dfix_kernel(const void* __restrict__ diag, int N, int S, l
 }
 
 // Digit planes: one thread per (tile i, chunk j, row i, group of 8 j).
-template <bool INT8>
+template <typename Tw>
 __global__ void build_digits_kernel(const void* __restrict__ W, int N, int ldw, int S, int bits, int limbs,
                                     int kchunks, __half* __restrict__ B, long long total)
 {
@@ -95,7 +95,7 @@ __global__ void build_digits_kernel(const void* __restrict__ W, int N, int ldw, 
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int j = jb + e;
-        v[e] = (i < N && j < N) ? fixed_w<INT8>(W, (size_t)j * ldw + i, S) : 0ll;
+        v[e] = (i < N && j < N) ? fixed_w<Tw>(W, (size_t)j * ldw + i, S) : 0ll;
     }
     const long long half_range = 1ll << (bits - 1);
     const long long mask = (1ll << bits) - 1;
@@ -352,17 +352,22 @@ int ceil_log2(long long n)
 
 }  // namespace
 
-void tc_digits(bool is_int8, int N, int* bits, int* limbs)
+void tc_digits(int wtype, int N, int* bits, int* limbs)
 {
-    if (is_int8) {   // the couplings are balanced 8-bit digits already
+    if (wtype == kWInt8) {   // the couplings are balanced 8-bit digits already
         *bits = 8;
         *limbs = 1;
         return;
     }
-    // |partial sum| <= 2^(b-1) * N <= 2^21; |v| <= 2^(62 - L), 2^L >= N + 1
+    // |partial sum| <= 2^(b-1) * N <= 2^21
     const int b = std::min(12, 22 - ceil_log2(std::max(N, 2)));
-    const int L = ceil_log2((long long)N + 1);
     *bits = b;
+    if (wtype == kWInt16) {  // |v| <= 2^15 - 1 needs b * limbs >= 17
+        *limbs = (17 + b - 1) / b;
+        return;
+    }
+    // |v| <= 2^(62 - L), 2^L >= N + 1
+    const int L = ceil_log2((long long)N + 1);
     *limbs = (64 - L + b - 1) / b;
 }
 
@@ -373,10 +378,10 @@ size_t tc_state_bytes(int N, int R)
     return rtiles * kchunks * kATile;
 }
 
-cudaError_t tc_operand_build(bool is_int8, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
                              cudaStream_t st)
 {
-    tc_digits(is_int8, N, &op->bits, &op->limbs);
+    tc_digits(wtype, N, &op->bits, &op->limbs);
     op->kchunks = (N + kBK - 1) / kBK;
     const int itiles = (N + kBN - 1) / kBN;
     const size_t bytes = (size_t)itiles * op->kchunks * op->limbs * kBTile;
@@ -390,15 +395,17 @@ cudaError_t tc_operand_build(bool is_int8, const void* W, const void* diag, int 
     const int tb = 256;
     const unsigned blocks = (unsigned)((total + tb - 1) / tb);
     const int nd = op->kchunks * kBK;
-    if (is_int8) {
-        build_digits_kernel<true><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
-                                                         static_cast<__half*>(op->B), total);
-        build_dfix_kernel<true><<<(nd + tb - 1) / tb, tb, 0, st>>>(diag, N, S, op->dfix, nd);
-    } else {
-        build_digits_kernel<false><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks,
-                                                          static_cast<__half*>(op->B), total);
+    __half* B = static_cast<__half*>(op->B);
+    if (wtype == kWInt8)
+        build_digits_kernel<int8_t><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks, B, total);
+    else if (wtype == kWInt16)
+        build_digits_kernel<int16_t><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks, B, total);
+    else
+        build_digits_kernel<float><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks, B, total);
+    if (wtype == kWFp32)
         build_dfix_kernel<false><<<(nd + tb - 1) / tb, tb, 0, st>>>(diag, N, S, op->dfix, nd);
-    }
+    else
+        build_dfix_kernel<true><<<(nd + tb - 1) / tb, tb, 0, st>>>(diag, N, S, op->dfix, nd);
     return cudaGetLastError();
 }
 
@@ -419,7 +426,7 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
     int dev = 0;
     cudaGetDevice(&dev);
     const size_t smem = smem_bytes(op.limbs);
-    const int max_limbs = is_int8 ? 1 : kMaxLimbs;
+    const int max_limbs = is_int8 ? 2 : kMaxLimbs;   // integer couplings: 1 (int8) or 2 (int16) planes
     if (op.limbs < 1 || op.limbs > max_limbs) return cudaErrorInvalidValue;
     if (dev < 64 && !attr_set[is_int8][dev]) {
         const int bytes = (int)smem_bytes(max_limbs);

@@ -328,7 +328,7 @@ bool admit(da_server* s, Req& q)
             p.t0 = t0;
             p.t1 = std::min(T, t0 + (1ll << 14));
             if (P > 0) p.t1 = std::min(p.t1, (t0 / P + 1) * P);
-            if (!cu_ok(da::launch_step(q.int8, sh, p, false, st), q, "step")) return false;
+            if (!cu_ok(da::launch_step(q.int8 ? da::kWInt8 : da::kWFp32, sh, p, false, st), q, "step")) return false;
             if (P > 0 && p.t1 % P == 0 &&
                 !cu_ok(da::launch_recompute(false, W, diag, q.N, q.inst.ldw, q.inst.S, xs, sh.nwords(), R, h, sh.npad(),
                                             reinterpret_cast<long long*>(sc), (int)(sizeof(da::ReplicaScalars) / 8),
@@ -534,7 +534,8 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     if (!s || !job || !out) return sfail(DA_EINVAL, "null argument");
     *out = nullptr;
     if (!job->Q || job->N < 1 || job->N > 8192) return sfail(DA_EINVAL, "need Q and 1 <= N <= 8192");
-    if (job->dtype != DA_INT8 && job->dtype != DA_FP32) return sfail(DA_EINVAL, "unknown dtype");
+    if (job->dtype != DA_INT8 && job->dtype != DA_FP32)
+        return sfail(DA_EINVAL, "the request loop takes DA_INT8 or DA_FP32 jobs");
     if (job->steps < 0 || job->steps >= (1ll << 32) || (job->steps > 0 && !job->beta))
         return sfail(DA_EINVAL, "bad schedule");
     if (job->steps > 0 && !da::schedule_ok(job->beta, job->steps))
@@ -548,7 +549,7 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     q->int8 = job->dtype == DA_INT8;
     q->big = q->N > 1024;
     std::string why;
-    if (!da::build_instance(job->Q, q->N, q->int8, q->inst, why)) return sfail(DA_EINVAL, why);
+    if (!da::build_instance(job->Q, q->N, q->int8 ? da::kWInt8 : da::kWFp32, q->inst, why)) return sfail(DA_EINVAL, why);
     if (q->big) {
         q->shape = da::default_shape(q->N);
     } else {

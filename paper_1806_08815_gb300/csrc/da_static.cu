@@ -120,7 +120,7 @@ extern "C" da_status da_anneal_static(const int8_t* W, const int32_t* diag, int6
     for (long long t0 = 0; t0 < steps; t0 = p.t1) {
         p.t0 = t0;
         p.t1 = std::min<long long>(steps, t0 + (1ll << 14));
-        if (da::launch_step(true, s, p, out && out->trace, st) != cudaSuccess) return DA_ECUDA;
+        if (da::launch_step(da::kWInt8, s, p, out && out->trace, st) != cudaSuccess) return DA_ECUDA;
     }
     if (da::launch_best_fixup(R, sc, true, x, p.bestx, s.nwords(), st) != cudaSuccess) return DA_ECUDA;
     if (da::launch_recompute(true, W, diag, n, (int)ldw, 0, x, s.nwords(), 2 * R, nullptr, s.npad(), eex, 1, st,

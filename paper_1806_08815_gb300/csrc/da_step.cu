@@ -7,6 +7,7 @@ namespace da {
 
 cudaError_t launch_step_i8(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 cudaError_t launch_step_f32(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
+cudaError_t launch_step_i16(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 
 bool step_shape_supported(const StepShape& s)
 {
@@ -22,10 +23,15 @@ bool step_shape_supported(const StepShape& s)
     return vg && s.rpb >= 1 && s.rpb <= max_rpb;
 }
 
-cudaError_t launch_step(bool is_int8, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)
+cudaError_t launch_step(int wtype, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)
 {
     if (!step_shape_supported(s)) return cudaErrorInvalidConfiguration;
-    return is_int8 ? launch_step_i8(s, p, trace, st) : launch_step_f32(s, p, trace, st);
+    switch (wtype) {
+    case kWInt8: return launch_step_i8(s, p, trace, st);
+    case kWFp32: return launch_step_f32(s, p, trace, st);
+    case kWInt16: return launch_step_i16(s, p, trace, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace da

@@ -21,6 +21,20 @@ template <> struct Arith<int8_t> {
     static __device__ __forceinline__ long long store_e(E e) { return e; }
     static __device__ __forceinline__ E book(E e, H dE) { return e + (E)dE; }
 };
+// 16-bit integer couplings (the DA's fixed-point precision): as int8, wider W.
+template <> struct Arith<int16_t> {
+    using H = int32_t;
+    using E = long long;
+    static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
+    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
+    static __device__ __forceinline__ H apply(H h, int16_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
+    using Sign = int32_t;
+    static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1 : 1; }
+    static __device__ __forceinline__ H apply_signed(H h, int16_t w, Sign s) { return h + s * (H)w; }
+    static __device__ __forceinline__ E load_e(long long b) { return b; }
+    static __device__ __forceinline__ long long store_e(E e) { return e; }
+    static __device__ __forceinline__ E book(E e, H dE) { return e + (E)dE; }
+};
 template <> struct Arith<float> {
     using H = float;
     using E = double;
@@ -129,6 +143,28 @@ template <int V, bool CG> struct Row<int8_t, V, CG> {
                 const uint4 u = ldx<CG>(reinterpret_cast<const uint4*>(p) + q);
                 unpack(u.x, c + 16 * q); unpack(u.y, c + 16 * q + 4);
                 unpack(u.z, c + 16 * q + 8); unpack(u.w, c + 16 * q + 12);
+            }
+        }
+    }
+};
+
+template <int V, bool CG> struct Row<int16_t, V, CG> {
+    static __device__ __forceinline__ void unpack(uint32_t u, int16_t* c)
+    {
+        c[0] = (int16_t)(u & 0xFFFFu);
+        c[1] = (int16_t)(u >> 16);
+    }
+    static __device__ __forceinline__ void load(const int16_t* p, int16_t (&c)[V])
+    {
+        if constexpr (V == 4) {
+            const uint2 u = ldx<CG>(reinterpret_cast<const uint2*>(p));
+            unpack(u.x, c); unpack(u.y, c + 2);
+        } else {
+#pragma unroll
+            for (int q = 0; q < V / 8; ++q) {
+                const uint4 u = ldx<CG>(reinterpret_cast<const uint4*>(p) + q);
+                unpack(u.x, c + 8 * q); unpack(u.y, c + 8 * q + 2);
+                unpack(u.z, c + 8 * q + 4); unpack(u.w, c + 8 * q + 6);
             }
         }
     }

@@ -474,3 +474,51 @@ def test_move_energy_percentiles_match_brute_force(da, inst, dtype):
         assert np.allclose(got, ref, rtol=1e-6, atol=1e-6)
     grid = tuning.temperature_grid(ctx, n_states=16)
     assert 0 < grid["T_low"][0] <= grid["T_low"][1] <= grid["T_high"][0] <= grid["T_high"][1]
+
+
+def _int16_instance(inst, N, seed):
+    """An SK-Gaussian instance in the DA's fixed-point precision (16-bit couplers)."""
+    from paper_1806_08815_gb300 import binding
+    Qi, scale = binding.da_quantize(inst.sk_gaussian(N, seed).Q)
+    return Qi, scale
+
+
+@pytest.mark.parametrize("N,shape", [(100, (0, 0, 0)), (100, (4, 1, 4)), (100, (4, 2, 2)), (256, (8, 1, 2)),
+                                     (1024, (0, 0, 0)), (1024, (8, 4, 1)), (2100, (0, 0, 0))])
+def test_int16_fixed_point_trajectories(da, inst, N, shape):
+    """The fixed-point DA mode (16-bit couplers, 26-bit biases): bit-exact
+    trajectories against the oracle's integer mode, over launch shapes."""
+    import oracle
+    Qi, scale = _int16_instance(inst, N, 5)
+    assert np.abs(np.triu(Qi, 1)).max() <= 2 ** 15 - 1
+    beta = (inst.beta_linear(0.1, 10.0, 1200) / scale).astype(np.float32)
+    ctx = da.da_create(Qi, da.DA_INT16)
+    if shape[0]:
+        da.da_set_launch_shape(ctx, *shape)
+    R = 7 if N <= 1024 else 3
+    got = da.da_anneal(ctx, beta, 0.0, R, 8, trace=True)
+    ref = oracle.da_anneal(Qi, beta, R=R, seed=8, inc=0.0, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, Qi, True)
+
+
+def test_int16_draw_warp_pt_and_energies(da, inst):
+    import oracle
+    Qi, scale = _int16_instance(inst, 200, 6)
+    ctx = da.da_create(Qi, da.DA_INT16)
+    beta = (inst.beta_linear(0.1, 10.0, 800) / scale).astype(np.float32)
+    da.binding.da_set_draw_warp(ctx, True)
+    got = da.da_anneal(ctx, beta, 0.5 * scale, 5, 2, trace=True)
+    ref = oracle.da_anneal(Qi, beta, R=5, seed=2, inc=np.float32(0.5 * scale), trace=True, nthreads=NT)
+    _compare_anneal(got, ref, Qi, True)
+    betas = (inst.beta_geometric(0.2, 5.0, 6) / scale).astype(np.float32)
+    g = da.da_pt(ctx, betas, 10, 3, 4, swap_trace=True)
+    r = oracle.ptda(Qi, betas, 10, L=3, seed=4, nthreads=NT)
+    assert np.array_equal(g["swap_trace"], r["swap_trace"]) and np.array_equal(g["best_x"], r["x_best"])
+    rng = np.random.default_rng(1)
+    xp = oracle.pack(rng.integers(0, 2, (9, 200)))
+    assert np.array_equal(da.da_energy(ctx, xp), oracle.energy(Qi, xp).astype(float))
+    h = da.da_field_recompute(ctx, xp)
+    for k in range(9):
+        assert np.array_equal(h[k].astype(np.int64), oracle.fields_int(Qi, xp[k]) + np.diag(Qi))
+    with pytest.raises(da.DAError):
+        da.da_anneal_plain(ctx, beta, 0.0, 2, 0)

@@ -147,3 +147,21 @@ def test_scaled_float_conversion_matches_intrinsics(da):
     host = np.ldexp(v.astype(np.float32).astype(np.float64), -S.astype(np.int64))
     normal = (np.abs(host) >= 2.0 ** -126) & (np.abs(host) < 2.0 ** 128)
     assert np.array_equal(got[normal].astype(np.float64), host[normal])
+
+
+@pytest.mark.parametrize("N,R", [(130, 129), (1000, 150), (5000, 140)])
+def test_int16(da, N, R):
+    """16-bit couplings (two digit planes) at both ends of their range, 26-bit diagonal."""
+    rng = np.random.default_rng(N + 1)
+    Q = np.triu(rng.integers(-32767, 32768, (N, N)), 1).astype(np.int32)
+    Q[0, 1:] = -32767
+    Q[1, 2:] = 32767
+    np.fill_diagonal(Q, rng.integers(-(2 ** 25) + 1, 2 ** 25, N))
+    import oracle
+    ctx = da.da_create(Q, da.DA_INT16)
+    xp = oracle.pack(_states(rng, R, N))
+    assert np.array_equal(da.da_energy(ctx, xp), oracle.energy(Q, xp).astype(float))
+    h = da.da_field_recompute(ctx, xp)
+    d = np.diag(Q).astype(np.int64)
+    for r in sorted({0, 1, R - 1} | set(rng.choice(R, 6, replace=False))):
+        assert np.array_equal(h[r].astype(np.int64), oracle.fields_int(Q, xp[r]) + d), r

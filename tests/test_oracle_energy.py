@@ -181,3 +181,43 @@ def test_recompute_energy_is_the_rounded_exact_fixed_point_sum(orc):
             exact = sum(round(Fraction(float(inst.Q[i, i])) * scale) + int(sums[i])
                         for i in range(inst.N) if x[i])
             assert orc.recompute_energy_f32(inst.Q, orc.pack(x)[0]) == float(Fraction(exact) / (2 * scale))
+
+
+@pytest.mark.parametrize("kind", ["sk", "lattice", "diag_binds"])
+def test_quantize_scales_to_the_hardware_limits(orc, kind):
+    """The DA's fixed-point scaling: the binding limit is reached exactly, every
+    entry is within 1/2 of the scaled value, and the quantized energy is the
+    scaled energy up to the summed rounding (exact bound, on random states)."""
+    from paper_1806_08815_gb300 import instances
+    if kind == "sk":
+        Q = instances.sk_gaussian(200, 1).Q
+    elif kind == "lattice":
+        Q = instances.lattice2d(12, 1, True).Q
+    else:
+        Q = instances.sk_gaussian(60, 2).Q.copy()
+        np.fill_diagonal(Q, np.diag(Q) * 3000)
+    Qi, s = orc.quantize(Q)
+    off = np.triu(np.ones(Q.shape, bool), 1)
+    qmax = np.abs(Qi[off]).max()
+    dmax = np.abs(np.diag(Qi)).max()
+    assert qmax <= 2 ** 15 - 1 and dmax <= 2 ** 25 - 1
+    assert qmax == 2 ** 15 - 1 or dmax == 2 ** 25 - 1
+    err = Qi - s * np.triu(Q).astype(np.float64)
+    assert np.abs(err).max() <= 0.5
+    assert np.all(np.tril(Qi, -1) == 0)
+    rng = np.random.default_rng(4)
+    X = rng.integers(0, 2, (20, Q.shape[0]))
+    xp = orc.pack(X)
+    Ei = orc.energy(Qi, xp)
+    Ef = orc.energy(Q, xp)
+    bound = np.array([np.abs(err)[np.ix_(x == 1, x == 1)][np.triu_indices(x.sum())].sum() for x in X])
+    assert np.all(np.abs(Ei - s * Ef) <= bound + 1e-6 * np.abs(s * Ef) + 1e-6)
+
+
+def test_library_quantize_equals_oracle(orc):
+    from paper_1806_08815_gb300 import build, binding, instances
+    build.build()
+    for Q in (instances.sk_gaussian(150, 3).Q, instances.random_qubo(70, 2, False).Q, np.zeros((5, 5), np.float32)):
+        a, sa = binding.da_quantize(Q)
+        b, sb = orc.quantize(Q)
+        assert np.array_equal(a, b) and sa == sb
