@@ -260,6 +260,31 @@ def run_density(da, instances, per_density=8, R=100, T=100_000):
             "per_density": out}
 
 
+def run_fixed_point(da, instances, R=1024, T=200_000):
+    """The DA's fixed-point precision against fp32 on the headline workload: the SK-Gaussian
+    instance scaled to 16-bit couplers / 26-bit biases and rounded (da_quantize), annealed as a
+    DA_INT16 context with beta / scale; best states of both evaluated exactly in the original
+    fp32 problem."""
+    q = instances.sk_gaussian(C3["N"], C3["instance_seed"])
+    beta = instances.beta_linear(C3["beta0"], C3["beta1"], T)
+    ctx_f = da.da_create(q.Q)
+    rf = da.da_anneal(ctx_f, beta, C3["inc"], R, 11, recompute_every=C3["recompute_every"])
+    Qi, scale = da.da_quantize(q.Q)
+    ctx_i = da.da_create(Qi, da.DA_INT16)
+    ri = da.da_anneal(ctx_i, (beta / scale).astype(np.float32), C3["inc"], R, 11)
+    Ei = da.da_energy(ctx_f, ri["best_x"])
+    Ef = rf["best_E"]
+    Eref = float(min(Ef.min(), Ei.min()))
+    tol = 1e-6 * abs(Eref)
+    return {"workload": f"SK-Gaussian N={C3['N']}, {R} replicas, {T} steps, beta linear "
+                        f"{C3['beta0']} -> {C3['beta1']}; fp32 vs 16-bit couplers (scale {scale:.6g})",
+            "value": R * T * C3["N"] / ri["elapsed_s"], "unit": UNIT, "fp32_value": R * T * C3["N"] / rf["elapsed_s"],
+            "best_E_mean": {"fp32": float(Ef.mean()), "int16": float(Ei.mean())},
+            "best_E_min": {"fp32": float(Ef.min()), "int16": float(Ei.min())},
+            "hits_of_common_best": {"fp32": int((Ef <= Eref + tol).sum()), "int16": int((Ei <= Eref + tol).sum())},
+            "relative_gap_of_means": float((Ei.mean() - Ef.mean()) / abs(Ef.mean()))}
+
+
 def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30):
     """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
     [256, 8192], half bimodal / half Gaussian, R replicas, T steps, HBM budget 120 GB."""
@@ -510,6 +535,7 @@ def main():
         line["ptda"] = run_ptda(da, instances)
         line["served"] = run_served(da, instances)
         line["density"] = run_density(da, instances)
+        line["fixed_point"] = run_fixed_point(da, instances)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

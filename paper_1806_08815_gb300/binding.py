@@ -277,7 +277,7 @@ def da_energy(ctx: Context, x: np.ndarray) -> np.ndarray:
 
 def da_field_recompute(ctx: Context, x: np.ndarray) -> np.ndarray:
     xs = np.ascontiguousarray(np.atleast_2d(x), dtype=np.uint32)
-    h = np.zeros((xs.shape[0], ctx.N), np.int32 if ctx.dtype == DA_INT8 else np.float32)
+    h = np.zeros((xs.shape[0], ctx.N), np.float32 if ctx.dtype == DA_FP32 else np.int32)
     _check(lib().da_field_recompute(ctx.handle, _ptr(xs), xs.shape[0], _ptr(h)))
     return h
 
