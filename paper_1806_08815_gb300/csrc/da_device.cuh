@@ -101,18 +101,17 @@ __device__ __forceinline__ float exp_neg(float x)
 }
 
 // The Metropolis test u < exp_neg(x), x = -beta delta, as the step kernels
-// make it, in the log domain: every
-// trial's draw is kept as Lg = log2 U (hardware approximation, lg2_draw),
-// U = (w >> 8) + 1 in [1, 2^24], and the annealer forms s = delta beta log2(e)
-// + Lg with one fused multiply-add.  u < exp(-beta delta) is s < 24 up to the
-// error of Lg, of exp_neg and of the roundings of beta log2(e) and of s,
+// make it, in the log domain: every trial's draw is kept as Lg = log2 U
+// (hardware approximation, lg2_draw), U = (w >> 8) + 1 in [1, 2^24], and the
+// annealer forms s = delta beta log2(e) + Lg with one fused multiply-add and
+// t = s - 24 (exact wherever |t| < 12).  u < exp(-beta delta) is t < 0 up to
+// the error of Lg, of exp_neg and of the roundings of beta log2(e) and of s,
 // together far below 2^-15 for every argument (the tests bound each term); so
-// s < kLogLo accepts, s >= kLogHi rejects, and only trials in between (and
-// delta <= 0 trials whose s falls there) take the exact test
+// t < -kLogBand accepts, t > kLogBand rejects, and only trials with
+// |t| <= kLogBand (and delta <= 0 trials among them) take the exact test
 // delta <= 0 || u < exp_neg(x).
 constexpr float kLog2e = 1.44269504088896341f;
-constexpr float kLogLo = 24.0f - 3.0517578125e-05f;   // 24 -+ 2^-15 (exact in fp32)
-constexpr float kLogHi = 24.0f + 3.0517578125e-05f;
+constexpr float kLogBand = 3.0517578125e-05f;   // 2^-15
 
 __device__ __forceinline__ float lg2_draw(uint32_t w)
 {

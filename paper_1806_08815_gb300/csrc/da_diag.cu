@@ -43,9 +43,9 @@ __global__ void accept_log_kernel(const float* delta, const float* beta, const u
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float c = __fmul_rn(beta[i], da::kLog2e);
-    const float sv = __fmaf_rn(delta[i], c, da::lg2_draw(w[i]));
-    bool acc = sv < da::kLogLo;
-    const bool band = sv >= da::kLogLo && sv < da::kLogHi;
+    const float t = __fsub_rn(__fmaf_rn(delta[i], c, da::lg2_draw(w[i])), 24.0f);
+    bool acc = t < -da::kLogBand;
+    const bool band = fabsf(t) <= da::kLogBand;
     if (band) acc = delta[i] <= 0.0f || da::uniform01(w[i]) < da::exp_neg(-__fmul_rn(beta[i], delta[i]));
     out[i] = (uint8_t)((acc ? 1 : 0) | (band ? 2 : 0));
 }

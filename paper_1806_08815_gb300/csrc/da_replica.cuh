@@ -103,34 +103,18 @@ struct WarpReplica {
     }
 
     // One step t whose acceptance draws are L[v] = log2 U of this lane's trials
-    // (lg2_draw; from draw() or from a producer warp): s = delta beta log2(e) + L
-    // decides every trial outside the band [kLogLo, kLogHi); inside it the
-    // exact test recomputes the trial's Philox word.  `overlap` runs while row
-    // k is in flight.
+    // (lg2_draw; from draw() or from a producer warp), decided in the log domain
+    // (decide_log; the rare trials near the threshold by decide_exact).
+    // `overlap` runs while row k is in flight.
     template <bool FULL, class Keys, class Overlap>
     __device__ __forceinline__ int step_log(long long t, float beta, float inc, const float (&L)[V], const Keys& keys,
                                             Overlap&& overlap)
     {
         const float Eoff = __fmul_rn(__uint2float_rn(m), inc);
-        const float c = __fmul_rn(beta, kLog2e);
-        uint32_t accm = 0, band = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
-            const float sv = __fmaf_rn(delta, c, L[v]);
-            accm |= (uint32_t)(sv < kLogLo) << v;
-            band |= (uint32_t)(sv >= kLogLo && sv < kLogHi) << v;
-        }
-        if (__any_sync(0xffffffffu, band != 0u)) {
-            while (band) {
-                const int v = __ffs(band) - 1;
-                band &= band - 1;
-                const float delta = A::delta(A::signed_field(select_slot<H, V>(h, v), (xm >> v) & 1u), Eoff);
-                const float ax = -__fmul_rn(beta, delta);
-                const uint32_t wd = pick(philox4x32_10((uint32_t)((base + v) >> 2), (uint32_t)t, rep, 0u, keys), v & 3);
-                accm |= (uint32_t)(delta <= 0.0f || uniform01(wd) < exp_neg(ax)) << v;
-            }
-        }
+        bool unsure;
+        uint32_t accm = decide_log<A, V>(h, xm, Eoff, __fmul_rn(beta, kLog2e), L, unsure);
+        if (__any_sync(0xffffffffu, unsure))
+            accm = decide_exact<A, V>(h, xm, Eoff, beta, L, accm, base, (uint32_t)t, rep, keys);
         return choose_and_flip<FULL>(t, accm, keys, overlap);
     }
 

@@ -117,28 +117,12 @@ __global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_
         if (!per_rep && t + 1 < p.t1) beta_next = p.beta[t + 1];
         const float Eoff = __fmul_rn(__uint2float_rn(m), p.inc);
 
-        // (a) + (b): every trial of this lane in the log domain (lg2_draw),
-        // branch-free except for the rare trials inside the band, which take the
-        // exact test with their Philox word recomputed.
-        const float c = __fmul_rn(beta, kLog2e);
-        uint32_t accm = 0, band = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float delta = A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff);
-            const float sv = __fmaf_rn(delta, c, lg[v]);
-            accm |= (uint32_t)(sv < kLogLo) << v;
-            band |= (uint32_t)(sv >= kLogLo && sv < kLogHi) << v;
-        }
-        if (__any_sync(0xffffffffu, band != 0u)) {
-            while (band) {
-                const int v = __ffs(band) - 1;
-                band &= band - 1;
-                const float delta = A::delta(A::signed_field(select_slot<H, V>(h, v), (xm >> v) & 1u), Eoff);
-                const float ax = -__fmul_rn(beta, delta);
-                const uint32_t wd = pick(philox4x32_10((uint32_t)((base + v) >> 2), (uint32_t)t, rep, 0u, keys), v & 3);
-                accm |= (uint32_t)(delta <= 0.0f || uniform01(wd) < exp_neg(ax)) << v;
-            }
-        }
+        // (a) + (b): every trial of this lane in the log domain (decide_log),
+        // the rare trials near the threshold by the exact test (decide_exact).
+        bool unsure;
+        uint32_t accm = decide_log<A, V>(h, xm, Eoff, __fmul_rn(beta, kLog2e), lg, unsure);
+        if (__any_sync(0xffffffffu, unsure))
+            accm = decide_exact<A, V>(h, xm, Eoff, beta, lg, accm, base, (uint32_t)t, rep, keys);
         if constexpr (!FULL) accm &= valid;
 
         // (c) uniform choice among the accepted trials

@@ -13,6 +13,7 @@ template <> struct Arith<int8_t> {
     using E = long long;  // tracked energy
     static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
+    static __device__ __forceinline__ float delta0(H dE) { return __int2float_rn(dE); }   // delta at E_off = +0
     static __device__ __forceinline__ H apply(H h, int8_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
     using Sign = int32_t;
     static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1 : 1; }
@@ -27,6 +28,7 @@ template <> struct Arith<int16_t> {
     using E = long long;
     static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return x ? -g : g; }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(__int2float_rn(dE), Eoff); }
+    static __device__ __forceinline__ float delta0(H dE) { return __int2float_rn(dE); }
     static __device__ __forceinline__ H apply(H h, int16_t w, bool minus) { return minus ? h - (H)w : h + (H)w; }
     using Sign = int32_t;
     static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1 : 1; }
@@ -43,6 +45,7 @@ template <> struct Arith<float> {
         return __int_as_float(__float_as_int(g) ^ (int)(x << 31));
     }
     static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
+    static __device__ __forceinline__ float delta0(H dE) { return dE; }   // dE - (+0) = dE, also for dE = -0
     static __device__ __forceinline__ H apply(H h, float w, bool minus) { return minus ? __fsub_rn(h, w) : __fadd_rn(h, w); }
     using Sign = float;
     static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1.0f : 1.0f; }
@@ -188,6 +191,63 @@ __device__ __forceinline__ uint32_t gather_word(uint32_t bits, int lane)
 #pragma unroll
     for (int o = 1; o < P; o <<= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
     return m;
+}
+
+// Trials (a)-(b) of one lane's V variables in the log domain (lg2_draw,
+// kLogBand in da_device.cuh): returns the mask of surely accepted trials and
+// sets `unsure` when any trial has |t| <= kLogBand and must take the exact
+// test (decide_exact).  With E_off = +0 (no offset, or no step without a flip
+// since the last one) the subtraction is left out: it would return delta
+// unchanged.
+template <typename A, int V>
+__device__ __forceinline__ uint32_t decide_log(const typename A::H (&h)[V], uint32_t xm, float Eoff, float c,
+                                               const float (&L)[V], bool& unsure)
+{
+    uint32_t acc = 0;
+    float tmin = 1.0f;
+    if (Eoff == 0.0f) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float t = __fsub_rn(__fmaf_rn(A::delta0(A::signed_field(h[v], (xm >> v) & 1u)), c, L[v]), 24.0f);
+            acc |= (uint32_t)(t < -kLogBand) << v;
+            tmin = fminf(tmin, fabsf(t));
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const float t = __fsub_rn(__fmaf_rn(A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff), c, L[v]), 24.0f);
+            acc |= (uint32_t)(t < -kLogBand) << v;
+            tmin = fminf(tmin, fabsf(t));
+        }
+    }
+    unsure = tmin <= kLogBand;
+    return acc;
+}
+
+// The trials of this lane with |t| <= kLogBand, decided by the exact test
+// delta <= 0 || u < exp_neg(-beta delta) with u from the trial's Philox word
+// (recomputed: block (i/4, t, rep, 0), lane i%4 for variable i = base + v).
+template <typename A, int V, class Keys>
+__device__ __forceinline__ uint32_t decide_exact(const typename A::H (&h)[V], uint32_t xm, float Eoff, float beta,
+                                                 const float (&L)[V], uint32_t acc, int base, uint32_t step,
+                                                 uint32_t rep, const Keys& keys)
+{
+    const float c = __fmul_rn(beta, kLog2e);
+    uint32_t band = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float t = __fsub_rn(__fmaf_rn(A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff), c, L[v]), 24.0f);
+        band |= (uint32_t)(fabsf(t) <= kLogBand) << v;
+    }
+    while (band) {
+        const int v = __ffs(band) - 1;
+        band &= band - 1;
+        const float delta = A::delta(A::signed_field(select_slot<typename A::H, V>(h, v), (xm >> v) & 1u), Eoff);
+        const float ax = -__fmul_rn(beta, delta);
+        const uint32_t wd = pick(philox4x32_10((uint32_t)((base + v) >> 2), step, rep, 0u, keys), v & 3);
+        acc |= (uint32_t)(delta <= 0.0f || uniform01(wd) < exp_neg(ax)) << v;
+    }
+    return acc;
 }
 
 }  // namespace step_detail
