@@ -353,6 +353,21 @@ def cpu_baseline(sample_R=None, sample_T=32768):
                       f"{dt:.1f} s wall"}
 
 
+def rank_seed(rank: int) -> int:
+    """Replicas only: rank r anneals its own replica set with seed C3 seed + r (no exchange)."""
+    return C3["seed"] + rank
+
+
+def max_over_ranks(t: float, dist, device) -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -408,7 +423,7 @@ def main():
     N, R, T, P = C3["N"], C3["replicas"], args.steps_per_anneal, C3["recompute_every"]
     q = instances.sk_gaussian(N, C3["instance_seed"])
     beta = instances.beta_linear(C3["beta0"], C3["beta1"], T)
-    seed = C3["seed"] + rank            # weak scaling: each rank anneals its own 1024 replicas
+    seed = rank_seed(rank)              # weak scaling: each rank anneals its own 1024 replicas
     ctx = da.da_create(q.Q)
     beta_dev = torch.from_numpy(beta).to(dev)
     Wd = da.da_words(N)
@@ -454,11 +469,7 @@ def main():
     launches, step_ms = da.da_profile_read(ctx)
     da.da_profile_enable(ctx, False)
     clk = clocks.stop()
-    t_step = float(np.mean(times))
-    if dist:
-        tt = torch.tensor([t_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(float(np.mean(times)), dist, dev)
     trials = R * T * N
     value = world * trials / t_step
 
