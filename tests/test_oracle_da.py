@@ -76,6 +76,37 @@ def test_one_step_transition_law(orc, integer, m, inc):
     assert counts[~keep].sum() <= 10
 
 
+def test_acceptance_boost_at_low_temperature(orc):
+    """Eq. 1-3: at a local minimum and low temperature the parallel-trial acceptance
+    P_p = 1 - prod(1 - A_i) is close to N times the single-trial P_s = mean(A_i); the
+    oracle's frequency of steps with a flip matches P_p (A_i from brute-force energies)."""
+    N = 12
+    inst = instances.random_qubo(N, 5, True, -4, 4)
+    # descend to a local minimum by brute-force single flips
+    x = np.zeros(N, np.uint8)
+    while True:
+        E0 = _E(inst.Q, x)
+        d = []
+        for i in range(N):
+            y = x.copy(); y[i] ^= 1
+            d.append(_E(inst.Q, y) - E0)
+        i = int(np.argmin(d))
+        if d[i] >= 0:
+            break
+        x[i] ^= 1
+    assert min(d) > 0, "need a strict local minimum"
+    for beta in (1.0, 2.0):
+        A = np.array([_accept_prob(orc, np.float32(v), beta) for v in d])
+        Pp, Ps = 1 - np.prod(1 - A), A.mean()
+        if beta == 2.0:
+            assert 0.9 * N < Pp / Ps <= N
+        n = 20_000
+        xp = orc.pack(x)[0]
+        flips = sum(orc.da_one_step(inst.Q, xp, 0, beta, 0.0, seed=99, t=3, replica=r)[0] >= 0 for r in range(n))
+        sd = np.sqrt(n * Pp * (1 - Pp))
+        assert abs(flips - n * Pp) < 5 * sd + 1
+
+
 def test_infinite_temperature_choice_is_uniform(orc):
     """At beta = 0 every trial is accepted (p = 1 > u except u = 1), so the flip is uniform."""
     N = 24
