@@ -212,7 +212,7 @@ da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 // After a call's stream work has completed: a bounded wait inside a kernel
 // (the tensor-core recompute's pipeline, the step's producer/annealer
 // handshake) that gave up invalidates the call's results.
-da_status check_tc(da_ctx* c)
+da_status check_kernel_flag(da_ctx* c)
 {
     int flag = 0;
     DA_CU(cudaMemcpy(&flag, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -563,7 +563,7 @@ da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int3
     DA_CU(cudaEventRecord(c->ev1, st));
     if (!out) {
         DA_CU(cudaStreamSynchronize(st));
-        return check_tc(c);
+        return check_kernel_flag(c);
     }
     const size_t words = (size_t)da_words(c->N);
     std::vector<double> hres((size_t)4 * R);
@@ -577,7 +577,7 @@ da_status da_anneal(da_ctx* c, const float* beta, int64_t steps, float inc, int3
     if (want_trace && steps > 0)
         DA_CU(cudaMemcpyAsync(out->trace, b.base + b.L.trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
-    if (da_status e = check_tc(c)) return e;
+    if (da_status e = check_kernel_flag(c)) return e;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     out->elapsed_s = ms * 1e-3;
@@ -691,7 +691,7 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     if (want_trace && sweeps > 0)
         DA_CU(cudaMemcpyAsync(out->swap_trace, strace, n_sw * (size_t)sweeps, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
-    if (da_status e = check_tc(c)) return e;
+    if (da_status e = check_kernel_flag(c)) return e;
     if (!out) return DA_OK;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
@@ -745,7 +745,7 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     if (h) DA_CU(cudaMemcpyAsync(h, hd, (size_t)R * c->N * 4, cudaMemcpyDeviceToHost, st));
     if (E) DA_CU(cudaMemcpyAsync(eh.data(), ed, (size_t)R * 8, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
-    if (da_status e = check_tc(c)) return e;
+    if (da_status e = check_kernel_flag(c)) return e;
     if (E)
         for (int r = 0; r < R; ++r)
             E[r] = is_int(c) ? (double)eh[r] : reinterpret_cast<const double*>(eh.data())[r];
@@ -796,7 +796,7 @@ da_status da_anneal_plain(da_ctx* c, const float* beta, int64_t steps, float inc
     if (want_trace && steps > 0)
         DA_CU(cudaMemcpyAsync(out->trace, base + o_trace, (size_t)R * steps * 4, cudaMemcpyDeviceToHost, st));
     DA_CU(cudaStreamSynchronize(st));
-    if (da_status e = check_tc(c)) return e;
+    if (da_status e = check_kernel_flag(c)) return e;
     if (!out) return DA_OK;
     float ms = 0.f;
     DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));

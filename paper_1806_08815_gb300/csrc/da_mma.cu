@@ -29,6 +29,9 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "da_fixed.cuh"
 #include "da_internal.h"
@@ -422,20 +425,25 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
                                 cudaStream_t st, long long* scratch, void* state_ws)
 {
     if (R <= 0) return cudaSuccess;
-    static bool attr_set[2][64] = {};
+    // the dynamic shared-memory limit of each kernel form, set once per device
+    static std::mutex attr_mu;
+    static std::set<std::pair<int, int>> attr_done;
     int dev = 0;
     cudaGetDevice(&dev);
     const size_t smem = smem_bytes(op.limbs);
     const int max_limbs = is_int8 ? 2 : kMaxLimbs;   // integer couplings: 1 (int8) or 2 (int16) planes
     if (op.limbs < 1 || op.limbs > max_limbs) return cudaErrorInvalidValue;
-    if (dev < 64 && !attr_set[is_int8][dev]) {
-        const int bytes = (int)smem_bytes(max_limbs);
-        cudaError_t e = is_int8 ? cudaFuncSetAttribute(recompute_tc_kernel<true>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                                : cudaFuncSetAttribute(recompute_tc_kernel<false>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        attr_set[is_int8][dev] = true;
+    {
+        std::lock_guard<std::mutex> lock(attr_mu);
+        if (!attr_done.count({is_int8 ? 1 : 0, dev})) {
+            const int bytes = (int)smem_bytes(max_limbs);
+            cudaError_t e = is_int8 ? cudaFuncSetAttribute(recompute_tc_kernel<true>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                                    : cudaFuncSetAttribute(recompute_tc_kernel<false>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+            attr_done.insert({is_int8 ? 1 : 0, dev});
+        }
     }
 
     const int rtiles = (R + kBM - 1) / kBM;
