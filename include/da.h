@@ -396,6 +396,13 @@ da_status da_percentiles(const double* v, int64_t n, const double* q, int32_t nq
  * the exact test delta <= 0 || u < exp_neg(-fl(beta delta)). */
 da_status da_diag_log_uniform(const uint32_t* w, float* L, int64_t n);
 da_status da_diag_accept_log(const float* delta, const float* beta, const uint32_t* w, uint8_t* out, int64_t n);
+/* The bounded wait used by every pipelined kernel (tensor-core recompute,
+ * producer-warp step): out3[0] = 1 if a wait on an mbarrier that received its
+ * arrival succeeded, out3[1] = 0 if a wait on an mbarrier that never receives
+ * one gave up, out3[2] = nanoseconds that wait took (about ns, 1 <= ns <= 1e9).
+ * No kernel hangs on a lost arrival: it records the failure and returns.
+ * Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_diag_bounded_wait(int64_t ns, int64_t* out3);
 /* The fixed-point conversions of the exact recompute (da_field_recompute) as
  * the kernels evaluate them, in integer arithmetic (got), beside the same
  * conversions through the 64-bit conversion instructions (ref):

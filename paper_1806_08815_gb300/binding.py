@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
     L.da_quantize.restype = ctypes.c_int
     L.da_percentiles.argtypes = [_P, i64, _P, i32, _P]
     L.da_percentiles.restype = ctypes.c_int
+    L.da_diag_bounded_wait.argtypes = [i64, _P]
+    L.da_diag_bounded_wait.restype = ctypes.c_int
     L.da_diag_log_uniform.argtypes = [_P, _P, i64]
     L.da_diag_accept_log.argtypes = [_P, _P, _P, _P, i64]
     L.da_diag_log_uniform.restype = ctypes.c_int
@@ -343,6 +345,12 @@ def da_percentiles(v, q) -> np.ndarray:
     qs = np.ascontiguousarray(q, dtype=np.float64)
     out = np.zeros(qs.size)
     _check(lib().da_percentiles(_ptr(vs), vs.size, _ptr(qs), qs.size, _ptr(out)))
+    return out
+
+
+def da_diag_bounded_wait(ns: int) -> np.ndarray:
+    out = np.zeros(3, np.int64)
+    _check(lib().da_diag_bounded_wait(int(ns), _ptr(out)))
     return out
 
 

@@ -8,6 +8,7 @@
 #include "da.h"
 #include "da_device.cuh"
 #include "da_fixed.cuh"
+#include "da_tc.cuh"
 
 namespace {
 
@@ -27,6 +28,23 @@ __global__ void philox_kernel(const uint32_t* in, uint32_t* out, long long n)
     out[4 * i + 1] = r.y;
     out[4 * i + 2] = r.z;
     out[4 * i + 3] = r.w;
+}
+
+// The bounded mbarrier wait of the pipelined kernels: one barrier that receives
+// its arrival (the wait succeeds) and one that never does (the wait must give
+// up after `ns` nanoseconds instead of hanging).  out = {arrived wait result,
+// abandoned wait result, ns spent in the abandoned wait}.
+__global__ void wait_probe_kernel(unsigned long long ns, unsigned long long* out)
+{
+    __shared__ uint64_t bars[2];
+    if (threadIdx.x != 0) return;
+    da::tc::mbar_init(&bars[0], 1);
+    da::tc::mbar_init(&bars[1], 1);
+    da::tc::mbar_arrive(&bars[0]);
+    out[0] = da::tc::mbar_wait(&bars[0], 0, 1u << 20, ns) ? 1ull : 0ull;
+    const uint64_t t0 = da::tc::global_ns();
+    out[1] = da::tc::mbar_wait(&bars[1], 0, 0xffffffffu, ns) ? 1ull : 0ull;
+    out[2] = da::tc::global_ns() - t0;
 }
 
 __global__ void log_uniform_kernel(const uint32_t* w, float* L, long long n)
@@ -171,5 +189,14 @@ extern "C" da_status da_diag_accept_log(const float* delta, const float* beta, c
         const float* da_ = static_cast<const float*>(a);
         accept_log_kernel<<<(unsigned)((n + 255) / 256), 256>>>(da_, da_ + n, reinterpret_cast<const uint32_t*>(da_ + 2 * n),
                                                                 static_cast<uint8_t*>(b), n);
+    });
+}
+
+extern "C" da_status da_diag_bounded_wait(int64_t ns, int64_t* out3)
+{
+    if (ns < 1 || ns > 1000000000ll || !out3) return DA_EINVAL;
+    const int64_t zero = 0;
+    return run(sizeof(zero), 3 * sizeof(unsigned long long), &zero, out3, [&](void*, void* b) {
+        wait_probe_kernel<<<1, 32>>>((unsigned long long)ns, static_cast<unsigned long long*>(b));
     });
 }

@@ -522,3 +522,12 @@ def test_int16_draw_warp_pt_and_energies(da, inst):
         assert np.array_equal(h[k].astype(np.int64), oracle.fields_int(Qi, xp[k]) + np.diag(Qi))
     with pytest.raises(da.DAError):
         da.da_anneal_plain(ctx, beta, 0.0, 2, 0)
+
+
+def test_bounded_wait_gives_up_instead_of_hanging(da):
+    """The mbarrier wait of the pipelined kernels returns failure after its time limit
+    when the arrival never comes (and success when it does), so a lost arrival ends a
+    kernel with an error flag rather than a hung GPU."""
+    ok, abandoned, ns = da.binding.da_diag_bounded_wait(2_000_000)
+    assert ok == 1 and abandoned == 0
+    assert 2_000_000 <= ns < 200_000_000
