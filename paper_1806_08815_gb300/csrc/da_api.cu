@@ -72,26 +72,37 @@ namespace {
 bool is_int(const da_ctx* c) { return c->dtype != DA_FP32; }
 
 // Default launch shape: one warp per replica up to N = 1024 (V <= 32
-// variables per lane); beyond that 8 warps per replica, with shapes that keep
-// the registers within one wave of 7+ replicas per SM and spill nothing.
-StepShape auto_shape(int N)
+// variables per lane).  Beyond, the fewest warps per replica that cover N
+// with V <= 32 (G = 2, 4 or 8), doubled while the launch has fewer than 1024
+// warps (few replicas: more warps per replica keep the SMs busy); V the
+// smallest supported width for that G.  Register budgets keep every choice in
+// one wave for the replica counts that select it.
+StepShape auto_shape(int N, int R)
 {
     StepShape s;
     if (N <= 1024) {
         int V = 4;
         while (32 * V < N) V *= 2;
         s.V = V; s.G = 1; s.rpb = 4;
-    } else {
-        int V = 8;
-        while (32 * 8 * V < N) V *= 2;
-        s.V = V; s.G = 8; s.rpb = 1;
+        return s;
     }
+    auto width = [N](int G) {
+        int V = G == 8 ? 8 : 4;
+        while (32 * V * G < N) V *= 2;
+        return V;
+    };
+    int G = 2;
+    while (32 * 32 * G < N) G *= 2;
+    while (G < 8 && (long long)R * G < 1024) G *= 2;
+    s.G = G;
+    s.V = width(G);
+    s.rpb = G == 2 ? 2 : 1;
     return s;
 }
 
-StepShape shape_for(const da_ctx* c)
+StepShape shape_for(const da_ctx* c, int R)
 {
-    StepShape s = c->forced.V > 0 ? c->forced : auto_shape(c->N);
+    StepShape s = c->forced.V > 0 ? c->forced : auto_shape(c->N, R);
     s.ws = s.G == 1 && c->draw_warp;
     return s;
 }
@@ -370,7 +381,7 @@ bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::str
     return true;
 }
 
-StepShape default_shape(int N) { return auto_shape(N); }
+StepShape default_shape(int N, int R) { return auto_shape(N, R); }
 
 void set_last_error(const std::string& msg) { g_err = msg; }
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S)
@@ -527,7 +538,7 @@ static da_status anneal_common(da_ctx* c, const float* beta, bool beta_on_host, 
     if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
     if (recompute_every < 0) return fail(DA_EINVAL, "recompute_every < 0");
     if (beta_on_host && !da::schedule_ok(beta, steps)) return fail(DA_EINVAL, "beta must be finite and >= 0");
-    const StepShape s = shape_for(c);
+    const StepShape s = shape_for(c, R);
     if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
     const Layout L = plan(c, s, R, steps, beta_on_host, want_trace, 0);
     if (da_status e = ensure_ws(c, L.total)) return e;
@@ -634,7 +645,7 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     CtxLock lock(c);
     cudaStream_t st = c->stream;
     const int R = L * K;
-    const StepShape s = shape_for(c);
+    const StepShape s = shape_for(c, R);
     if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
     const bool want_trace = out && out->swap_trace && K > 1;
     const size_t n_sw = (size_t)L * std::max(K - 1, 0);

@@ -161,8 +161,8 @@ struct HostInstance {
 };
 bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why);
 
-// The default launch shape of the step kernel for N variables.
-StepShape default_shape(int N);
+// The default launch shape of the step kernel for N variables and R replicas.
+StepShape default_shape(int N, int R);
 
 // True when every entry of a host schedule is finite and >= 0 (the kernels'
 // fast Metropolis test relies on beta >= 0).

@@ -551,7 +551,7 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     std::string why;
     if (!da::build_instance(job->Q, q->N, q->int8 ? da::kWInt8 : da::kWFp32, q->inst, why)) return sfail(DA_EINVAL, why);
     if (q->big) {
-        q->shape = da::default_shape(q->N);
+        q->shape = da::default_shape(q->N, job->replicas);
     } else {
         int V = 4;
         while (32 * V < q->N) V *= 2;

@@ -15,7 +15,7 @@ bool step_shape_supported(const StepShape& s)
     switch (s.G) {
     case 1: vg = s.V == 4 || s.V == 8 || s.V == 16 || s.V == 32; break;
     case 2: vg = s.V == 4 || s.V == 8 || s.V == 16 || s.V == 32; break;
-    case 4: vg = s.V == 4 || s.V == 8 || s.V == 16; break;
+    case 4: vg = s.V == 4 || s.V == 8 || s.V == 16 || s.V == 32; break;
     case 8: vg = s.V == 8 || s.V == 16 || s.V == 32; break;
     default: vg = false;
     }

@@ -40,7 +40,7 @@ namespace da {
 namespace step_detail {
 
 template <typename Tw, int V, int G, bool FULL, bool TRACE>
-__global__ void __launch_bounds__(32 * G * Occupancy<G>::rpb, Occupancy<G>::min_blocks)
+__global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G, V>::min_blocks)
     step_kernel(const __grid_constant__ StepParams p)
 {
     using A = Arith<Tw>;
@@ -464,7 +464,7 @@ cudaError_t launch_typed(const StepShape& s, const StepParams& p, bool trace, cu
     if (s.V == VV && s.G == GG) return launch_vg<Tw, VV, GG>(s, p, trace, st);
     DA_CASE(4, 1) DA_CASE(8, 1) DA_CASE(16, 1) DA_CASE(32, 1)
     DA_CASE(4, 2) DA_CASE(8, 2) DA_CASE(16, 2) DA_CASE(32, 2)
-    DA_CASE(4, 4) DA_CASE(8, 4) DA_CASE(16, 4)
+    DA_CASE(4, 4) DA_CASE(8, 4) DA_CASE(16, 4) DA_CASE(32, 4)
     DA_CASE(8, 8) DA_CASE(16, 8) DA_CASE(32, 8)
 #undef DA_CASE
     return cudaErrorInvalidConfiguration;

@@ -180,6 +180,12 @@ template <> struct Occupancy<1> { static constexpr int rpb = 4, min_blocks = 2; 
 template <> struct Occupancy<2> { static constexpr int rpb = 2, min_blocks = 4; };
 template <> struct Occupancy<4> { static constexpr int rpb = 1, min_blocks = 7; };
 template <> struct Occupancy<8> { static constexpr int rpb = 1, min_blocks = 2; };
+// Per (G, V): as Occupancy<G>, except G = 4 with V = 32, whose 32 fields per lane need
+// more registers than 7 blocks of 4 warps per SM leave (3 blocks: 12 warps per SM).
+template <int G, int V> struct OccupancyGV {
+    static constexpr int rpb = Occupancy<G>::rpb, min_blocks = Occupancy<G>::min_blocks;
+};
+template <> struct OccupancyGV<4, 32> { static constexpr int rpb = 1, min_blocks = 3; };
 
 // The state words of a replica are standard bit-packed words (x_i is bit i%32
 // of word i/32); a lane's V bits are one slice of word (w*32V + l*V) / 32.

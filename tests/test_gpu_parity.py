@@ -195,7 +195,8 @@ def test_draw_warp_on_and_off(da, inst, N, dtype):
 
 
 @pytest.mark.parametrize("N,shape", [(300, (0, 0, 0)), (300, (16, 1, 2)), (1000, (0, 0, 0)), (1000, (8, 4, 1)),
-                                     (1500, (0, 0, 0)), (2100, (0, 0, 0)), (2100, (16, 8, 1))])
+                                     (1500, (0, 0, 0)), (1500, (32, 2, 2)), (2100, (0, 0, 0)), (2100, (16, 8, 1)),
+                                     (3000, (32, 4, 1))])
 def test_int8_larger_sizes(da, inst, N, shape):
     import oracle
     q = inst.sk_bimodal(N, 3)
@@ -208,7 +209,7 @@ def test_int8_larger_sizes(da, inst, N, shape):
     _compare_anneal(got, ref, q.Q, True)
 
 
-@pytest.mark.parametrize("shape", [(0, 0, 0), (4, 2, 2), (8, 1, 4), (8, 4, 1), (16, 2, 2)])
+@pytest.mark.parametrize("shape", [(0, 0, 0), (4, 2, 2), (8, 1, 4), (8, 4, 1), (16, 2, 2), (32, 4, 1)])
 def test_fp32_sk_gaussian_with_recompute(da, inst, shape):
     import oracle
     q = inst.sk_gaussian(256, 5)
