@@ -82,13 +82,31 @@ struct WarpReplica {
     template <class Keys>
     __device__ __forceinline__ void draw(uint32_t tt, const Keys& keys)
     {
+        // the NQ Philox4x32-10 blocks round by round, so that their independent
+        // multiply-xor chains interleave
+        uint32_t c0[NQ], c1[NQ], c2[NQ], c3[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) { c0[q] = (uint32_t)(base >> 2) + q; c1[q] = tt; c2[q] = rep; c3[q] = 0u; }
+#pragma unroll
+        for (int round = 0; round < 10; ++round) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint64_t pa = (uint64_t)kPhiloxMulA * c0[q];
+                const uint64_t pb = (uint64_t)kPhiloxMulB * c2[q];
+                const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1[q] ^ keys.a[round];
+                const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3[q] ^ keys.b[round];
+                c1[q] = (uint32_t)pb;
+                c3[q] = (uint32_t)pa;
+                c0[q] = n0;
+                c2[q] = n2;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const u32x4 w = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
-            lg[4 * q] = lg2_draw(w.x);
-            lg[4 * q + 1] = lg2_draw(w.y);
-            lg[4 * q + 2] = lg2_draw(w.z);
-            lg[4 * q + 3] = lg2_draw(w.w);
+            lg[4 * q] = lg2_draw(c0[q]);
+            lg[4 * q + 1] = lg2_draw(c1[q]);
+            lg[4 * q + 2] = lg2_draw(c2[q]);
+            lg[4 * q + 3] = lg2_draw(c3[q]);
         }
     }
 
