@@ -182,16 +182,19 @@ da_status da_set_draw_warp(da_ctx* ctx, int32_t on);
  *                  device.
  *   recompute_every  DA_FP32 only: recompute the fields exactly every this many
  *                  steps to bound the fp32 drift (0 = never).  Ignored for
- *                  DA_INT8, whose fields are exact.
- * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+ *                  DA_INT8 and DA_INT16, whose fields are exact.
+ * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA, DA_ETIMEOUT (a bounded wait inside a
+ * pipelined kernel gave up; the results are invalid). */
 da_status da_anneal(da_ctx* ctx, const float* beta_schedule, int64_t steps, float offset_inc,
                     int32_t replicas, uint64_t seed, int64_t recompute_every, da_result* out);
 
 /* As da_anneal, with the schedule and every output in device memory, queued
  * on `stream` (a cudaStream_t; NULL = the legacy default stream) and
  * returning without waiting.  The device schedule is not inspected: its
- * entries must be finite and >= 0 (other values give undefined results).  The context's workspace is reused: calls on one
- * context must be ordered on one stream. */
+ * entries must be finite and >= 0 (other values give undefined results).
+ * The context's workspace is reused: calls on one context must be ordered on
+ * one stream.  A bounded wait that gave up in a queued call is reported
+ * (DA_ETIMEOUT) by the next blocking call on the context. */
 da_status da_anneal_async(da_ctx* ctx, const float* beta_schedule_dev, int64_t steps, float offset_inc,
                           int32_t replicas, uint64_t seed, int64_t recompute_every,
                           const da_dev_result* out, void* stream);
