@@ -532,3 +532,20 @@ def test_bounded_wait_gives_up_instead_of_hanging(da):
     ok, abandoned, ns = da.binding.da_diag_bounded_wait(2_000_000)
     assert ok == 1 and abandoned == 0
     assert 2_000_000 <= ns < 200_000_000
+
+
+@pytest.mark.parametrize("dtype,shape", [("i8", (0, 0, 0)), ("f32", (0, 0, 0)), ("f32", (32, 4, 1))])
+def test_largest_instances(da, inst, dtype, shape):
+    """N = 8192 (the largest the library takes; G = 8 warps of 32 variables per lane) and
+    N = 4096 on G = 4: bit-exact trajectories with a recompute inside the run."""
+    import oracle
+    N = 8192 if shape[0] == 0 else 4096
+    q = inst.sk_bimodal(N, 1) if dtype == "i8" else inst.sk_gaussian(N, 1)
+    beta = inst.beta_linear(0.1, 3.0 if dtype == "i8" else 9.0, 700)
+    ctx = da.da_create(q.Q)
+    if shape[0]:
+        da.da_set_launch_shape(ctx, *shape)
+    rec = 0 if dtype == "i8" else 512
+    got = da.da_anneal(ctx, beta, 0.0, 3, 21, recompute_every=rec, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=3, seed=21, inc=0.0, recompute_every=rec, trace=True, nthreads=NT)
+    _compare_anneal(got, ref, q.Q, dtype == "i8")
