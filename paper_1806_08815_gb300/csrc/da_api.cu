@@ -51,6 +51,7 @@ struct da_ctx {
     int S = 0;  // fixed-point scale of the fp32 recompute
     int device = 0;
     void* W = nullptr;
+    void* Wf = nullptr;  // DA_INT8: the couplings as exact fp32, for the step kernel
     void* diag = nullptr;
     da::TcOperand tc;  // digit planes of W for the tensor-core recompute
     void* ws = nullptr;
@@ -68,8 +69,13 @@ struct da_ctx {
 
 namespace {
 
-// Integer couplings (DA_INT8, DA_INT16): int32 fields, exact int64 energies.
+// Integer couplings (DA_INT8, DA_INT16): exact fields, exact int64 energies.
 bool is_int(const da_ctx* c) { return c->dtype != DA_FP32; }
+
+// The step kernel's coupling form: DA_INT8 contexts anneal on their couplings
+// held as exact fp32 (the same values, FFMA updates, int64 energies).
+int step_wtype(const da_ctx* c) { return c->dtype == DA_INT8 ? da::kWInt8AsF32 : (int)c->dtype; }
+const void* step_W(const da_ctx* c) { return c->dtype == DA_INT8 ? c->Wf : c->W; }
 
 // Default launch shape: one warp per replica up to N = 1024 (V <= 32
 // variables per lane).  Beyond, the fewest warps per replica that cover N
@@ -187,7 +193,7 @@ struct RunBuffers {
 StepParams base_params(const da_ctx* c, const RunBuffers& b)
 {
     StepParams p;
-    p.W = c->W;
+    p.W = step_W(c);
     p.diag = c->diag;
     p.N = c->N;
     p.ldw = c->ldw;
@@ -206,7 +212,7 @@ StepParams base_params(const da_ctx* c, const RunBuffers& b)
 // linear terms and E = 0 (all runs start from the same state, Sec. II).
 da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
-    DA_CU(da::launch_init_state(is_int(c), c->diag, c->N, b.R, b.h(), b.s.npad(), st));
+    DA_CU(da::launch_init_state(is_int(c), c->diag, c->N, b.R, b.h(), b.s.npad(), st, c->dtype == DA_INT8));
     DA_CU(cudaMemsetAsync(b.x(), 0, (size_t)2 * b.R * b.s.nwords() * 4, st));
     DA_CU(cudaMemsetAsync(b.sc(), 0, (size_t)b.R * sizeof(ReplicaScalars), st));
     return DA_OK;
@@ -271,7 +277,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
             if (da_status e = prof_pair(c, &e0, &e1)) return e;
             DA_CU(cudaEventRecord(e0, st));
         }
-        DA_CU(da::launch_step((int)c->dtype, b.s, p, trace_dev != nullptr, st));
+        DA_CU(da::launch_step(step_wtype(c), b.s, p, trace_dev != nullptr, st));
         if (e1) DA_CU(cudaEventRecord(e1, st));
         if (rec && p.t1 % recompute_every == 0) {
             DA_CU(da::launch_recompute_tc(false, c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), b.R, b.h(),
@@ -442,6 +448,17 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
+    if (dtype == DA_INT8) {   // the same couplings as exact fp32, same pitch and slack
+        std::vector<float> wf(Wh.size());
+        for (size_t k = 0; k < Wh.size(); ++k) wf[k] = (float)(int8_t)Wh[k];
+        e = cudaMalloc(&c->Wf, wf.size() * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(DA_ENOMEM, std::string("instance: ") + cudaGetErrorString(e));
+        }
+        e = cudaMemcpy(c->Wf, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
+    }
     e = da::tc_operand_build((int)dtype, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -484,6 +501,7 @@ void da_destroy(da_ctx* c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->W) cudaFree(c->W);
+    if (c->Wf) cudaFree(c->Wf);
     if (c->diag) cudaFree(c->diag);
     da::tc_operand_free(&c->tc);
     if (c->ws) cudaFree(c->ws);
@@ -680,7 +698,7 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     for (long long sw = 0; sw < sweeps; ++sw) {
         p.t0 = sw * c->N;
         p.t1 = p.t0 + c->N;
-        DA_CU(da::launch_step((int)c->dtype, s, p, false, st));
+        DA_CU(da::launch_step(step_wtype(c), s, p, false, st));
         DA_CU(da::launch_pt_exchange(is_int(c), betas_dev, K, L, b.sc(), temp_of, rep_at, swaps, strace, sw, sweeps,
                                      seed, st));
         if (adapt_every > 0 && (sw + 1) % adapt_every == 0 && sw + 1 <= adapt_sweeps)

@@ -168,17 +168,20 @@ __global__ void energy_kernel(const I128* __restrict__ part, int tiles, int R, i
     }
 }
 
-// g[r][i] = diag[i] for i < N, 0 on the padding.
-template <bool INT8>
+// g[r][i] = diag[i] for i < N, 0 on the padding (MODE 0: int32 diag and
+// fields, 1: fp32, 2: int32 diag into fp32 fields, exact below 2^24).
+template <int MODE>
 __global__ void init_state_kernel(const void* __restrict__ diag, int N, int R, void* g, int npad)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)R * npad) return;
     const int i = (int)(idx % npad);
-    if constexpr (INT8)
+    if constexpr (MODE == 0)
         static_cast<int32_t*>(g)[idx] = i < N ? static_cast<const int32_t*>(diag)[i] : 0;
-    else
+    else if constexpr (MODE == 1)
         static_cast<float*>(g)[idx] = i < N ? static_cast<const float*>(diag)[i] : 0.f;
+    else
+        static_cast<float*>(g)[idx] = i < N ? __int2float_rn(static_cast<const int32_t*>(diag)[i]) : 0.f;
 }
 
 __global__ void best_fixup_kernel(int R, ReplicaScalars* sc, bool int8, const uint32_t* x, uint32_t* bestx, int nw)
@@ -218,16 +221,19 @@ int fix_scale(float amax, int N)
     return 62 - L - e;
 }
 
-cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st)
+cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st,
+                              bool float_fields)
 {
     const long long n = (long long)R * npad;
     if (n == 0) return cudaSuccess;
     const int tb = 256;
     const unsigned blocks = (unsigned)((n + tb - 1) / tb);
-    if (is_int8)
-        init_state_kernel<true><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
+    if (is_int8 && float_fields)
+        init_state_kernel<2><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
+    else if (is_int8)
+        init_state_kernel<0><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
     else
-        init_state_kernel<false><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
+        init_state_kernel<1><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
     return cudaGetLastError();
 }
 

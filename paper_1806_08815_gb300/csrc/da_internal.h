@@ -11,8 +11,10 @@ struct da_ctx;
 
 namespace da {
 
-// Coupling types, with the values of da_dtype in include/da.h.
-constexpr int kWInt8 = 0, kWFp32 = 1, kWInt16 = 2;
+// Coupling types, with the values of da_dtype in include/da.h; kWInt8AsF32:
+// int8 couplings held as exact fp32 for the step kernel (int32-exact fields in
+// fp32, int64 energies), the form DA_INT8 contexts anneal with.
+constexpr int kWInt8 = 0, kWFp32 = 1, kWInt16 = 2, kWInt8AsF32 = 3;
 
 // Per-replica scalars kept in global memory between kernel launches.
 // E and best hold int64 energies (int8 instances) or fp64 bit patterns (fp32).
@@ -74,8 +76,10 @@ inline void set_seed(StepParams& p, uint64_t seed)
 }
 
 // Start state x = 0 of R replicas: fields g = diag (the effective field of
-// x = 0), words and scalars zero (da_fields.cu).
-cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st);
+// x = 0), words and scalars zero (da_fields.cu).  float_fields: an integer
+// diagonal written as fp32 fields (for kWInt8AsF32).
+cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st,
+                              bool float_fields = false);
 
 // The best-state test left pending by the last step of an anneal (made after
 // any recompute of that step): if E < best, best = E and the state words are

@@ -8,6 +8,7 @@ namespace da {
 cudaError_t launch_step_i8(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 cudaError_t launch_step_f32(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 cudaError_t launch_step_i16(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
+cudaError_t launch_step_i8f(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 
 bool step_shape_supported(const StepShape& s)
 {
@@ -30,6 +31,7 @@ cudaError_t launch_step(int wtype, const StepShape& s, const StepParams& p, bool
     case kWInt8: return launch_step_i8(s, p, trace, st);
     case kWFp32: return launch_step_f32(s, p, trace, st);
     case kWInt16: return launch_step_i16(s, p, trace, st);
+    case kWInt8AsF32: return launch_step_i8f(s, p, trace, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -57,6 +57,27 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ E book(E e, H dE) { return __dadd_rn(e, (double)dE); }
 };
 
+// Integer couplings of a DA_INT8 instance stored as fp32 (exact: |W| <= 128 and
+// every |Q_ii| + sum_j |Q_ij| < 2^24, so every field and Delta E is an exact
+// fp32 integer): the step runs on fp32 fields and FFMA updates, with exactly
+// the values of the int8/int32 form, and books the energy in int64.
+struct f32e {
+    float f;
+};
+template <> struct Arith<f32e> {
+    using H = float;
+    using E = long long;
+    static __device__ __forceinline__ H signed_field(H g, uint32_t x) { return Arith<float>::signed_field(g, x); }
+    static __device__ __forceinline__ float delta(H dE, float Eoff) { return __fsub_rn(dE, Eoff); }
+    static __device__ __forceinline__ float delta0(H dE) { return dE; }
+    using Sign = float;
+    static __device__ __forceinline__ Sign sign(uint32_t xold) { return xold ? -1.0f : 1.0f; }
+    static __device__ __forceinline__ H apply_signed(H h, f32e w, Sign s) { return __fmaf_rn(s, w.f, h); }
+    static __device__ __forceinline__ E load_e(long long b) { return b; }
+    static __device__ __forceinline__ long long store_e(E e) { return e; }
+    static __device__ __forceinline__ E book(E e, H dE) { return e + (E)__float2int_rn(dE); }
+};
+
 __device__ __forceinline__ int warp_inclusive_scan(int v, int lane)
 {
 #pragma unroll
@@ -124,6 +145,17 @@ template <int V, bool CG> struct Row<float, V, CG> {
         for (int q = 0; q < V / 4; ++q) {
             const float4 f = ldx<CG>(reinterpret_cast<const float4*>(p) + q);
             c[4 * q] = f.x; c[4 * q + 1] = f.y; c[4 * q + 2] = f.z; c[4 * q + 3] = f.w;
+        }
+    }
+};
+template <int V, bool CG> struct Row<f32e, V, CG> {
+    static __device__ __forceinline__ void load(const f32e* p, f32e (&c)[V])
+    {
+        static_assert(V % 4 == 0, "V");
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) {
+            const float4 f = ldx<CG>(reinterpret_cast<const float4*>(p) + q);
+            c[4 * q].f = f.x; c[4 * q + 1].f = f.y; c[4 * q + 2].f = f.z; c[4 * q + 3].f = f.w;
         }
     }
 };
