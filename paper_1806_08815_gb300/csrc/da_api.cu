@@ -390,9 +390,10 @@ bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::str
 StepShape default_shape(int N, int R) { return auto_shape(N, R); }
 
 void set_last_error(const std::string& msg) { g_err = msg; }
-void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S)
+void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S, const void** Wstep)
 {
     *W = c->W;
+    if (Wstep) *Wstep = step_W(c);
     *diag = c->diag;
     *ldw = c->ldw;
     *S = c->S;

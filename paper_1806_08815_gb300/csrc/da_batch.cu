@@ -10,6 +10,7 @@
 // whose block shape is chosen by a small autotuner that times short probes of
 // the real work and caches the winner per device and class.
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -78,8 +79,12 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
         R_ rp;
         rp.init(static_cast<const Tw*>(it.W), it.N, it.ldw, (uint32_t)r, it.xs + ((size_t)it.R + r) * nw);
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-            rp.h[v] = ((rp.valid >> v) & 1u) ? static_cast<const H*>(it.diag)[rp.base + v] : H(0);
+        for (int v = 0; v < V; ++v) {
+            if constexpr (std::is_same<Tw, step_detail::f32e>::value)   // int32 diagonal, exact in fp32
+                rp.h[v] = ((rp.valid >> v) & 1u) ? __int2float_rn(static_cast<const int32_t*>(it.diag)[rp.base + v]) : 0.f;
+            else
+                rp.h[v] = ((rp.valid >> v) & 1u) ? static_cast<const H*>(it.diag)[rp.base + v] : H(0);
+        }
         rp.xm = 0;
         rp.m = 0;
         rp.Ecur = 0;
@@ -94,7 +99,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
             if (t + 1 < T) beta_next = it.beta[t + 1];
             const int k = rp.template step<false>(t, t + 1 < T, beta, it.inc, keys);
             if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
-            if constexpr (sizeof(Tw) == 4) {
+            if constexpr (std::is_same<Tw, float>::value) {
                 if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
                     rp.recompute(static_cast<const float*>(it.diag), it.S);
                     if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
@@ -122,10 +127,10 @@ BatchKernel kernel_for(bool int8, int V)
 {
     if (int8) {
         switch (V) {
-        case 4: return batch_kernel<int8_t, 4>;
-        case 8: return batch_kernel<int8_t, 8>;
-        case 16: return batch_kernel<int8_t, 16>;
-        case 32: return batch_kernel<int8_t, 32>;
+        case 4: return batch_kernel<step_detail::f32e, 4>;
+        case 8: return batch_kernel<step_detail::f32e, 8>;
+        case 16: return batch_kernel<step_detail::f32e, 16>;
+        case 32: return batch_kernel<step_detail::f32e, 32>;
         }
     } else {
         switch (V) {
@@ -244,7 +249,8 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return bfail(DA_ECUDA, "no device");
     struct Host {
-        const void* W;
+        const void* W;       // couplings for the exact evaluation
+        const void* Wstep;   // couplings in the step kernel's form (int8 instances: exact fp32)
         const void* diag;
         int N, ldw, S;
         bool int8;
@@ -267,7 +273,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
             return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad offset or recompute period");
         Host h{};
         int32_t ldw = 0, S = 0;
-        da::ctx_device_view(it.ctx, &h.W, &h.diag, &ldw, &S);
+        da::ctx_device_view(it.ctx, &h.W, &h.diag, &ldw, &S, &h.Wstep);
         h.N = (int)N;
         h.ldw = ldw;
         h.S = S;
@@ -345,7 +351,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
             for (int i : c.item_idx) {
                 const da_batch_item& it = items[i];
                 BatchItemDev d{};
-                d.W = hi[i].W;
+                d.W = hi[i].Wstep;
                 d.diag = hi[i].diag;
                 d.beta = reinterpret_cast<const float*>(base + o_beta[i]);
                 d.xs = reinterpret_cast<uint32_t*>(base + o_xs[i]);

@@ -182,7 +182,10 @@ void set_last_error(const std::string& msg);
 
 // Device copies of a context's instance: W (row pitch ldw), diag, and the
 // fixed-point scale S of its fp32 recompute (da_api.cu).
-void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S);
+// Wstep (may be null): the couplings in the step kernel's form (DA_INT8: exact
+// fp32, kWInt8AsF32; otherwise W).
+void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S,
+                     const void** Wstep = nullptr);
 
 // Fixed-point scale of the fp32 recompute for amax = max(|W_ij|, |diag_i|)
 // and N variables (N + 1 terms per sum).
