@@ -112,7 +112,9 @@ const char* da_last_error(void);
 
 /* Create a context holding one QUBO instance on the current CUDA device.
  *   Q      host, N x N row-major (int32_t for DA_INT8 and DA_INT16, float for
- *          DA_FP32); the upper triangle is read and copied, the caller keeps Q.
+ *          DA_FP32); the upper triangle is checked on the host, then the
+ *          array goes to the device once (a transient N*N*4-byte copy) where
+ *          W and diag are built from it; the caller keeps Q.
  *   N      1 <= N <= 8192 (the next-generation DA size named in Sec. II).
  *   dtype  DA_INT8 requires every coupling in [-128, 127] and every
  *          |Q_ii| + sum_j |Q_ij| < 2^24 (so that every Delta E is exact in
@@ -264,8 +266,10 @@ typedef struct da_job {
  * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
 da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_server** out);
 
-/* Queue a request; returns at once.  The instance is validated and built on the
- * host here (as da_create).  Errors: DA_EINVAL; DA_EBUDGET if the request alone
+/* Queue a request; returns at once.  The instance is checked on the host here
+ * (as da_create); its device layout is built at admission from a transient
+ * device copy of Q (N*N*4 bytes, outside the budget, freed once built).
+ * Errors: DA_EINVAL; DA_EBUDGET if the request alone
  * exceeds the budget (it could never be admitted); DA_EBUSY while the server is
  * shutting down. */
 da_status da_submit(da_server* srv, const da_job* job, da_req** out);

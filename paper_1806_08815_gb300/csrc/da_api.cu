@@ -308,18 +308,14 @@ struct CtxLock {
 }  // namespace
 
 namespace da {
-// Integer couplings into W of element type T (int8 or int16): range of every
-// coupling, and |Q_ii| + sum_j |Q_ij| below row_limit.
-template <typename T>
-static bool integer_instance(const int32_t* q, int n, int ldw, int32_t lo, int32_t hi, long long row_limit,
-                             const char* name, HostInstance& out, std::string& why)
+// Integer couplings: range of every coupling (upper triangle) and
+// |Q_ii| + sum_j |Q_ij| below row_limit; the rows are read in order.
+static bool check_integer(const int32_t* q, int n, int32_t lo, int32_t hi, long long row_limit, const char* name,
+                          std::string& why)
 {
-    T* w = reinterpret_cast<T*>(out.W.data());
-    int32_t* d = reinterpret_cast<int32_t*>(out.diag.data());
     std::vector<long long> rowabs(n, 0);
     for (int i = 0; i < n; ++i) {
-        d[i] = q[(size_t)i * n + i];
-        rowabs[i] += std::llabs((long long)d[i]);
+        rowabs[i] += std::llabs((long long)q[(size_t)i * n + i]);
         for (int j = i + 1; j < n; ++j) {
             const int32_t v = q[(size_t)i * n + j];
             if (v < lo || v > hi) {
@@ -327,8 +323,6 @@ static bool integer_instance(const int32_t* q, int n, int ldw, int32_t lo, int32
                       std::to_string(v) + " outside [" + std::to_string(lo) + ", " + std::to_string(hi) + "]";
                 return false;
             }
-            w[(size_t)i * ldw + j] = (T)v;
-            w[(size_t)j * ldw + i] = (T)v;
             rowabs[i] += std::abs(v);
             rowabs[j] += std::abs(v);
         }
@@ -343,48 +337,36 @@ static bool integer_instance(const int32_t* q, int n, int ldw, int32_t lo, int32
 
 bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why)
 {
-    const int ldw = (int)align_up((size_t)n, 128);
-    const size_t esz = dtype == DA_INT8 ? 1 : dtype == DA_INT16 ? 2 : 4;
-    out.ldw = ldw;
+    out.ldw = (int)align_up((size_t)n, 128);
     out.S = 0;
-    // 8192 zero entries after the last row: a lane whose slice straddles N
-    // reads up to the launch width (at most 8192) past the row start
-    out.W.assign(((size_t)n * ldw + 8192) * esz, 0);
-    out.diag.assign((size_t)n * 4, 0);
-    float amax = 0.f;
+    out.dtype = dtype;
     if (dtype == DA_INT8) {
-        if (!integer_instance<int8_t>(static_cast<const int32_t*>(Q), n, ldw, -128, 127, 1ll << 24, "DA_INT8", out,
-                                      why))
-            return false;
+        if (!check_integer(static_cast<const int32_t*>(Q), n, -128, 127, 1ll << 24, "DA_INT8", why)) return false;
     } else if (dtype == DA_INT16) {
-        if (!integer_instance<int16_t>(static_cast<const int32_t*>(Q), n, ldw, -32767, 32767, 1ll << 31, "DA_INT16",
-                                       out, why))
-            return false;
+        if (!check_integer(static_cast<const int32_t*>(Q), n, -32767, 32767, 1ll << 31, "DA_INT16", why)) return false;
     } else {
         const float* q = static_cast<const float*>(Q);
-        float* w = reinterpret_cast<float*>(out.W.data());
-        float* d = reinterpret_cast<float*>(out.diag.data());
-        for (int i = 0; i < n; ++i) {
-            d[i] = q[(size_t)i * n + i];
-            if (!std::isfinite(d[i])) {
-                why = "non-finite Q entry";
-                return false;
-            }
-            amax = std::max(amax, std::fabs(d[i]));
-            for (int j = i + 1; j < n; ++j) {
+        float amax = 0.f;
+        for (int i = 0; i < n; ++i)
+            for (int j = i; j < n; ++j) {
                 const float v = q[(size_t)i * n + j];
                 if (!std::isfinite(v)) {
                     why = "non-finite Q entry";
                     return false;
                 }
-                w[(size_t)i * ldw + j] = v;
-                w[(size_t)j * ldw + i] = v;
                 amax = std::max(amax, std::fabs(v));
             }
-        }
         out.S = fix_scale(amax, n);
     }
     return true;
+}
+
+size_t instance_W_bytes(int n, int dtype)
+{
+    const size_t esz = dtype == DA_INT8 ? 1 : dtype == DA_INT16 ? 2 : 4;
+    // 8192 zero entries after the last row: a lane whose slice straddles N
+    // reads up to the launch width (at most 8192) past the row start
+    return ((size_t)n * align_up((size_t)n, 128) + 8192) * esz;
 }
 
 StepShape default_shape(int N, int R) { return auto_shape(N, R); }
@@ -421,8 +403,6 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     std::string why;
     if (!da::build_instance(Q, n, (int)dtype, hin, why)) return fail(DA_EINVAL, why);
     const int ldw = hin.ldw;
-    std::vector<char>& Wh = hin.W;
-    std::vector<char>& dh = hin.diag;
     int dev = 0;
     DA_CU(cudaGetDevice(&dev));
     da_ctx* c = new (std::nothrow) da_ctx;
@@ -440,26 +420,25 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("stream/event: ") + cudaGetErrorString(e));
-    e = cudaMalloc(&c->W, Wh.size());
-    if (e == cudaSuccess) e = cudaMalloc(&c->diag, dh.size());
+    // DA_INT8 also keeps its couplings as exact fp32, same pitch and slack
+    const size_t qbytes = (size_t)n * n * 4;
+    void* qd = nullptr;
+    e = cudaMalloc(&c->W, da::instance_W_bytes(n, (int)dtype));
+    if (e == cudaSuccess) e = cudaMalloc(&c->diag, (size_t)n * 4);
+    if (e == cudaSuccess && dtype == DA_INT8) e = cudaMalloc(&c->Wf, da::instance_W_bytes(n, DA_FP32));
+    if (e == cudaSuccess) e = cudaMalloc(&qd, qbytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (qd) cudaFree(qd);
         return bail(DA_ENOMEM, std::string("instance: ") + cudaGetErrorString(e));
     }
-    e = cudaMemcpy(c->W, Wh.data(), Wh.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c->diag, dh.data(), dh.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(qd, Q, qbytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = da::launch_expand_instance(qd, n, ldw, (int)dtype, c->W, static_cast<float*>(c->Wf), c->diag, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const cudaError_t ef = cudaFree(qd);
+    if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
-    if (dtype == DA_INT8) {   // the same couplings as exact fp32, same pitch and slack
-        std::vector<float> wf(Wh.size());
-        for (size_t k = 0; k < Wh.size(); ++k) wf[k] = (float)(int8_t)Wh[k];
-        e = cudaMalloc(&c->Wf, wf.size() * sizeof(float));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return bail(DA_ENOMEM, std::string("instance: ") + cudaGetErrorString(e));
-        }
-        e = cudaMemcpy(c->Wf, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
-    }
     e = da::tc_operand_build((int)dtype, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "da.h"
 #include "da_fixed.cuh"
 #include "da_internal.h"
 
@@ -219,6 +220,57 @@ int fix_scale(float amax, int N)
     int L = 0;
     while ((1ll << L) < (long long)N + 1) ++L;
     return 62 - L - e;
+}
+
+// The instance in device layout from Q (n x n, row-major; only the upper
+// triangle is read): 32 x 32 tiles of W, each filled from the Q tile that
+// holds its entries (its mirror image below the diagonal), staged in shared
+// memory so that the reads and writes of a warp stay on one row.
+template <typename Tq, typename Tw>
+__global__ void __launch_bounds__(256) expand_kernel(const Tq* __restrict__ Q, int n, int ldw, Tw* __restrict__ W,
+                                                     float* __restrict__ Wf, Tq* __restrict__ diag)
+{
+    __shared__ Tq tile[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    const int a = min(bi, bj), b = max(bi, bj);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        const int row = a * 32 + r, col = b * 32 + tx;
+        tile[r][tx] = (row < n && col < n) ? Q[(size_t)row * n + col] : Tq(0);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = bi * 32 + r, j = bj * 32 + tx;
+        if (i >= n || j >= n) continue;
+        // i < j: Q[i][j] (bi <= bj, the tile as read); i > j: Q[j][i] (the mirror)
+        const Tq v = i < j ? tile[r][tx] : i > j ? tile[tx][r] : Tq(0);
+        W[(size_t)i * ldw + j] = (Tw)v;
+        if (Wf) Wf[(size_t)i * ldw + j] = (float)v;
+        if (i == j) diag[i] = tile[r][tx];
+    }
+}
+
+cudaError_t launch_expand_instance(const void* Q, int n, int ldw, int dtype, void* W, float* Wf, void* diag,
+                                   cudaStream_t st)
+{
+    const size_t entries = (size_t)n * ldw + 8192;
+    const size_t esz = dtype == DA_INT8 ? 1 : dtype == DA_INT16 ? 2 : 4;
+    cudaError_t e = cudaMemsetAsync(W, 0, entries * esz, st);
+    if (e == cudaSuccess && Wf) e = cudaMemsetAsync(Wf, 0, entries * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    if (dtype == DA_INT8)
+        expand_kernel<int32_t, int8_t><<<grid, block, 0, st>>>(static_cast<const int32_t*>(Q), n, ldw,
+                                                               static_cast<int8_t*>(W), Wf,
+                                                               static_cast<int32_t*>(diag));
+    else if (dtype == DA_INT16)
+        expand_kernel<int32_t, int16_t><<<grid, block, 0, st>>>(static_cast<const int32_t*>(Q), n, ldw,
+                                                                static_cast<int16_t*>(W), Wf,
+                                                                static_cast<int32_t*>(diag));
+    else
+        expand_kernel<float, float><<<grid, block, 0, st>>>(static_cast<const float*>(Q), n, ldw,
+                                                            static_cast<float*>(W), Wf, static_cast<float*>(diag));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void* g, int npad, cudaStream_t st,

@@ -155,14 +155,21 @@ cudaError_t plain_anneal(const void* W, const void* diag, bool int8, int N, int 
                          long long* eex, long long* part, double* tracked_E, int64_t* flips, cudaStream_t st);
 size_t plain_workspace_bytes(int N, int R);
 
-// An instance in the library's device layout, built on the host from the
-// upper triangle of Q (da_api.cu): W symmetric with zero diagonal (element
-// type of the da_dtype `dtype`), row pitch ldw, 8192 zero entries of slack;
-// diag; fixed-point scale S (fp32).
+// An instance in the library's device layout: W symmetric with zero
+// diagonal (element type of the da_dtype `dtype`), row pitch ldw, 8192 zero
+// entries of slack (instance_W_bytes); diag (n x 4 bytes, int32 or fp32);
+// fixed-point scale S (fp32).  build_instance (da_api.cu) checks the upper
+// triangle of Q on the host and sets ldw and S; launch_expand_instance
+// (da_fields.cu) writes W, the optional fp32 copy Wf of integer couplings and
+// diag from a device copy of Q (int32 entries for the integer dtypes, fp32
+// otherwise).
 struct HostInstance {
-    std::vector<char> W, diag;
-    int ldw = 0, S = 0;
+    std::vector<char> Q;   // a host copy of Q where the caller keeps one
+    int ldw = 0, S = 0, dtype = 0;
 };
+size_t instance_W_bytes(int n, int dtype);
+cudaError_t launch_expand_instance(const void* Q, int n, int ldw, int dtype, void* W, float* Wf, void* diag,
+                                   cudaStream_t st);
 bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why);
 
 // The default launch shape of the step kernel for N variables and R replicas.

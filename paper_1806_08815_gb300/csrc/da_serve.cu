@@ -130,7 +130,7 @@ struct Req {
     bool int8 = false;
     bool big = false;                 // N > 1024: chunked path on its own stream
     da::StepShape shape;              // big path launch shape; small path: V in shape.V
-    da::HostInstance inst;            // built at submit, released after upload
+    da::HostInstance inst;            // checked at submit (ldw, S); W and diag built on the device at admission
     size_t bytes = 0;                 // device bytes charged to the budget
     int slot = -1;
     ReqState state = ReqState::Queued;
@@ -206,7 +206,7 @@ void plan_request(Req& q)
     const size_t esz = q.int8 ? 1 : 4;
     size_t o = 0;
     auto take = [&](size_t b) { size_t at = o; o += al256(b); return at; };
-    q.o_W = take(q.inst.W.size());
+    q.o_W = take(da::instance_W_bytes(q.N, q.int8 ? DA_INT8 : DA_FP32));
     q.o_diag = take((size_t)q.N * 4);
     q.o_beta = take((size_t)q.job.steps * 4);
     if (!q.big) {
@@ -250,13 +250,23 @@ bool admit(da_server* s, Req& q)
         return false;
     }
     const int R = q.job.replicas;
-    if (!cu_ok(cudaMemcpyAsync(q.dmem + q.o_W, q.inst.W.data(), q.inst.W.size(), cudaMemcpyHostToDevice, s->s_copy), q,
-               "upload W"))
-        return false;
-    if (!cu_ok(cudaMemcpyAsync(q.dmem + q.o_diag, q.inst.diag.data(), q.inst.diag.size(), cudaMemcpyHostToDevice,
-                               s->s_copy),
-               q, "upload diag"))
-        return false;
+    // W and diag from a transient device copy of Q (the caller keeps Q valid)
+    {
+        void* qd = nullptr;
+        const size_t qbytes = (size_t)q.N * q.N * 4;
+        if (cudaMallocAsync(&qd, qbytes, s->s_copy) != cudaSuccess) {
+            cudaGetLastError();
+            q.err = DA_ENOMEM;
+            q.msg = "device allocation of " + std::to_string(qbytes) + " bytes (copy of Q)";
+            return false;
+        }
+        bool ok = cu_ok(cudaMemcpyAsync(qd, q.job.Q, qbytes, cudaMemcpyHostToDevice, s->s_copy), q, "upload Q");
+        ok = ok && cu_ok(da::launch_expand_instance(qd, q.N, q.inst.ldw, q.int8 ? DA_INT8 : DA_FP32, q.dmem + q.o_W,
+                                                    nullptr, q.dmem + q.o_diag, s->s_copy),
+                         q, "build instance");
+        cudaFreeAsync(qd, s->s_copy);
+        if (!ok) return false;
+    }
     if (q.job.steps > 0 &&
         !cu_ok(cudaMemcpyAsync(q.dmem + q.o_beta, q.job.beta, (size_t)q.job.steps * 4, cudaMemcpyHostToDevice, s->s_copy),
                q, "upload beta"))
@@ -346,8 +356,6 @@ bool admit(da_server* s, Req& q)
         if (!cu_ok(cudaGetLastError(), q, "finalize")) return false;
         if (!cu_ok(cudaEventRecord(q.done_ev, st), q, "event")) return false;
     }
-    q.inst.W.clear();
-    q.inst.W.shrink_to_fit();
     q.t_start = Clock::now();
     return true;
 }

@@ -165,3 +165,32 @@ def test_int16(da, N, R):
     d = np.diag(Q).astype(np.int64)
     for r in sorted({0, 1, R - 1} | set(rng.choice(R, 6, replace=False))):
         assert np.array_equal(h[r].astype(np.int64), oracle.fields_int(Q, xp[r]) + d), r
+
+
+@pytest.mark.parametrize("dtype_name,N", [("DA_INT8", 33), ("DA_INT16", 1000), ("DA_FP32", 4097)])
+def test_instance_reads_upper_triangle_only(da, dtype_name, N):
+    """The device-side instance build mirrors the upper triangle: values below
+    the diagonal change nothing, and the fields match the oracle's."""
+    import oracle
+    rng = np.random.default_rng(N + 7)
+    dtype = getattr(da, dtype_name)
+    if dtype_name == "DA_FP32":
+        Q = np.triu(rng.standard_normal((N, N))).astype(np.float32)
+        junk = rng.standard_normal((N, N)).astype(np.float32) * 1e30
+    else:
+        hi = 127 if dtype_name == "DA_INT8" else 32767
+        Q = np.triu(rng.integers(-hi, hi + 1, (N, N)), 1).astype(np.int32)
+        np.fill_diagonal(Q, rng.integers(-1000, 1000, N))
+        junk = rng.integers(-2 ** 31, 2 ** 31, (N, N)).astype(np.int32)
+    Qj = Q + np.tril(junk, -1)
+    xp = oracle.pack(_states(rng, 9, N))
+    a = da.da_field_recompute(da.da_create(Q, dtype), xp)
+    b = da.da_field_recompute(da.da_create(Qj, dtype), xp)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    for r in (0, 1, 5):
+        if dtype_name == "DA_FP32":
+            hr, _, _ = oracle.recompute_f32(Q, xp[r])
+            assert np.array_equal(a[r].view(np.uint32), hr.view(np.uint32)), r
+        else:
+            ref = oracle.fields_int(Q, xp[r]) + np.diag(Q).astype(np.int64)
+            assert np.array_equal(a[r].astype(np.int64), ref), r
