@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128) serve_kernel(const __grid_constant__ Serv
                     continue;
                 }
                 if (++idle > sp.idle_polls) break;
-                __nanosleep(1000);
+                __nanosleep(2000);
             }
         }
         u = __shfl_sync(0xffffffffu, u, 0);
@@ -118,7 +118,9 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr unsigned long long kRingCap = 1ull << 20;
-constexpr int kIdlePolls = 20000;        // ~30-60 ms of empty polling before a warp leaves
+constexpr int kIdlePolls = 1 << 21;      // seconds of empty polling before a warp leaves on its own
+// the host stops the kernel after this long without a request of its path in flight
+constexpr auto kIdleStop = std::chrono::milliseconds(20);
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -184,8 +186,15 @@ struct da_server {
     unsigned long long units_done = 0;     // units of completed requests
     unsigned long long head_seen = 0;      // head read after the kernel last ended
     cudaStream_t s_kernel = nullptr, s_copy = nullptr;
+    // requests' device memory: a pool of the server's own that keeps what it
+    // has reserved (a pool that trims at every synchronisation unmaps memory,
+    // which waits for the running kernels: admission would stall behind the
+    // persistent kernel and behind every running anneal)
+    cudaMemPool_t pool = nullptr;
     cudaEvent_t k_done = nullptr;
     bool k_running = false;
+    bool k_stopping = false;               // stop raised because the kernel's path went idle
+    std::chrono::steady_clock::time_point last_busy{};
     int kernel_blocks = 0;
     // statistics
     long long kernel_launches = 0, completed = 0;
@@ -242,7 +251,7 @@ bool cu_ok(cudaError_t e, Req& q, const char* what)
 // Upload an admitted request and start its work.  Runs on the worker thread.
 bool admit(da_server* s, Req& q)
 {
-    if (cudaMallocAsync(reinterpret_cast<void**>(&q.dmem), q.bytes, s->s_copy) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&q.dmem), q.bytes, s->pool, s->s_copy) != cudaSuccess) {
         cudaGetLastError();
         q.dmem = nullptr;
         q.err = DA_ENOMEM;
@@ -254,7 +263,7 @@ bool admit(da_server* s, Req& q)
     {
         void* qd = nullptr;
         const size_t qbytes = (size_t)q.N * q.N * 4;
-        if (cudaMallocAsync(&qd, qbytes, s->s_copy) != cudaSuccess) {
+        if (cudaMallocFromPoolAsync(&qd, qbytes, s->pool, s->s_copy) != cudaSuccess) {
             cudaGetLastError();
             q.err = DA_ENOMEM;
             q.msg = "device allocation of " + std::to_string(qbytes) + " bytes (copy of Q)";
@@ -441,8 +450,19 @@ void worker_loop(da_server* s)
             s->k_running = false;
             cudaMemcpyAsync(&s->head_seen, s->head, 8, cudaMemcpyDeviceToHost, s->s_copy);
             cudaStreamSynchronize(s->s_copy);
+            if (s->k_stopping) {
+                __atomic_store_n(s->stop_h, 0, __ATOMIC_RELEASE);
+                s->k_stopping = false;
+            }
         } else {
             cudaGetLastError();   // cudaErrorNotReady
+        }
+        // units pushed whose request has not completed: the kernel has work
+        const auto now = Clock::now();
+        if (s->tail > s->units_done) s->last_busy = now;
+        if (s->k_running && !s->k_stopping && s->tail == s->units_done && now - s->last_busy > kIdleStop) {
+            __atomic_store_n(s->stop_h, 1, __ATOMIC_RELEASE);
+            s->k_stopping = true;
         }
         if (!s->k_running && s->tail > s->head_seen) launch_kernel(s);
         // completions
@@ -500,6 +520,16 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
                      std::string(what) + ": " + cudaGetErrorString(e));
     };
     cudaError_t e;
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->dev;
+        if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return bad(e, "memory pool");
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+            return bad(e, "memory pool");
+    }
     if ((e = cudaMalloc(&s->descs, sizeof(da::ServeDesc) * max_requests)) != cudaSuccess) return bad(e, "descriptors");
     if ((e = cudaMalloc(&s->done, sizeof(unsigned int) * max_requests)) != cudaSuccess) return bad(e, "counters");
     if ((e = cudaMalloc(&s->head, 8)) != cudaSuccess) return bad(e, "head");
@@ -520,6 +550,16 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
     if ((e = cudaStreamCreateWithFlags(&s->s_kernel, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "stream");
     if ((e = cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "stream");
     if ((e = cudaEventCreateWithFlags(&s->k_done, cudaEventDisableTiming)) != cudaSuccess) return bad(e, "event");
+    // An SM runs blocks of several kernels at once only under one split of its
+    // on-chip memory between L1 and shared memory.  The persistent kernel
+    // needs no shared memory, and left to itself would put its SMs in a split
+    // where every other kernel of the server (instance build, the anneals of
+    // large requests) waits until it ends; it takes the split with the most
+    // shared memory instead.
+    if ((e = cudaFuncSetAttribute(reinterpret_cast<const void*>(da::serve_kernel),
+                                  cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared)) !=
+        cudaSuccess)
+        return bad(e, "carveout");
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(da::serve_kernel), 128, 0) !=
             cudaSuccess ||
@@ -646,6 +686,7 @@ void da_server_destroy(da_server* s)
     cudaFreeHost(s->tail_h);
     cudaFreeHost(s->flags_h);
     cudaFreeHost(s->stop_h);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
 }
 

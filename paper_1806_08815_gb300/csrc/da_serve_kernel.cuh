@@ -8,10 +8,11 @@
 // itself.  The last unit of a request raises the request's completion flag in
 // host-mapped memory.
 //
-// Every wait is bounded: a warp that finds no unit polls the ring with a short
-// sleep for at most `idle_polls` rounds and then leaves the kernel; the host
-// relaunches the kernel when new units arrive.  A stop flag ends the kernel at
-// the next poll.
+// Every wait is bounded.  The host ends the kernel through the stop flag once
+// no request of this path has been in flight for a while, and relaunches it
+// when new units arrive; so the warps of one launch leave together and a
+// launch never drains to a few warps while units wait.  A warp that finds no
+// unit for `idle_polls` rounds (seconds) leaves on its own all the same.
 #pragma once
 #include <cuda/atomic>
 
