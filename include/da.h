@@ -235,14 +235,14 @@ typedef struct da_batch_item {
 da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s);
 
 /* ---- Request loop (continuous batching) ------------------------------------
- * A server keeps a persistent kernel whose warps pull work units (one replica of
- * one request) from a queue that keeps growing while the kernel runs: requests
- * that arrive while others are on the GPU are admitted as soon as device memory
- * (within the server's budget) and a request slot are free, and their replicas
- * run beside those already in flight.  Requests with N > 1024 run as chunked
- * multi-warp launches on their own streams, concurrently with the kernel.  A
- * request's results are identical to da_anneal on the same instance, schedule
- * and seed (recompute_every applies to DA_FP32, as in da_anneal). */
+ * A server runs each admitted request on a CUDA stream of its own: requests that
+ * arrive while others are on the GPU are admitted as soon as device memory
+ * (within the server's budget) and a request slot are free, and their kernels
+ * start at once beside those already in flight.  Admission queues all of a
+ * request's work (upload, instance build, the anneal in chunks, the exact final
+ * evaluation) without waiting for the GPU.  A request's results are identical
+ * to da_anneal on the same instance, schedule and seed (recompute_every applies
+ * to DA_FP32, as in da_anneal). */
 typedef struct da_server da_server;
 typedef struct da_req da_req;
 
@@ -283,7 +283,7 @@ da_status da_poll(da_req* req, int32_t timeout_us, da_result* out);
 /* Release a request handle (after its last poll). */
 void da_req_free(da_req* req);
 
-/* Requests completed, persistent-kernel launches so far, device bytes in use. */
+/* Requests completed, kernels queued so far (all requests), device bytes in use. */
 da_status da_server_stats(da_server* srv, int64_t* completed, int64_t* kernel_launches, int64_t* bytes_in_use);
 
 /* Wait for every submitted request to finish, stop the kernel, free everything. */

@@ -208,6 +208,7 @@ cudaError_t launch_best_fixup(int R, ReplicaScalars* sc, bool is_int8, const uin
                               cudaStream_t st)
 {
     if (R <= 0) return cudaSuccess;
+    prefer_shared<best_fixup_kernel>();
     best_fixup_kernel<<<R, 64, 0, st>>>(R, sc, is_int8, x, bestx, nw);
     return cudaGetLastError();
 }
@@ -244,10 +245,44 @@ __global__ void __launch_bounds__(256) expand_kernel(const Tq* __restrict__ Q, i
         if (i >= n || j >= n) continue;
         // i < j: Q[i][j] (bi <= bj, the tile as read); i > j: Q[j][i] (the mirror)
         const Tq v = i < j ? tile[r][tx] : i > j ? tile[tx][r] : Tq(0);
-        W[(size_t)i * ldw + j] = (Tw)v;
+        if (W) W[(size_t)i * ldw + j] = (Tw)v;
         if (Wf) Wf[(size_t)i * ldw + j] = (float)v;
         if (i == j) diag[i] = tile[r][tx];
     }
+}
+
+__global__ void zero_kernel(uint4* __restrict__ p, size_t n16)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n16; k += (size_t)gridDim.x * blockDim.x)
+        p[k] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) return cudaErrorInvalidValue;
+    const size_t n16 = bytes / 16;
+    const unsigned blocks = (unsigned)std::min<size_t>((n16 + 255) / 256, 4096);
+    prefer_shared<zero_kernel>();
+    zero_kernel<<<blocks, 256, 0, st>>>(static_cast<uint4*>(p), n16);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_field_kernels()
+{
+    prefer_shared<zero_kernel>();
+    prefer_shared<expand_kernel<int32_t, int8_t>>();
+    prefer_shared<expand_kernel<int32_t, int16_t>>();
+    prefer_shared<expand_kernel<float, float>>();
+    prefer_shared<init_state_kernel<0>>();
+    prefer_shared<init_state_kernel<1>>();
+    prefer_shared<init_state_kernel<2>>();
+    prefer_shared<best_fixup_kernel>();
+    prefer_shared<recompute_kernel<true>>();
+    prefer_shared<recompute_kernel<false>>();
+    prefer_shared<energy_kernel<true>>();
+    prefer_shared<energy_kernel<false>>();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_expand_instance(const void* Q, int n, int ldw, int dtype, void* W, float* Wf, void* diag,
@@ -255,10 +290,13 @@ cudaError_t launch_expand_instance(const void* Q, int n, int ldw, int dtype, voi
 {
     const size_t entries = (size_t)n * ldw + 8192;
     const size_t esz = dtype == DA_INT8 ? 1 : dtype == DA_INT16 ? 2 : 4;
-    cudaError_t e = cudaMemsetAsync(W, 0, entries * esz, st);
-    if (e == cudaSuccess && Wf) e = cudaMemsetAsync(Wf, 0, entries * sizeof(float), st);
+    cudaError_t e = W ? launch_zero(W, entries * esz, st) : cudaSuccess;
+    if (e == cudaSuccess && Wf) e = launch_zero(Wf, entries * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    prefer_shared<expand_kernel<int32_t, int8_t>>();
+    prefer_shared<expand_kernel<int32_t, int16_t>>();
+    prefer_shared<expand_kernel<float, float>>();
     if (dtype == DA_INT8)
         expand_kernel<int32_t, int8_t><<<grid, block, 0, st>>>(static_cast<const int32_t*>(Q), n, ldw,
                                                                static_cast<int8_t*>(W), Wf,
@@ -280,6 +318,9 @@ cudaError_t launch_init_state(bool is_int8, const void* diag, int N, int R, void
     if (n == 0) return cudaSuccess;
     const int tb = 256;
     const unsigned blocks = (unsigned)((n + tb - 1) / tb);
+    prefer_shared<init_state_kernel<0>>();
+    prefer_shared<init_state_kernel<1>>();
+    prefer_shared<init_state_kernel<2>>();
     if (is_int8 && float_fields)
         init_state_kernel<2><<<blocks, tb, 0, st>>>(diag, N, R, g, npad);
     else if (is_int8)
@@ -295,10 +336,13 @@ cudaError_t launch_energy_sum(bool is_int8, const long long* part, int tiles, in
     if (R <= 0) return cudaSuccess;
     const int tb = 128;
     const I128* pp = reinterpret_cast<const I128*>(part);
-    if (is_int8)
+    if (is_int8) {
+        prefer_shared<energy_kernel<true>>();
         energy_kernel<true><<<(R + tb - 1) / tb, tb, 0, st>>>(pp, tiles, R, S, E, Estride);
-    else
+    } else {
+        prefer_shared<energy_kernel<false>>();
         energy_kernel<false><<<(R + tb - 1) / tb, tb, 0, st>>>(pp, tiles, R, S, E, Estride);
+    }
     return cudaGetLastError();
 }
 
@@ -311,10 +355,13 @@ cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int 
     const int tiles = (rows + kRows - 1) / kRows;
     dim3 grid(tiles, (R + kStates - 1) / kStates);
     I128* part = E ? reinterpret_cast<I128*>(scratch) : nullptr;
-    if (is_int8)
+    if (is_int8) {
+        prefer_shared<recompute_kernel<true>>();
         recompute_kernel<true><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
-    else
+    } else {
+        prefer_shared<recompute_kernel<false>>();
         recompute_kernel<false><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !E) return err;
     return launch_energy_sum(is_int8, scratch, tiles, R, S, E, Estride, st);

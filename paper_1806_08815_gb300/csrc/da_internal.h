@@ -160,14 +160,40 @@ size_t plain_workspace_bytes(int N, int R);
 // entries of slack (instance_W_bytes); diag (n x 4 bytes, int32 or fp32);
 // fixed-point scale S (fp32).  build_instance (da_api.cu) checks the upper
 // triangle of Q on the host and sets ldw and S; launch_expand_instance
-// (da_fields.cu) writes W, the optional fp32 copy Wf of integer couplings and
-// diag from a device copy of Q (int32 entries for the integer dtypes, fp32
+// (da_fields.cu) writes W (unless null), the optional fp32 copy Wf of integer
+// couplings and diag from a device copy of Q (int32 entries for the integer dtypes, fp32
 // otherwise).
 struct HostInstance {
     std::vector<char> Q;   // a host copy of Q where the caller keeps one
     int ldw = 0, S = 0, dtype = 0;
 };
 size_t instance_W_bytes(int n, int dtype);
+// Zeroes `bytes` bytes at p (device, 16-byte aligned) with a kernel of this
+// library, so that zeroing takes the same on-chip memory split as the rest.
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
+// Sets the on-chip memory split (prefer_shared) of every step-kernel instance
+// of coupling type wtype (da_step.cu), and of the instance build, state and
+// recompute kernels (da_fields.cu), which also loads them: a kernel loaded on
+// first use while other kernels run may wait for them.
+cudaError_t prepare_step(int wtype);
+cudaError_t prepare_field_kernels();
+
+// An SM runs blocks of several kernels at once only under one split of its
+// on-chip memory between L1 and shared memory.  Kernels that run beside the
+// kernels of other requests ask for the split with the most shared memory, so
+// that none of them holds its SMs in a split the others cannot use.  Called
+// before a launch; the attribute is set once per kernel.
+template <auto K>
+inline void prefer_shared()
+{
+    static const bool once = [] {
+        if (cudaFuncSetAttribute(reinterpret_cast<const void*>(K), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            cudaGetLastError();
+        return true;
+    }();
+    (void)once;
+}
 cudaError_t launch_expand_instance(const void* Q, int n, int ldw, int dtype, void* W, float* Wf, void* diag,
                                    cudaStream_t st);
 bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::string& why);

@@ -36,4 +36,25 @@ cudaError_t launch_step(int wtype, const StepShape& s, const StepParams& p, bool
     }
 }
 
+cudaError_t prepare_step(int wtype)
+{
+    StepParams p;
+    p.R = 0;   // no blocks: the launch only sets the kernel's attributes
+    for (int G = 1; G <= 8; G *= 2)
+        for (int V = 4; V <= 32; V *= 2)
+            for (int rpb = 1; rpb <= 4; rpb *= 2) {
+                StepShape s;
+                s.V = V;
+                s.G = G;
+                s.rpb = rpb;
+                if (!step_shape_supported(s)) continue;
+                for (int full = 0; full < 2; ++full) {
+                    p.N = 32 * V * G - (full ? 0 : 1);
+                    const cudaError_t e = launch_step(wtype, s, p, false, nullptr);
+                    if (e != cudaSuccess) return e;
+                }
+            }
+    return cudaSuccess;
+}
+
 }  // namespace da

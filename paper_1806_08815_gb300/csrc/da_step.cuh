@@ -419,16 +419,25 @@ __global__ void __launch_bounds__(64, 7) step_kernel_ws(const __grid_constant__ 
     }
 }
 
+// One launch of kernel K with the on-chip memory split of prefer_shared; with
+// no blocks (p.R = 0) only the attribute is set, which also loads the kernel.
+template <auto K>
+inline void launch_shared(int blocks, int threads, size_t shm, cudaStream_t st, const StepParams& p)
+{
+    prefer_shared<K>();
+    if (blocks > 0) K<<<blocks, threads, shm, st>>>(p);
+}
+
 template <typename Tw, int V, int G>
 cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaStream_t st)
 {
     const int threads = 32 * G * s.rpb;
     const int blocks = (p.R + s.rpb - 1) / s.rpb;
     const size_t shm = G > 1 ? (size_t)s.rpb * (4 * 32 * G + 4) * sizeof(uint32_t) : 0;
-    if (blocks == 0) return cudaSuccess;
     const bool full = p.N == 32 * V * G;
     if constexpr (G == 1) {
         if (s.ws) {
+            if (blocks == 0) return cudaSuccess;
             if (full) {
                 if (trace) step_kernel_ws<Tw, V, true, true><<<p.R, 64, 0, st>>>(p);
                 else step_kernel_ws<Tw, V, true, false><<<p.R, 64, 0, st>>>(p);
@@ -439,20 +448,20 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
             return cudaGetLastError();
         }
         if (full) {
-            if (trace) step_kernel_g1<Tw, V, true, true><<<blocks, threads, 0, st>>>(p);
-            else step_kernel_g1<Tw, V, true, false><<<blocks, threads, 0, st>>>(p);
+            if (trace) launch_shared<step_kernel_g1<Tw, V, true, true>>(blocks, threads, 0, st, p);
+            else launch_shared<step_kernel_g1<Tw, V, true, false>>(blocks, threads, 0, st, p);
         } else {
-            if (trace) step_kernel_g1<Tw, V, false, true><<<blocks, threads, 0, st>>>(p);
-            else step_kernel_g1<Tw, V, false, false><<<blocks, threads, 0, st>>>(p);
+            if (trace) launch_shared<step_kernel_g1<Tw, V, false, true>>(blocks, threads, 0, st, p);
+            else launch_shared<step_kernel_g1<Tw, V, false, false>>(blocks, threads, 0, st, p);
         }
         return cudaGetLastError();
     }
     if (full) {
-        if (trace) step_kernel<Tw, V, G, true, true><<<blocks, threads, shm, st>>>(p);
-        else step_kernel<Tw, V, G, true, false><<<blocks, threads, shm, st>>>(p);
+        if (trace) launch_shared<step_kernel<Tw, V, G, true, true>>(blocks, threads, shm, st, p);
+        else launch_shared<step_kernel<Tw, V, G, true, false>>(blocks, threads, shm, st, p);
     } else {
-        if (trace) step_kernel<Tw, V, G, false, true><<<blocks, threads, shm, st>>>(p);
-        else step_kernel<Tw, V, G, false, false><<<blocks, threads, shm, st>>>(p);
+        if (trace) launch_shared<step_kernel<Tw, V, G, false, true>>(blocks, threads, shm, st, p);
+        else launch_shared<step_kernel<Tw, V, G, false, false>>(blocks, threads, shm, st, p);
     }
     return cudaGetLastError();
 }

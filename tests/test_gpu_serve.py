@@ -1,10 +1,10 @@
 """The request loop (da_server_create / da_submit / da_poll): every request's
 result is the same alone and in the mix, whatever else is on the GPU.
 
-Requests of mixed sizes and coupling types are submitted together (small ones
-become units of the persistent kernel, large ones chunked launches on their own
-streams); each must equal da_anneal on the same instance, schedule and seed,
-bit for bit.  A budget that admits one request at a time must give the same
+Requests of mixed sizes and coupling types are submitted together (each runs
+as chunked launches on a stream of its own, concurrently with the others, in
+the launch shape the server picks for the load); each must equal da_anneal on
+the same instance, schedule and seed, bit for bit.  A budget that admits one request at a time must give the same
 results, and a request that can never fit is refused."""
 import numpy as np
 import pytest
