@@ -442,16 +442,9 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     q->int8 = job->dtype == DA_INT8;
     std::string why;
     if (!da::build_instance(job->Q, q->N, job->dtype, q->inst, why)) return sfail(DA_EINVAL, why);
-    // Alone on the GPU a request takes a context's launch shape (for N > 1024
-    // the shortest step: more warps per replica); beside other requests, the
-    // fewest warps per replica (the most variables per lane), which does the
-    // most trials per warp and so per second when the SMs are shared.
-    bool busy;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        busy = !s->active.empty() || !s->pending.empty();
-    }
-    q->shape = da::default_shape(q->N, busy ? 1 << 16 : job->replicas);
+    // a context's launch shape: measured on a mix of concurrent requests it
+    // gives more trials per second than the fewest warps per replica
+    q->shape = da::default_shape(q->N, job->replicas);
     plan_request(*q);
     if ((int64_t)q->bytes > s->budget)
         return sfail(DA_EBUDGET, "request needs " + std::to_string(q->bytes) + " bytes, over the budget of " +
