@@ -77,3 +77,25 @@ def test_request_over_budget_is_refused(da):
         da.da_submit(srv, q.Q, inst.beta_linear(0.1, 1.0, 10), 0.0, 4, 0)
     assert e.value.status == 3
     srv.close()
+
+
+def test_short_request_is_not_held_behind_a_long_one(da):
+    """Requests run concurrently: a short request submitted while a long one
+    runs finishes long before it (the long one leaves SMs free), and both
+    results equal da_anneal."""
+    from paper_1806_08815_gb300 import instances as inst
+    long_q = inst.sk_gaussian(2048, 11)
+    short_q = inst.sk_bimodal(64, 12)
+    long_beta = inst.beta_linear(0.1, 4.0, 60_000)
+    short_beta = inst.beta_linear(0.1, 4.0, 500)
+    srv = da.Server(8 << 30, 8)
+    warm = da.da_submit(srv, short_q.Q, short_beta, 0.5, 2, 1)
+    da.da_poll(warm, 60_000_000)
+    rl = da.da_submit(srv, long_q.Q, long_beta, 0.0, 16, 3, 1024)
+    rs = da.da_submit(srv, short_q.Q, short_beta, 0.5, 4, 4)
+    os_ = da.da_poll(rs, 60_000_000)
+    ol = da.da_poll(rl, 120_000_000)
+    srv.close()
+    assert os_["latency_s"] < 0.5 * ol["latency_s"], (os_["latency_s"], ol["latency_s"])
+    _same(os_, _alone(da, dict(Q=short_q.Q, beta=short_beta, inc=0.5, R=4, seed=4, P=0)))
+    _same(ol, _alone(da, dict(Q=long_q.Q, beta=long_beta, inc=0.0, R=16, seed=3, P=1024)))
