@@ -339,7 +339,6 @@ bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::str
 {
     out.ldw = (int)align_up((size_t)n, 128);
     out.S = 0;
-    out.dtype = dtype;
     if (dtype == DA_INT8) {
         if (!check_integer(static_cast<const int32_t*>(Q), n, -128, 127, 1ll << 24, "DA_INT8", why)) return false;
     } else if (dtype == DA_INT16) {

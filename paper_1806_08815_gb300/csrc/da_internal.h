@@ -164,8 +164,7 @@ size_t plain_workspace_bytes(int N, int R);
 // couplings and diag from a device copy of Q (int32 entries for the integer dtypes, fp32
 // otherwise).
 struct HostInstance {
-    std::vector<char> Q;   // a host copy of Q where the caller keeps one
-    int ldw = 0, S = 0, dtype = 0;
+    int ldw = 0, S = 0;
 };
 size_t instance_W_bytes(int n, int dtype);
 // Zeroes `bytes` bytes at p (device, 16-byte aligned) with a kernel of this
