@@ -4,8 +4,7 @@
 //
 // Lane l owns the V consecutive variables i = l*V + v of the replica and keeps
 // their effective fields g_i, bits x_i and the Philox words of the current step
-// in registers.  CG selects L2-only loads of the instance (for the persistent
-// request loop, whose inputs change while it runs).  step() performs one step of Algorithm 2 (see da_step.cuh for
+// in registers.  step() performs one step of Algorithm 2 (see da_step.cuh for
 // the decomposition); recompute() replaces the fp32 fields and the tracked
 // energy by their exact fixed-point values (the same definition as the tiled
 // recompute in da_fields.cu, evaluated by the warp itself).
@@ -18,7 +17,7 @@
 namespace da {
 namespace step_detail {
 
-template <typename Tw, int V, bool CG = false>
+template <typename Tw, int V>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -168,7 +167,7 @@ struct WarpReplica {
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
-        if (FULL || base < N) Row<Tw, V, CG>::load(W + (size_t)k * ldw + base, cv);
+        if (FULL || base < N) Row<Tw, V>::load(W + (size_t)k * ldw + base, cv);
         overlap();
         if (FULL || base < N) {
             const typename A::Sign sg = A::sign(xold);
@@ -193,7 +192,7 @@ struct WarpReplica {
         long long acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            acc[v] = ((valid >> v) & 1u) ? fixed_of_f32(ldx<CG>(diag + base + v), S) : 0ll;
+            acc[v] = ((valid >> v) & 1u) ? fixed_of_f32(ldx(diag + base + v), S) : 0ll;
         const uint32_t myword = word();
         const int nw = (N + 31) >> 5;
         for (int wi = 0; wi < nw; ++wi) {
@@ -204,7 +203,7 @@ struct WarpReplica {
                 const int j = wi * 32 + b;
                 if (base < N) {
                     Tw cv[V];
-                    Row<Tw, V, CG>::load(W + (size_t)j * ldw + base, cv);
+                    Row<Tw, V>::load(W + (size_t)j * ldw + base, cv);
 #pragma unroll
                     for (int v = 0; v < V; ++v) acc[v] += fixed_of_f32(cv[v], S);
                 }
@@ -216,7 +215,7 @@ struct WarpReplica {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             if (((valid & xm) >> v) & 1u) {
-                const long long t = fixed_of_f32(ldx<CG>(diag + base + v), S) + acc[v];
+                const long long t = fixed_of_f32(ldx(diag + base + v), S) + acc[v];
                 const unsigned long long nlo = lo + (unsigned long long)t;
                 hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
                 lo = nlo;

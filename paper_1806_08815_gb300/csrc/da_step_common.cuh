@@ -122,44 +122,40 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Loads of instance data.  Kernels that live only while their inputs are
-// fixed read through the read-only path (__ldg); a persistent kernel whose
-// inputs are rewritten while it runs (the request loop) reads from L2 only
-// (__ldcg), because the L1 and read-only caches are coherent only at kernel
-// boundaries.
-template <bool CG, typename T>
+// Loads of instance data through the read-only path: a kernel's inputs are
+// fixed while it runs.
+template <typename T>
 __device__ __forceinline__ T ldx(const T* p)
 {
-    if constexpr (CG) return __ldcg(p);
-    else return __ldg(p);
+    return __ldg(p);
 }
 
 // Row k of W at the V consecutive entries of this lane (16-byte loads where
 // the lane's slice allows).
-template <typename Tw, int V, bool CG = false> struct Row;
-template <int V, bool CG> struct Row<float, V, CG> {
+template <typename Tw, int V> struct Row;
+template <int V> struct Row<float, V> {
     static __device__ __forceinline__ void load(const float* p, float (&c)[V])
     {
         static_assert(V % 4 == 0, "V");
 #pragma unroll
         for (int q = 0; q < V / 4; ++q) {
-            const float4 f = ldx<CG>(reinterpret_cast<const float4*>(p) + q);
+            const float4 f = ldx(reinterpret_cast<const float4*>(p) + q);
             c[4 * q] = f.x; c[4 * q + 1] = f.y; c[4 * q + 2] = f.z; c[4 * q + 3] = f.w;
         }
     }
 };
-template <int V, bool CG> struct Row<f32e, V, CG> {
+template <int V> struct Row<f32e, V> {
     static __device__ __forceinline__ void load(const f32e* p, f32e (&c)[V])
     {
         static_assert(V % 4 == 0, "V");
 #pragma unroll
         for (int q = 0; q < V / 4; ++q) {
-            const float4 f = ldx<CG>(reinterpret_cast<const float4*>(p) + q);
+            const float4 f = ldx(reinterpret_cast<const float4*>(p) + q);
             c[4 * q].f = f.x; c[4 * q + 1].f = f.y; c[4 * q + 2].f = f.z; c[4 * q + 3].f = f.w;
         }
     }
 };
-template <int V, bool CG> struct Row<int8_t, V, CG> {
+template <int V> struct Row<int8_t, V> {
     static __device__ __forceinline__ void unpack(uint32_t u, int8_t* c)
     {
         c[0] = (int8_t)(u & 0xFFu); c[1] = (int8_t)((u >> 8) & 0xFFu);
@@ -168,14 +164,14 @@ template <int V, bool CG> struct Row<int8_t, V, CG> {
     static __device__ __forceinline__ void load(const int8_t* p, int8_t (&c)[V])
     {
         if constexpr (V == 4) {
-            unpack(ldx<CG>(reinterpret_cast<const unsigned int*>(p)), c);
+            unpack(ldx(reinterpret_cast<const unsigned int*>(p)), c);
         } else if constexpr (V == 8) {
-            const uint2 u = ldx<CG>(reinterpret_cast<const uint2*>(p));
+            const uint2 u = ldx(reinterpret_cast<const uint2*>(p));
             unpack(u.x, c); unpack(u.y, c + 4);
         } else {
 #pragma unroll
             for (int q = 0; q < V / 16; ++q) {
-                const uint4 u = ldx<CG>(reinterpret_cast<const uint4*>(p) + q);
+                const uint4 u = ldx(reinterpret_cast<const uint4*>(p) + q);
                 unpack(u.x, c + 16 * q); unpack(u.y, c + 16 * q + 4);
                 unpack(u.z, c + 16 * q + 8); unpack(u.w, c + 16 * q + 12);
             }
@@ -183,7 +179,7 @@ template <int V, bool CG> struct Row<int8_t, V, CG> {
     }
 };
 
-template <int V, bool CG> struct Row<int16_t, V, CG> {
+template <int V> struct Row<int16_t, V> {
     static __device__ __forceinline__ void unpack(uint32_t u, int16_t* c)
     {
         c[0] = (int16_t)(u & 0xFFFFu);
@@ -192,12 +188,12 @@ template <int V, bool CG> struct Row<int16_t, V, CG> {
     static __device__ __forceinline__ void load(const int16_t* p, int16_t (&c)[V])
     {
         if constexpr (V == 4) {
-            const uint2 u = ldx<CG>(reinterpret_cast<const uint2*>(p));
+            const uint2 u = ldx(reinterpret_cast<const uint2*>(p));
             unpack(u.x, c); unpack(u.y, c + 2);
         } else {
 #pragma unroll
             for (int q = 0; q < V / 8; ++q) {
-                const uint4 u = ldx<CG>(reinterpret_cast<const uint4*>(p) + q);
+                const uint4 u = ldx(reinterpret_cast<const uint4*>(p) + q);
                 unpack(u.x, c + 8 * q); unpack(u.y, c + 8 * q + 2);
                 unpack(u.z, c + 8 * q + 4); unpack(u.w, c + 8 * q + 6);
             }

@@ -99,3 +99,19 @@ def test_short_request_is_not_held_behind_a_long_one(da):
     assert os_["latency_s"] < 0.5 * ol["latency_s"], (os_["latency_s"], ol["latency_s"])
     _same(os_, _alone(da, dict(Q=short_q.Q, beta=short_beta, inc=0.5, R=4, seed=4, P=0)))
     _same(ol, _alone(da, dict(Q=long_q.Q, beta=long_beta, inc=0.0, R=16, seed=3, P=1024)))
+
+
+def test_degenerate_and_largest_requests(da):
+    """N = 1, no steps, one replica, and the largest N of both coupling types
+    through the request loop, each equal to da_anneal."""
+    from paper_1806_08815_gb300 import instances as inst
+    jobs = [dict(Q=np.array([[5]], np.int32), beta=inst.beta_linear(0.1, 2.0, 50), inc=1.0, R=1, seed=1, P=0),
+            dict(Q=inst.sk_gaussian(33, 2).Q, beta=np.zeros(0, np.float32), inc=0.0, R=3, seed=2, P=16),
+            dict(Q=inst.sk_bimodal(8192, 3).Q, beta=inst.beta_linear(0.1, 3.0, 300), inc=1.0, R=5, seed=3, P=0),
+            dict(Q=inst.sk_gaussian(8192, 4).Q, beta=inst.beta_linear(0.1, 3.0, 300), inc=0.0, R=3, seed=4, P=128)]
+    srv = da.Server(16 << 30, 8)
+    reqs = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], j["P"]) for j in jobs]
+    outs = [da.da_poll(r, 120_000_000) for r in reqs]
+    srv.close()
+    for j, o in zip(jobs, outs):
+        _same(o, _alone(da, j))
