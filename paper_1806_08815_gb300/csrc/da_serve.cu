@@ -61,6 +61,11 @@ using Clock = std::chrono::steady_clock;
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
+// Admission stops while the running requests' step launches hold this many
+// warps per SM: beyond it further requests would only share the SMs (and L2)
+// with those already running, which stretches every request's latency.
+constexpr int kWarpsPerSm = 8;
+
 enum class ReqState { Queued, Running, Done, Failed };
 
 struct Req {
@@ -98,6 +103,9 @@ struct da_req {
 struct da_server {
     int dev = 0;
     int64_t budget = 0, used = 0;
+    // warps of the running requests' step launches, and the most admitted at
+    // once (a request is admitted alone whatever its size)
+    long long warps = 0, warp_cap = 0;
     int max_slots = 0;
     std::vector<int> free_slots;
     std::mutex mu;
@@ -307,6 +315,9 @@ void worker_loop(da_server* s)
         while (!s->pending.empty()) {
             std::shared_ptr<Req> q = s->pending.front();
             if (s->free_slots.empty() || s->used + (int64_t)q->bytes > s->budget) break;
+            const long long qw = (long long)q->job.replicas * q->shape.G;
+            if (!s->active.empty() && s->warps + qw > s->warp_cap) break;
+            s->warps += qw;
             s->pending.pop_front();
             q->slot = s->free_slots.back();
             s->free_slots.pop_back();
@@ -325,6 +336,7 @@ void worker_loop(da_server* s)
                 q->t_done = Clock::now();
                 s->active.erase(std::find(s->active.begin(), s->active.end(), q));
                 s->used -= (int64_t)q->bytes;
+                s->warps -= (long long)q->job.replicas * q->shape.G;
                 s->free_slots.push_back(q->slot);
                 s->cv_done.notify_all();
             }
@@ -354,6 +366,7 @@ void worker_loop(da_server* s)
             release(s, *q);
             s->active.erase(std::find(s->active.begin(), s->active.end(), q));
             s->used -= (int64_t)q->bytes;
+            s->warps -= (long long)q->job.replicas * q->shape.G;
             s->free_slots.push_back(q->slot);
             s->completed++;
         }
@@ -392,6 +405,12 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
         return sfail(DA_ECUDA, "no CUDA device");
     }
     s->budget = hbm_budget_bytes;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(DA_ECUDA, "no CUDA device");
+    }
+    s->warp_cap = (long long)kWarpsPerSm * sms;
     s->max_slots = max_requests;
     for (int i = max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = da::prepare_step(da::kWFp32);
