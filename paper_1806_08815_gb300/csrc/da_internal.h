@@ -5,7 +5,6 @@
 #include <cuda_runtime.h>
 
 #include <string>
-#include <vector>
 
 struct da_ctx;
 
