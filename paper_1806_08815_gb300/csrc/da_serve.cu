@@ -287,8 +287,9 @@ void release(da_server* s, Req& q)
     q.done_ev = nullptr;
 }
 
-// Copy a finished request's results to the host.
-void finish(Req& q)
+// Copy a finished request's results to the host; false on a CUDA error
+// (recorded in q.err and q.msg).
+bool finish(Req& q)
 {
     const int R = q.job.replicas;
     q.E.resize((size_t)3 * R);
@@ -302,8 +303,7 @@ void finish(Req& q)
     ok = ok && cu_ok(cudaMemcpyAsync(q.flips.data(), q.dmem + q.o_flips, q.flips.size() * 8, cudaMemcpyDeviceToHost,
                                      st),
                      q, "results");
-    ok = ok && cu_ok(cudaStreamSynchronize(st), q, "results");
-    q.state = ok ? ReqState::Done : ReqState::Failed;
+    return ok && cu_ok(cudaStreamSynchronize(st), q, "results");
 }
 
 void worker_loop(da_server* s)
@@ -345,24 +345,26 @@ void worker_loop(da_server* s)
         const bool idle = s->pending.empty() && s->active.empty();
         if (idle && s->quit) break;
         lk.unlock();
-        // completions
-        std::vector<std::shared_ptr<Req>> fin;
+        // completions: results are copied without the lock; the state that
+        // da_poll reads changes under it, after everything else it reads
+        std::vector<std::pair<std::shared_ptr<Req>, bool>> fin;
         for (auto& q : act) {
             const cudaError_t e = cudaEventQuery(q->done_ev);
             if (e == cudaErrorNotReady) continue;
+            bool ok = false;
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 q->err = DA_ECUDA;
                 q->msg = std::string("request: ") + cudaGetErrorString(e);
-                q->state = ReqState::Failed;
             } else {
-                finish(*q);
+                ok = finish(*q);
             }
             q->t_done = Clock::now();
-            fin.push_back(q);
+            fin.emplace_back(q, ok);
         }
         lk.lock();
-        for (auto& q : fin) {
+        for (auto& [q, ok] : fin) {
+            q->state = ok ? ReqState::Done : ReqState::Failed;
             release(s, *q);
             s->active.erase(std::find(s->active.begin(), s->active.end(), q));
             s->used -= (int64_t)q->bytes;
