@@ -9,10 +9,11 @@
 //       N trials of the step run in parallel, Sec. II);
 //   (b) Metropolis against the dynamic offset: delta = Delta E - E_off is
 //       accepted when delta <= 0, else when u < exp(-beta delta).  u comes from
-//       Philox block (i/4, t, replica, 0); the test is decided against a band
-//       around a hardware estimate of exp and falls back to the exact
-//       exponential only inside the band, so every decision equals the exact
-//       one;
+//       Philox block (i/4, t, replica, 0).  The test is made in the log
+//       domain, t = delta beta log2(e) + log2(2^24 u) - 24 < 0, with a
+//       hardware log2 of the draw; trials with |t| within a band of 2^-15,
+//       wider than the error of that estimate, take the exact test with the
+//       library's exponential instead, so every decision equals the exact one;
 //   (c) each lane's acceptance bits are already in index order, so a warp
 //       prefix sum of their popcounts locates the j-th accepted variable,
 //       j = floor(u * count); the chosen x_k flips while every lane adds
