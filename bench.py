@@ -42,7 +42,7 @@ C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1,
 # Warp instructions per replica-step of the step kernel (smsp__inst_executed.sum / (R x steps))
 # from the same capture: the issue-slot roofline of a kernel bound by instruction issue.
 STEP_INST_PER_REPLICA_STEP = 812.2
-STEP_TRAFFIC = {"source_sha256_16": "7bbf32aca2229073", "bytes_per_launch": 8.601344e6,
+STEP_TRAFFIC = {"source_sha256_16": "f587d5979380dd0d", "bytes_per_launch": 8.601344e6,
                 "profile": "profiles/step_kernel_f32_v32_g1_sk_gaussian_n1024_r1024.md"}
 
 
