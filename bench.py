@@ -418,6 +418,8 @@ def main():
                     help="skip the batched, PTDA and served workloads reported beside the headline")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run two 2048-step anneals from the middle of the schedule and exit (for ncu captures)")
+    ap.add_argument("--served-case", action="store_true",
+                    help="run the served workload once, print its figures and exit (for ncu launch lists)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -437,6 +439,10 @@ def main():
     da.lib()
 
     dev = torch.device("cuda", local)
+    if args.served_case:
+        r = run_served(da, instances)
+        print(json.dumps({"served_case": r["workload"], **{k: v for k, v in r.items() if k != "workload"}}))
+        return
     N, R, T, P = C3["N"], C3["replicas"], args.steps_per_anneal, C3["recompute_every"]
     q = instances.sk_gaussian(N, C3["instance_seed"])
     beta = instances.beta_linear(C3["beta0"], C3["beta1"], T)
