@@ -262,8 +262,12 @@ typedef struct da_job {
 
 /* Start a server on the current device.  hbm_budget_bytes bounds the device
  * memory of admitted requests (instance, schedule, state, results);
- * max_requests bounds how many are admitted at once.
- * Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+ * max_requests bounds how many are admitted at once.  Requests are admitted in
+ * arrival order; admission also waits while the running requests' step
+ * launches hold 8 warps per SM (replicas x warps per replica), beyond which
+ * a further request would only share SMs with them; a request is admitted
+ * alone whatever its size.  Creating a server loads and configures every
+ * kernel it launches.  Errors: DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
 da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_server** out);
 
 /* Queue a request; returns at once.  The instance is checked on the host here
