@@ -166,7 +166,8 @@ def tts99(best_E, tau_run):
     y = int(np.sum(best_E <= Eref + tol))
     r = len(best_E)
     theta = (y + 0.5) / (r + 1.0)
-    R99 = math.log(1 - 0.99) / math.log(1 - theta) if theta < 1 else 1.0
+    # at least one run: above theta = 0.99 the formula gives fewer (as the bootstrap clamps)
+    R99 = max(1.0, math.log(1 - 0.99) / math.log(1 - theta)) if theta < 1 else 1.0
     return dict(E_ref=Eref, hits=y, runs=r, theta=theta, R99=R99, tts99_s=tau_run * R99)
 
 

@@ -50,3 +50,20 @@ def test_bench_constants():
     spec.loader.exec_module(mod)
     assert mod.UNIT == "trials/s" and "trials/s" in mod.METRIC
     assert mod.C3["N"] == 1024 and mod.C3["replicas"] == 1024 and mod.C3["steps"] == 200_000
+
+
+def test_tts99_closed_form():
+    """TTS99 = tau R99 with R99 = log(0.01) / log(1 - theta), theta the Jeffreys
+    posterior mean (y + 1/2) / (r + 1), at least one run."""
+    import math
+    import numpy as np
+    import bench
+    E = np.array([-10.0, -10.0, -9.0, -8.0, -10.0 + 1e-9])       # 3 hits within the tolerance
+    t = bench.tts99(E, tau_run=2.0)
+    theta = 3.5 / 6.0
+    assert t["hits"] == 3 and t["runs"] == 5 and abs(t["theta"] - theta) < 1e-15
+    assert abs(t["R99"] - math.log(0.01) / math.log(1 - theta)) < 1e-12
+    assert abs(t["tts99_s"] - 2.0 * t["R99"]) < 1e-12
+    # every run a hit: theta = (r + 1/2) / (r + 1) > 0.99 for r >= 50, R99 clamps to one run
+    t = bench.tts99(np.full(100, -3.0), tau_run=0.5)
+    assert t["R99"] == 1.0 and t["tts99_s"] == 0.5
