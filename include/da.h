@@ -56,7 +56,8 @@ typedef enum da_status {
     DA_EBUSY = 4,     /* the context is in use by an incompatible call */
     DA_ETIMEOUT = 5,  /* a bounded wait ran out */
     DA_ECUDA = 6,     /* a CUDA call failed (no device, launch error, ...) */
-    DA_ENOTREADY = 7  /* asynchronous work has not finished yet */
+    DA_ENOTREADY = 7, /* asynchronous work has not finished yet */
+    DA_ECANCELED = 8  /* the request was cancelled (da_cancel) */
 } da_status;
 
 /* Results of da_anneal, one entry per replica r (host arrays, caller-allocated;
@@ -261,7 +262,8 @@ typedef struct da_job {
 } da_job;
 
 /* Start a server on the current device.  hbm_budget_bytes bounds the device
- * memory of admitted requests (instance, schedule, state, results);
+ * memory of admitted requests (instance, schedule, state, results, and the
+ * transient copy of Q until the instance is built from it);
  * max_requests bounds how many are admitted at once.  Requests are admitted in
  * arrival order; admission also waits while the running requests' step
  * launches hold 8 warps per SM (replicas x warps per replica), beyond which
@@ -272,10 +274,16 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
 
 /* Queue a request; returns at once.  The instance is checked on the host here
  * (as da_create); its device layout is built at admission from a transient
- * device copy of Q (N*N*4 bytes, outside the budget, freed once built).
+ * device copy of Q (N*N*4 bytes, charged to the budget from admission until
+ * the build is done).  The request loop is the one entry point that takes a
+ * server instead of a context: a request carries its own instance, which the
+ * server builds on its own stream, so that no context (and no host
+ * synchronisation of one) stands between requests.
  * Errors: DA_EINVAL; DA_EBUDGET if the request alone
  * exceeds the budget (it could never be admitted); DA_EBUSY while the server is
- * shutting down. */
+ * shutting down.  A request whose device allocation fails at admission
+ * finishes with DA_ENOMEM (reported by da_poll); the server goes on with the
+ * others. */
 da_status da_submit(da_server* srv, const da_job* job, da_req** out);
 
 /* Wait up to timeout_us microseconds for a request.  DA_OK: results written to
@@ -287,10 +295,20 @@ da_status da_poll(da_req* req, int32_t timeout_us, da_result* out);
 /* Release a request handle (after its last poll). */
 void da_req_free(da_req* req);
 
+/* Cancel a request.  A queued request leaves the queue at once; a running one
+ * stops at the start of its next step launch (launches already running finish
+ * their chunk), then its memory returns to the budget.  da_poll then returns
+ * DA_ECANCELED.  Cancelling a finished request changes nothing.
+ * Errors: DA_EINVAL (null request). */
+da_status da_cancel(da_req* req);
+
 /* Requests completed, kernels queued so far (all requests), device bytes in use. */
 da_status da_server_stats(da_server* srv, int64_t* completed, int64_t* kernel_launches, int64_t* bytes_in_use);
 
-/* Wait for every submitted request to finish, stop the kernel, free everything. */
+/* Wait for every submitted request to finish, then free the server.  A da_req
+ * refers to its server: poll every request for the last time before
+ * da_server_destroy (da_poll and da_cancel on a request of a destroyed server
+ * are undefined); da_req_free may follow at any time. */
 void da_server_destroy(da_server* srv);
 
 /* Parallel tempering with the DA step (PTDA, Sec. II and Algorithm 4): L
@@ -354,26 +372,46 @@ da_status da_profile_read(da_ctx* ctx, int64_t* launches, double* total_ms);
  * the library holds it until the process exits); it calls no cudaMalloc,
  * cudaFree or other allocating routine.  The paper has no counterpart: this
  * is a property of the library, not of the method.
- *   W      device, int8, N x ldw row-major: the symmetric couplings W_ij = Q_ij
- *          (i < j) mirrored, zero diagonal; entries in columns N..ldw-1 are read
- *          but only affect padding.  ldw >= da_static_pitch(N), a multiple of 16.
- *   diag   device, int32, the N linear terms Q_ii.
+ *   W      device, int8, N x ldw row-major, 16-byte aligned (rows are read
+ *          with 16-byte loads): the symmetric couplings W_ij = Q_ij (i < j)
+ *          mirrored, zero diagonal; entries in columns N..ldw-1 are read but
+ *          only affect padding.  da_static_pitch(N) <= ldw <= INT_MAX, a
+ *          multiple of 16.
+ *   diag   device, int32, the N linear terms Q_ii (4-byte aligned).
  *   N      1 <= N <= 1024.
- *   beta   device, [steps] schedule; other arguments as in da_anneal_async.
- *   out    device result arrays (each may be NULL).
- * Sizes beyond the array (roughly replicas * N > 3.4e6 at N = 1024) return
- * DA_EINVAL.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  Every call reuses the same array, so calls that overlap on the GPU
- * (different streams, or different host threads without ordering) race; order
- * them on one stream.  The call re-initialises the parts it needs, so results do
- * not depend on earlier calls.  Errors: DA_EINVAL, DA_ECUDA. */
+ *   beta   device, [steps] schedule (4-byte aligned); other arguments as in
+ *          da_anneal_async.
+ *   out    device result arrays (each may be NULL), each aligned to its
+ *          element size.
+ * A misaligned pointer or a pitch out of range returns DA_EINVAL before
+ * anything is queued.  Sizes beyond the array (roughly replicas * N > 3.4e6 at
+ * N = 1024) return DA_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it with the current CUDA
+ * context (it is looked up again when the context changes); make that first
+ * call before any stream capture.  A context destroyed by cudaDeviceReset may
+ * be re-created under the same handle with the array elsewhere, so do not call
+ * this entry point again after a device reset.  Every call reuses the same
+ * array, so calls that overlap on the GPU (different streams, or different host
+ * threads without ordering) race; order them on one stream.  The call
+ * re-initialises the parts it needs, so results do not depend on earlier
+ * calls.  Errors: DA_EINVAL, DA_ECUDA. */
 da_status da_anneal_static(const int8_t* W, const int32_t* diag, int64_t N, int64_t ldw, const float* beta,
                            int64_t steps, float offset_inc, int32_t replicas, uint64_t seed,
                            const da_dev_result* out, void* stream);
 /* The smallest row pitch da_anneal_static accepts for N variables (0 if N is
  * out of range). */
 int64_t da_static_pitch(int64_t N);
+
+/* Failure injection for tests of the error paths (host side; nothing is
+ * faulted on the device): the library's next `after` device allocations (of
+ * contexts, workspaces, tensor-core operands, batched launches and admitted
+ * requests) succeed and the `count` after them fail as if the device were out
+ * of memory, without being attempted.  count = 0 disarms.
+ * da_diag_live_allocations: device allocations of the library that are live
+ * now and their bytes, and how many failures were injected so far.
+ * Errors: DA_EINVAL (negative arguments). */
+da_status da_diag_fail_alloc(int32_t after, int32_t count);
+da_status da_diag_live_allocations(int64_t* count, int64_t* bytes, int64_t* injected_failures);
 
 /* Diagnostics: run the device's own fp32 exponential (used for every
  * Metropolis decision) on n host values x[n] -> y[n], and its Philox4x32-10

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libda.so")
 
 DA_INT8, DA_FP32, DA_INT16 = 0, 1, 2
 STATUS = {0: "DA_OK", 1: "DA_EINVAL", 2: "DA_ENOMEM", 3: "DA_EBUDGET", 4: "DA_EBUSY",
-          5: "DA_ETIMEOUT", 6: "DA_ECUDA", 7: "DA_ENOTREADY"}
+          5: "DA_ETIMEOUT", 6: "DA_ECUDA", 7: "DA_ENOTREADY", 8: "DA_ECANCELED"}
 
 
 class DAError(RuntimeError):
@@ -99,6 +99,12 @@ def lib() -> ctypes.CDLL:
     L.da_poll.argtypes = [_P, i32, ctypes.POINTER(da_result)]
     L.da_req_free.argtypes = [_P]
     L.da_req_free.restype = None
+    L.da_cancel.argtypes = [_P]
+    L.da_cancel.restype = ctypes.c_int
+    L.da_diag_fail_alloc.argtypes = [i32, i32]
+    L.da_diag_fail_alloc.restype = ctypes.c_int
+    L.da_diag_live_allocations.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.da_diag_live_allocations.restype = ctypes.c_int
     L.da_server_destroy.argtypes = [_P]
     L.da_server_destroy.restype = None
     L.da_server_stats.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -499,3 +505,20 @@ def da_poll(req: Request, timeout_us: int = 0):
     _check(st)
     out["latency_s"] = res.elapsed_s
     return out
+
+
+def da_cancel(req: Request) -> None:
+    """Cancel a queued or running request (da_poll then raises DA_ECANCELED)."""
+    _check(lib().da_cancel(req.handle))
+
+
+def da_diag_fail_alloc(after: int, count: int) -> None:
+    """Make the library's device allocations after the next `after` fail, `count` times
+    (host-side injection; count = 0 disarms)."""
+    _check(lib().da_diag_fail_alloc(int(after), int(count)))
+
+
+def da_diag_live_allocations() -> dict:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().da_diag_live_allocations(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(count=a.value, bytes=b.value, injected=c.value)

@@ -118,11 +118,11 @@ da_status ensure_ws(da_ctx* c, size_t bytes)
     if (bytes <= c->ws_bytes) return DA_OK;
     if (c->ws) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(c->ws);
+        da::dev_free(c->ws);
         c->ws = nullptr;
         c->ws_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    cudaError_t e = da::dev_malloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(DA_ENOMEM, std::string("workspace of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
@@ -422,20 +422,20 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     // DA_INT8 also keeps its couplings as exact fp32, same pitch and slack
     const size_t qbytes = (size_t)n * n * 4;
     void* qd = nullptr;
-    e = cudaMalloc(&c->W, da::instance_W_bytes(n, (int)dtype));
-    if (e == cudaSuccess) e = cudaMalloc(&c->diag, (size_t)n * 4);
-    if (e == cudaSuccess && dtype == DA_INT8) e = cudaMalloc(&c->Wf, da::instance_W_bytes(n, DA_FP32));
-    if (e == cudaSuccess) e = cudaMalloc(&qd, qbytes);
+    e = da::dev_malloc(&c->W, da::instance_W_bytes(n, (int)dtype));
+    if (e == cudaSuccess) e = da::dev_malloc(&c->diag, (size_t)n * 4);
+    if (e == cudaSuccess && dtype == DA_INT8) e = da::dev_malloc(&c->Wf, da::instance_W_bytes(n, DA_FP32));
+    if (e == cudaSuccess) e = da::dev_malloc(&qd, qbytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        if (qd) cudaFree(qd);
+        if (qd) da::dev_free(qd);
         return bail(DA_ENOMEM, std::string("instance: ") + cudaGetErrorString(e));
     }
     e = cudaMemcpyAsync(qd, Q, qbytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = da::launch_expand_instance(qd, n, ldw, (int)dtype, c->W, static_cast<float*>(c->Wf), c->diag, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    const cudaError_t ef = cudaFree(qd);
+    const cudaError_t ef = da::dev_free(qd);
     if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) return bail(DA_ECUDA, std::string("instance upload: ") + cudaGetErrorString(e));
     e = da::tc_operand_build((int)dtype, c->W, c->diag, n, ldw, c->S, &c->tc, c->stream);
@@ -479,11 +479,11 @@ void da_destroy(da_ctx* c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->W) cudaFree(c->W);
-    if (c->Wf) cudaFree(c->Wf);
-    if (c->diag) cudaFree(c->diag);
+    if (c->W) da::dev_free(c->W);
+    if (c->Wf) da::dev_free(c->Wf);
+    if (c->diag) da::dev_free(c->diag);
     da::tc_operand_free(&c->tc);
-    if (c->ws) cudaFree(c->ws);
+    if (c->ws) da::dev_free(c->ws);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);

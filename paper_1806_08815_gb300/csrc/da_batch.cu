@@ -308,7 +308,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     const size_t o_heads = off;
     off += da::al(classes.size() * 8);
     char* base = nullptr;
-    if (cudaMalloc(&base, off) != cudaSuccess) {
+    if (da::dev_malloc(reinterpret_cast<void**>(&base), off) != cudaSuccess) {
         cudaGetLastError();
         return bfail(DA_ENOMEM, "batch workspace of " + std::to_string(off) + " bytes");
     }
@@ -323,7 +323,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
         if (st) cudaStreamDestroy(st);
-        cudaFree(base);
+        da::dev_free(base);
     };
 #define DA_B(call)                                                                         \
     do {                                                                                   \

@@ -59,6 +59,8 @@ struct StepParams {
     int* trace = nullptr;         // optional [R][trace_T]
     long long trace_T = 0;
     int* err = nullptr;           // device flag, set to 2 when a bounded wait gives up
+    const int* stop = nullptr;    // optional flag (host-mapped): a launch that finds it
+                                  // set returns at once (a cancelled request)
 };
 
 // Philox4x32-10 round keys k + r * Weyl (r = 0..9) of a seed.
@@ -207,6 +209,14 @@ inline bool schedule_ok(const float* beta, long long n)
         if (!(beta[t] >= 0.f) || beta[t] == __builtin_huge_valf()) return false;
     return true;
 }
+
+// The library's device allocations (da_alloc.cu): cudaMalloc / cudaFree and
+// cudaMallocFromPoolAsync / cudaFreeAsync with a count of live allocations,
+// and the host-side failure injection of da_diag_fail_alloc.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+cudaError_t pool_malloc_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st);
+cudaError_t pool_free_async(void* p, cudaStream_t st);
 
 // Error text returned by da_last_error() on the calling thread (da_api.cu).
 void set_last_error(const std::string& msg);

@@ -388,9 +388,9 @@ cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, 
     op->kchunks = (N + kBK - 1) / kBK;
     const int itiles = (N + kBN - 1) / kBN;
     const size_t bytes = (size_t)itiles * op->kchunks * op->limbs * kBTile;
-    cudaError_t e = cudaMalloc(&op->B, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&op->err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&op->dfix, (size_t)op->kchunks * kBK * sizeof(long long));
+    cudaError_t e = dev_malloc(&op->B, bytes);
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->err), sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->dfix), (size_t)op->kchunks * kBK * sizeof(long long));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(op->err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -414,9 +414,9 @@ cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, 
 
 void tc_operand_free(TcOperand* op)
 {
-    if (op->B) cudaFree(op->B);
-    if (op->err) cudaFree(op->err);
-    if (op->dfix) cudaFree(op->dfix);
+    if (op->B) dev_free(op->B);
+    if (op->err) dev_free(op->err);
+    if (op->dfix) dev_free(op->dfix);
     *op = TcOperand{};
 }
 

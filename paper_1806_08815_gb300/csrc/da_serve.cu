@@ -18,7 +18,10 @@
 // until it ends.
 //
 // A worker thread admits, polls completion events, copies results and frees
-// memory; da_poll waits on a request with a timeout.
+// memory; da_poll waits on a request with a timeout.  da_cancel takes a queued
+// request out of the queue, and makes a running one's remaining step launches
+// return at once (a host-mapped stop flag per request slot that every step
+// launch reads when it starts).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -75,6 +78,9 @@ struct Req {
     da::StepShape shape;              // launch shape of the step kernel
     da::HostInstance inst;            // checked at submit (ldw, S); W and diag built on the device at admission
     size_t bytes = 0;                 // device bytes charged to the budget
+    size_t qcopy = 0;                 // the transient device copy of Q (N*N*4 bytes), charged
+    bool qcopy_held = false;          //   to the budget from admission until the instance is built
+    bool cancelled = false;           // da_cancel on a running request
     int slot = -1;
     ReqState state = ReqState::Queued;
     da_status err = DA_OK;
@@ -91,6 +97,7 @@ struct Req {
     Clock::time_point t_submit, t_done;
     cudaStream_t stream = nullptr;    // from the server's stream pool while running
     cudaEvent_t done_ev = nullptr;
+    cudaEvent_t built_ev = nullptr;   // recorded after the copy of Q is freed
 };
 
 }  // namespace
@@ -121,6 +128,9 @@ struct da_server {
     // has reserved (a pool that trims at every synchronisation unmaps memory,
     // which waits for the running kernels)
     cudaMemPool_t pool = nullptr;
+    // a stop flag per request slot in host-mapped memory, read by every step
+    // launch of the request in that slot (set by da_cancel)
+    int* stop = nullptr;
     // statistics
     long long kernel_launches = 0, completed = 0;
 };
@@ -131,6 +141,15 @@ da_status sfail(da_status s, const std::string& m)
 {
     da::set_last_error(m);
     return s;
+}
+
+bool cu_ok_static(cudaError_t e, Req& q, const char* what)
+{
+    if (e == cudaSuccess) return true;
+    cudaGetLastError();
+    q.err = DA_ECUDA;
+    q.msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
 }
 
 // Device bytes of a request and its buffer offsets.
@@ -155,16 +174,24 @@ void plan_request(Req& q)
     q.o_E = take((size_t)3 * R * 8);
     q.o_flips = take((size_t)R * 8);
     q.bytes = o;
+    q.qcopy = al256((size_t)q.N * q.N * 4);
 }
 
-bool cu_ok(cudaError_t e, Req& q, const char* what)
+// Device bytes a request holds at its peak (its buffers and the copy of Q).
+size_t peak_bytes(const Req& q) { return q.bytes + q.qcopy; }
+
+// Takes an event from the server's pool or creates one.
+bool take_event(da_server* s, Req& q, cudaEvent_t* ev)
 {
-    if (e == cudaSuccess) return true;
-    cudaGetLastError();
-    q.err = DA_ECUDA;
-    q.msg = std::string(what) + ": " + cudaGetErrorString(e);
-    return false;
+    if (!s->events.empty()) {
+        *ev = s->events.back();
+        s->events.pop_back();
+        return true;
+    }
+    return cu_ok_static(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), q, "event");
 }
+
+bool cu_ok(cudaError_t e, Req& q, const char* what) { return cu_ok_static(e, q, what); }
 
 // Queue all of an admitted request's work on its stream.  Runs on the worker
 // thread and returns without waiting for the GPU.
@@ -176,14 +203,9 @@ bool admit(da_server* s, Req& q, long long& launches)
     } else if (!cu_ok(cudaStreamCreateWithFlags(&q.stream, cudaStreamNonBlocking), q, "stream")) {
         return false;
     }
-    if (!s->events.empty()) {
-        q.done_ev = s->events.back();
-        s->events.pop_back();
-    } else if (!cu_ok(cudaEventCreateWithFlags(&q.done_ev, cudaEventDisableTiming), q, "event")) {
-        return false;
-    }
+    if (!take_event(s, q, &q.done_ev) || !take_event(s, q, &q.built_ev)) return false;
     cudaStream_t st = q.stream;
-    if (cudaMallocFromPoolAsync(reinterpret_cast<void**>(&q.dmem), q.bytes, s->pool, st) != cudaSuccess) {
+    if (da::pool_malloc_async(reinterpret_cast<void**>(&q.dmem), q.bytes, s->pool, st) != cudaSuccess) {
         cudaGetLastError();
         q.dmem = nullptr;
         q.err = DA_ENOMEM;
@@ -198,7 +220,7 @@ bool admit(da_server* s, Req& q, long long& launches)
     {
         void* qd = nullptr;
         const size_t qbytes = (size_t)q.N * q.N * 4;
-        if (cudaMallocFromPoolAsync(&qd, qbytes, s->pool, st) != cudaSuccess) {
+        if (da::pool_malloc_async(&qd, qbytes, s->pool, st) != cudaSuccess) {
             cudaGetLastError();
             q.err = DA_ENOMEM;
             q.msg = "device allocation of " + std::to_string(qbytes) + " bytes (copy of Q)";
@@ -209,8 +231,8 @@ bool admit(da_server* s, Req& q, long long& launches)
                                                     static_cast<float*>(Wf), diag, st),
                          q, "build instance");
         launches += 3;
-        cudaFreeAsync(qd, st);
-        if (!ok) return false;
+        da::pool_free_async(qd, st);
+        if (!ok || !cu_ok(cudaEventRecord(q.built_ev, st), q, "event")) return false;
     }
     if (q.job.steps > 0 &&
         !cu_ok(cudaMemcpyAsync(q.dmem + q.o_beta, q.job.beta, (size_t)q.job.steps * 4, cudaMemcpyHostToDevice, st), q,
@@ -243,6 +265,7 @@ bool admit(da_server* s, Req& q, long long& launches)
     p.sc = sc;
     p.beta = reinterpret_cast<const float*>(q.dmem + q.o_beta);
     p.inc = q.job.offset_inc;
+    p.stop = s->stop + q.slot;
     da::set_seed(p, q.job.seed);
     const long long T = q.job.steps, P = q.int8 ? 0 : q.job.recompute_every;
     for (long long t0 = 0; t0 < T; t0 = p.t1) {
@@ -278,13 +301,25 @@ bool admit(da_server* s, Req& q, long long& launches)
 void release(da_server* s, Req& q)
 {
     if (q.stream) {
-        if (q.dmem) cudaFreeAsync(q.dmem, q.stream);
+        if (q.dmem) da::pool_free_async(q.dmem, q.stream);
         s->streams.push_back(q.stream);
     }
     if (q.done_ev) s->events.push_back(q.done_ev);
+    if (q.built_ev) s->events.push_back(q.built_ev);
     q.dmem = nullptr;
     q.stream = nullptr;
     q.done_ev = nullptr;
+    q.built_ev = nullptr;
+}
+
+// The budget a request returns when it leaves the GPU (its buffers, and the
+// copy of Q if its release was not seen yet), and its slot and warps.
+void uncharge(da_server* s, Req& q)
+{
+    s->used -= (int64_t)q.bytes + (q.qcopy_held ? (int64_t)q.qcopy : 0);
+    q.qcopy_held = false;
+    s->warps -= (long long)q.job.replicas * q.shape.G;
+    s->free_slots.push_back(q.slot);
 }
 
 // Copy a finished request's results to the host; false on a CUDA error
@@ -314,15 +349,17 @@ void worker_loop(da_server* s)
         // admission, in arrival order, while memory and slots allow
         while (!s->pending.empty()) {
             std::shared_ptr<Req> q = s->pending.front();
-            if (s->free_slots.empty() || s->used + (int64_t)q->bytes > s->budget) break;
+            if (s->free_slots.empty() || s->used + (int64_t)peak_bytes(*q) > s->budget) break;
             const long long qw = (long long)q->job.replicas * q->shape.G;
             if (!s->active.empty() && s->warps + qw > s->warp_cap) break;
             s->warps += qw;
             s->pending.pop_front();
             q->slot = s->free_slots.back();
             s->free_slots.pop_back();
-            s->used += (int64_t)q->bytes;
+            s->used += (int64_t)peak_bytes(*q);
+            q->qcopy_held = true;
             q->state = ReqState::Running;
+            s->stop[q->slot] = 0;   // no step launch of this request is queued yet
             s->active.push_back(q);
             lk.unlock();
             long long launches = 0;
@@ -330,15 +367,24 @@ void worker_loop(da_server* s)
             lk.lock();
             s->kernel_launches += launches;
             if (!ok) {
-                if (q->stream) cudaStreamSynchronize(q->stream);   // what was queued, before the memory goes
+                if (q->stream) {            // what was queued, before the memory goes (without the lock)
+                    lk.unlock();
+                    cudaStreamSynchronize(q->stream);
+                    lk.lock();
+                }
                 release(s, *q);
                 q->state = ReqState::Failed;
                 q->t_done = Clock::now();
                 s->active.erase(std::find(s->active.begin(), s->active.end(), q));
-                s->used -= (int64_t)q->bytes;
-                s->warps -= (long long)q->job.replicas * q->shape.G;
-                s->free_slots.push_back(q->slot);
+                uncharge(s, *q);
                 s->cv_done.notify_all();
+            }
+        }
+        // the copy of Q of a request whose instance is built goes back to the budget
+        for (auto& q : s->active) {
+            if (q->qcopy_held && q->built_ev && cudaEventQuery(q->built_ev) == cudaSuccess) {
+                s->used -= (int64_t)q->qcopy;
+                q->qcopy_held = false;
             }
         }
         std::vector<std::shared_ptr<Req>> act = s->active;
@@ -356,6 +402,9 @@ void worker_loop(da_server* s)
                 cudaGetLastError();
                 q->err = DA_ECUDA;
                 q->msg = std::string("request: ") + cudaGetErrorString(e);
+            } else if (q->cancelled) {
+                q->err = DA_ECANCELED;
+                q->msg = "cancelled";
             } else {
                 ok = finish(*q);
             }
@@ -367,9 +416,7 @@ void worker_loop(da_server* s)
             q->state = ok ? ReqState::Done : ReqState::Failed;
             release(s, *q);
             s->active.erase(std::find(s->active.begin(), s->active.end(), q));
-            s->used -= (int64_t)q->bytes;
-            s->warps -= (long long)q->job.replicas * q->shape.G;
-            s->free_slots.push_back(q->slot);
+            uncharge(s, *q);
             s->completed++;
         }
         if (!fin.empty()) s->cv_done.notify_all();
@@ -388,6 +435,8 @@ void destroy_resources(da_server* s)
     s->events.clear();
     if (s->pool) cudaMemPoolDestroy(s->pool);
     s->pool = nullptr;
+    if (s->stop) cudaFreeHost(s->stop);
+    s->stop = nullptr;
 }
 
 }  // namespace
@@ -423,6 +472,14 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return sfail(DA_ECUDA, std::string("kernels: ") + cudaGetErrorString(e));
+    if ((e = cudaHostAlloc(reinterpret_cast<void**>(&s->stop), (size_t)max_requests * sizeof(int),
+                           cudaHostAllocMapped)) != cudaSuccess) {
+        cudaGetLastError();
+        s->stop = nullptr;
+        destroy_resources(s.get());
+        return sfail(DA_ENOMEM, std::string("stop flags: ") + cudaGetErrorString(e));
+    }
+    std::memset(s->stop, 0, (size_t)max_requests * sizeof(int));
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -467,8 +524,9 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     // gives more trials per second than the fewest warps per replica
     q->shape = da::default_shape(q->N, job->replicas);
     plan_request(*q);
-    if ((int64_t)q->bytes > s->budget)
-        return sfail(DA_EBUDGET, "request needs " + std::to_string(q->bytes) + " bytes, over the budget of " +
+    if ((int64_t)peak_bytes(*q) > s->budget)
+        return sfail(DA_EBUDGET, "request needs " + std::to_string(peak_bytes(*q)) +
+                                     " bytes (with the transient copy of Q), over the budget of " +
                                      std::to_string(s->budget));
     q->t_submit = Clock::now();
     {
@@ -512,6 +570,33 @@ da_status da_poll(da_req* req, int32_t timeout_us, da_result* out)
 }
 
 void da_req_free(da_req* req) { delete req; }
+
+da_status da_cancel(da_req* req)
+{
+    da::set_last_error("");
+    if (!req || !req->r) return sfail(DA_EINVAL, "null request");
+    da_server* s = req->srv;
+    std::shared_ptr<Req> q = req->r;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (q->state == ReqState::Queued) {
+            auto it = std::find(s->pending.begin(), s->pending.end(), q);
+            if (it != s->pending.end()) s->pending.erase(it);
+            q->state = ReqState::Failed;
+            q->err = DA_ECANCELED;
+            q->msg = "cancelled";
+            q->t_done = Clock::now();
+        } else if (q->state == ReqState::Running) {
+            q->cancelled = true;
+            // step launches that start from now on return at once; what is
+            // already running finishes its chunk
+            reinterpret_cast<volatile int*>(s->stop)[q->slot] = 1;
+        }
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+    return DA_OK;
+}
 
 da_status da_server_stats(da_server* s, int64_t* completed, int64_t* kernel_launches, int64_t* bytes_in_use)
 {

@@ -8,8 +8,11 @@
 // buffer placed in one file-scope device array of fixed size; the caller
 // passes the instance, the schedule and the result buffers in device memory.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <mutex>
+#include <string>
 
 #include "da.h"
 #include "da_internal.h"
@@ -21,7 +24,40 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
+// The array's device address per device, with the CUDA context it was looked
+// up in: a context that is destroyed and created again (cudaDeviceReset) loads
+// the module again, possibly at another address.
 void* g_static_ptr[kMaxDevices] = {};
+void* g_static_ctx[kMaxDevices] = {};
+
+// The calling thread's current CUDA context (driver handle), through the
+// runtime's driver entry point so that the library needs no link to libcuda;
+// nullptr if it cannot be had.
+void* current_context()
+{
+    using GetCurrent = int (*)(void**);
+    static GetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<GetCurrent>(f);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+da_status fail(da_status s, const char* why)
+{
+    da::set_last_error(why);
+    return s;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -50,11 +86,22 @@ extern "C" da_status da_anneal_static(const int8_t* W, const int32_t* diag, int6
                                       const float* beta, int64_t steps, float offset_inc, int32_t replicas,
                                       uint64_t seed, const da_dev_result* out, void* stream)
 {
-    if (!W || !diag || N < 1 || N > 1024) return DA_EINVAL;
+    da::set_last_error("");
+    if (!W || !diag || N < 1 || N > 1024) return fail(DA_EINVAL, "need W, diag and 1 <= N <= 1024");
     const int64_t pitch = da_static_pitch(N);
-    if (ldw < pitch || ldw % 16 != 0) return DA_EINVAL;
-    if (replicas < 1 || steps < 0 || steps >= (1ll << 32) || (steps > 0 && !beta)) return DA_EINVAL;
-    if (!(offset_inc >= 0.f) || !std::isfinite(offset_inc)) return DA_EINVAL;
+    if (ldw < pitch || ldw % 16 != 0 || ldw > INT_MAX)
+        return fail(DA_EINVAL, "ldw must be a multiple of 16, at least da_static_pitch(N) and at most INT_MAX");
+    // the step kernel reads a lane's slice of a row of W with 16-byte loads
+    // and diag as 4-byte words: a misaligned pointer would fault the device
+    if (!aligned(W, 16)) return fail(DA_EINVAL, "W must be 16-byte aligned");
+    if (!aligned(diag, 4) || (beta && !aligned(beta, 4))) return fail(DA_EINVAL, "diag and beta must be 4-byte aligned");
+    if (out && (!aligned(out->final_E, 8) || !aligned(out->best_E, 8) || !aligned(out->max_drift, 8) ||
+                !aligned(out->flips, 8) || !aligned(out->final_x, 4) || !aligned(out->best_x, 4) ||
+                !aligned(out->trace, 4)))
+        return fail(DA_EINVAL, "result arrays must be aligned to their element size");
+    if (replicas < 1 || steps < 0 || steps >= (1ll << 32) || (steps > 0 && !beta))
+        return fail(DA_EINVAL, "need replicas >= 1, 0 <= steps < 2^32 and a schedule");
+    if (!(offset_inc >= 0.f) || !std::isfinite(offset_inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
 
     da::StepShape s;
     s.V = (int)(pitch / 32);
@@ -69,20 +116,27 @@ extern "C" da_status da_anneal_static(const int8_t* W, const int32_t* diag, int6
     const size_t o_part = o_sc + align256((size_t)R * sizeof(da::ReplicaScalars));
     const size_t o_eex = o_part + align256(tiles * 16 * 2 * (size_t)R);
     const size_t total = o_eex + align256((size_t)2 * R * 8);
-    if (total > kStaticBytes) return DA_EINVAL;   // beyond the fixed scratch array
+    if (total > kStaticBytes)
+        return fail(DA_EINVAL, ("the replica state needs " + std::to_string(total) +
+                                " bytes, more than the fixed 16 MiB array").c_str());
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DA_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return fail(DA_ECUDA, "no usable CUDA device");
+    }
     char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_static_mu);
-        if (!g_static_ptr[dev]) {
+        void* ctx = current_context();
+        if (!g_static_ptr[dev] || ctx != g_static_ctx[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
-                return DA_ECUDA;
+                return fail(DA_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
             }
             g_static_ptr[dev] = p;
+            g_static_ctx[dev] = ctx;
         }
         base = static_cast<char*>(g_static_ptr[dev]);
     }

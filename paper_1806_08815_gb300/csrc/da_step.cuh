@@ -40,6 +40,18 @@
 namespace da {
 namespace step_detail {
 
+// A launch whose stop flag is set (a cancelled request of the request loop)
+// returns at once and leaves the replica state as it was.  One thread reads
+// the flag for the block, so that every warp of the block takes the same
+// branch (the G > 1 groups meet at barriers).
+__device__ __forceinline__ bool launch_stopped(const StepParams& p)
+{
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) s_stop = p.stop ? *reinterpret_cast<const volatile int*>(p.stop) : 0;
+    __syncthreads();
+    return s_stop != 0;
+}
+
 template <typename Tw, int V, int G, bool FULL, bool TRACE>
 __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G, V>::min_blocks)
     step_kernel(const __grid_constant__ StepParams p)
@@ -53,6 +65,7 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
     constexpr int P = 32 / V;                       // lanes per state word
 
     extern __shared__ uint32_t smem[];
+    if (launch_stopped(p)) return;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int g = wib / G;                          // group (replica) within the block
@@ -260,6 +273,7 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
 {
     using R_ = WarpReplica<Tw, V>;
     using H = typename R_::H;
+    if (launch_stopped(p)) return;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= p.R) return;
     R_ rp;
@@ -333,7 +347,8 @@ __global__ void __launch_bounds__(64, 7) step_kernel_ws(const __grid_constant__ 
             tc::mbar_init(&full[b], 32);
             tc::mbar_init(&empty[b], 32);
         }
-        failed = p.err ? *reinterpret_cast<volatile int*>(p.err) : 0;
+        failed = (p.err ? *reinterpret_cast<volatile int*>(p.err) : 0) |
+                 (p.stop ? *reinterpret_cast<const volatile int*>(p.stop) : 0);
     }
     __syncthreads();
     if (failed) return;     // whole block

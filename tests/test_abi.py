@@ -30,11 +30,23 @@ def libda():
     return binding.lib()
 
 
+# The boundary the library is built around: instance contexts and the anneal
+# (Algorithm 2), PTDA (Sec. II, Algorithm 4), the request loop, the batched and
+# plain forms, the allocation-free anneal, exact energies and the diagnostics
+# the tests use.
+REQUIRED = ("da_create", "da_destroy", "da_anneal", "da_anneal_async", "da_pt", "da_pt_adaptive",
+            "da_last_error", "da_energy", "da_field_recompute",
+            "da_server_create", "da_submit", "da_poll", "da_cancel", "da_req_free", "da_server_stats",
+            "da_server_destroy",
+            "da_batch_anneal", "da_anneal_plain", "da_anneal_static", "da_static_pitch",
+            "da_quantize", "da_move_energy_percentiles", "da_tts_bootstrap", "da_percentiles",
+            "da_diag_fail_alloc", "da_diag_live_allocations")
+
+
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("da_create", "da_anneal", "da_anneal_async", "da_pt", "da_destroy", "da_last_error",
-                     "da_energy", "da_field_recompute"):
-        assert required in names
+    missing = [r for r in REQUIRED if r not in names]
+    assert not missing, missing
 
 
 def test_library_exports_every_declared_symbol(libda):
@@ -77,3 +89,19 @@ def test_server_needs_a_device(libda):
     h = ctypes.c_void_p()
     assert libda.da_server_create(ctypes.c_int64(1 << 30), 16, ctypes.byref(h)) == 6
     assert libda.da_server_create(ctypes.c_int64(0), 16, ctypes.byref(h)) == 1
+
+
+def test_failure_injection_arguments(libda):
+    """The failure-injection switch validates its arguments and can be disarmed
+    without a device; nothing is live before any allocation."""
+    assert libda.da_diag_fail_alloc(-1, 1) == 1
+    assert libda.da_diag_fail_alloc(0, -1) == 1
+    assert libda.da_diag_fail_alloc(0, 0) == 0
+    c, b, inj = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    assert libda.da_diag_live_allocations(ctypes.byref(c), ctypes.byref(b), ctypes.byref(inj)) == 0
+    assert c.value >= 0 and b.value >= 0 and inj.value >= 0
+
+
+def test_cancel_rejects_null(libda):
+    from paper_1806_08815_gb300 import binding as b
+    assert libda.da_cancel(None) == 1

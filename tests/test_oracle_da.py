@@ -306,3 +306,59 @@ def test_adaptive_ptda_evens_out_exchange_rates(orc):
     assert adapt["betas"][0] == b0[0] and adapt["betas"][-1] == b0[-1]
     assert np.all(np.diff(adapt["betas"]) > 0)
     assert not np.array_equal(adapt["betas"], b0)
+
+
+def test_ptda_sequential_pair_order_three_temperatures(orc):
+    """Algorithm 4's exchange pass at K = 3 after one sweep: pair (0, 1) is
+    proposed first with min(1, exp((b0 - b1)(E_a - E_b))) for the replicas a, b
+    at indices 0 and 1; pair (1, 2) is proposed next between the replica that
+    holds index 1 after that first decision and the replica at index 2.  With
+    the energies after the sweep fixed (the exchange moves labels, not states),
+    the joint frequencies of the two decisions follow in closed form; the test
+    also shows that the labels before the first swap (a plausible mistake)
+    would be rejected by the same data."""
+    inst = instances.sk_bimodal(12, 21)
+    b = np.array([0.15, 0.5, 1.4], np.float32)
+    L = 20000
+    pt = orc.ptda(inst.Q, b, 1, L=L, seed=5)
+    E = pt["E_final"]                      # [L, 3] energies of replicas 0, 1, 2 after the sweep
+    s0 = pt["swap_trace"][:, 0, 0].astype(bool)
+    s1 = pt["swap_trace"][:, 0, 1].astype(bool)
+    b64 = b.astype(np.float64)
+
+    def p_swap(bi, bj, Ei, Ej):
+        return np.exp(np.minimum(0.0, (bi - bj) * (Ei - Ej)))
+
+    p0 = p_swap(b64[0], b64[1], E[:, 0], E[:, 1])
+    holder = np.where(s0, 0, 1)            # replica at index 1 once pair (0, 1) is decided
+    p1 = p_swap(b64[1], b64[2], E[np.arange(L), holder], E[:, 2])
+    p1_wrong = p_swap(b64[1], b64[2], E[:, 1], E[:, 2])
+
+    def z(obs, p):
+        return (obs.sum() - p.sum()) / math.sqrt((p * (1 - p)).sum())
+
+    assert abs(z(s0, p0)) < 4.0
+    assert abs(z(s1, p1)) < 4.0
+    # joint frequencies of (s0, s1) in the four cells against their closed form
+    p1_given = {True: p_swap(b64[1], b64[2], E[:, 0], E[:, 2]), False: p_swap(b64[1], b64[2], E[:, 1], E[:, 2])}
+    for a in (False, True):
+        for c in (False, True):
+            pa = p0 if a else 1 - p0
+            pc = p1_given[a] if c else 1 - p1_given[a]
+            cell = (s0 == a) & (s1 == c)
+            expect = pa * pc
+            assert abs(cell.sum() - expect.sum()) < 4.0 * math.sqrt((expect * (1 - expect)).sum()), (a, c)
+    # the data has the power to reject the pre-swap labels for pair (1, 2)
+    assert abs(z(s1[s0], p1_wrong[s0])) > 6.0
+    # final temperature labels follow the two decisions in order
+    tof = np.tile(np.arange(3), (L, 1))
+    at = np.tile(np.arange(3), (L, 1))
+    for p, s in ((0, s0), (1, s1)):
+        a_, c_ = at[s, p].copy(), at[s, p + 1].copy()
+        at[s, p], at[s, p + 1] = c_, a_
+        rows = np.nonzero(s)[0]
+        tof[rows, a_] = p + 1
+        tof[rows, c_] = p
+    assert np.array_equal(pt["temp_of"], tof)
+    assert np.array_equal(pt["swaps"][:, 0], s0.astype(np.int64))
+    assert np.array_equal(pt["swaps"][:, 1], s1.astype(np.int64))

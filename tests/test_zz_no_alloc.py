@@ -67,6 +67,8 @@ def test_static_anneal_rejects_oversize():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_1806_08815_gb300 import binding as da
     N = 1024
     ldw = da.da_static_pitch(N)
@@ -77,3 +79,38 @@ def test_static_anneal_rejects_oversize():
         da.da_anneal_static(W, d, N, ldw, beta, 10, 0.0, 1 << 16, 0, {}, 0)
     with pytest.raises(da.DAError):
         da.da_anneal_static(W, d, 2000, ldw, beta, 10, 0.0, 4, 0, {}, 0)
+
+
+def test_static_anneal_rejects_misaligned_pointers():
+    """A W that is not 16-byte aligned (e.g. a slice of a caller's buffer), a
+    misaligned diagonal or result array, and a pitch beyond int range are
+    refused on the host, before anything reaches the device."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1806_08815_gb300 import binding as da
+    N = 64
+    ldw = da.da_static_pitch(N)
+    buf = torch.zeros(N * ldw + 64, dtype=torch.int8, device="cuda")
+    d = torch.zeros(N + 4, dtype=torch.int32, device="cuda")
+    beta = torch.zeros(10, dtype=torch.float32, device="cuda")
+    for off in (1, 4, 8):
+        W = buf[off:off + N * ldw]
+        with pytest.raises(da.DAError, match="16-byte aligned"):
+            da.da_anneal_static(W, d, N, ldw, beta, 10, 0.0, 4, 0, {}, 0)
+    W = buf[:N * ldw]
+    dbytes = d.view(torch.int8)
+    with pytest.raises(da.DAError, match="4-byte aligned"):
+        da.da_anneal_static(W, dbytes[2:2 + 4 * N], N, ldw, beta, 10, 0.0, 4, 0, {}, 0)
+    E = torch.zeros(8 * 4 + 8, dtype=torch.int8, device="cuda")
+    with pytest.raises(da.DAError, match="aligned to their element size"):
+        da.da_anneal_static(W, d, N, ldw, beta, 10, 0.0, 4, 0, {"final_E": E[4:]}, 0)
+    with pytest.raises(da.DAError, match="INT_MAX"):
+        da.da_anneal_static(W, d, N, 1 << 31, beta, 10, 0.0, 4, 0, {}, 0)
+    # the aligned call still runs
+    torch.cuda.synchronize()
+    out = {"flips": torch.zeros(4, dtype=torch.int64, device="cuda")}
+    da.da_anneal_static(W, d, N, ldw, beta, 10, 0.0, 4, 0, out, 0)
+    torch.cuda.synchronize()
