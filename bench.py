@@ -37,13 +37,12 @@ UNIT = "trials/s"
 C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1, beta1=10.0, inc=0.0,
           instance_seed=0, seed=0)
 
-# DRAM bytes per step-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
-# capture summarised in profiles/, valid while the kernel source has the recorded hash.
+# DRAM bytes per step-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the headline workload, valid while the kernel source has the recorded hash.
 # Warp instructions per replica-step of the step kernel (smsp__inst_executed.sum / (R x steps))
 # from the same capture: the issue-slot roofline of a kernel bound by instruction issue.
 STEP_INST_PER_REPLICA_STEP = 812.2
-STEP_TRAFFIC = {"source_sha256_16": "f587d5979380dd0d", "bytes_per_launch": 8.601344e6,
-                "profile": "profiles/step_kernel_f32_v32_g1_sk_gaussian_n1024_r1024.md"}
+STEP_TRAFFIC = {"source_sha256_16": "f587d5979380dd0d", "bytes_per_launch": 8.601344e6}
 
 
 def step_source_sha():
@@ -386,6 +385,24 @@ def max_over_ranks(t: float, dist, device) -> float:
     return float(tt.item())
 
 
+def _free_port() -> int:
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def spawn_ranks(n: int) -> int:
+    """--gpus N without a launcher: start N ranks of this script (one process per GPU) with
+    torch.distributed.run on this node, and return their exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -423,9 +440,14 @@ def main():
                     help="run the served workload once, print its figures and exit (for ncu launch lists)")
     args = ap.parse_args()
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus and rank == 0:
+        print(f"bench.py: --gpus {args.gpus} but the launcher started {world} ranks; timing {world}",
+              file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 

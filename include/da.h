@@ -413,6 +413,15 @@ int64_t da_static_pitch(int64_t N);
 da_status da_diag_fail_alloc(int32_t after, int32_t count);
 da_status da_diag_live_allocations(int64_t* count, int64_t* bytes, int64_t* injected_failures);
 
+/* Read bandwidth of the device buffer buf[bytes] (device, 16-byte aligned,
+ * bytes a multiple of 16): one untimed pass, then `passes` timed passes of
+ * 16-byte loads that bypass L1; *seconds = device time of the timed passes.
+ * bytes * passes / *seconds is the L2 read bandwidth for a buffer that fits
+ * L2 (the step kernel reads its rows of W from there) and the HBM read
+ * bandwidth for a larger one; the roofline of the step kernel is stated
+ * against it.  Errors: DA_EINVAL, DA_ECUDA. */
+da_status da_diag_read_bandwidth(const void* buf, int64_t bytes, int32_t passes, double* seconds);
+
 /* Diagnostics: run the device's own fp32 exponential (used for every
  * Metropolis decision) on n host values x[n] -> y[n], and its Philox4x32-10
  * (Salmon et al., SC'11) on n host records ctr_key[6n] = (c0, c1, c2, c3, k0,

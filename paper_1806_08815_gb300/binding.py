@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.da_poll.argtypes = [_P, i32, ctypes.POINTER(da_result)]
     L.da_req_free.argtypes = [_P]
     L.da_req_free.restype = None
+    L.da_diag_read_bandwidth.argtypes = [_P, i64, i32, ctypes.POINTER(ctypes.c_double)]
+    L.da_diag_read_bandwidth.restype = ctypes.c_int
     L.da_cancel.argtypes = [_P]
     L.da_cancel.restype = ctypes.c_int
     L.da_diag_fail_alloc.argtypes = [i32, i32]
@@ -522,3 +524,11 @@ def da_diag_live_allocations() -> dict:
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(lib().da_diag_live_allocations(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return dict(count=a.value, bytes=b.value, injected=c.value)
+
+
+def da_diag_read_bandwidth(buf_dev, passes: int) -> float:
+    """Read bandwidth in bytes/s of a device tensor (L2 for one that fits L2, else HBM)."""
+    sec = ctypes.c_double()
+    nbytes = int(buf_dev.numel() * buf_dev.element_size())
+    _check(lib().da_diag_read_bandwidth(_ptr(buf_dev), nbytes, int(passes), ctypes.byref(sec)))
+    return nbytes * int(passes) / sec.value

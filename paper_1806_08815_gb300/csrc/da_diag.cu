@@ -86,6 +86,42 @@ __global__ void scaled_kernel(const long long* v, const int32_t* S, float* got, 
     ref[i] = ldexpf(__ll2float_rn(v[i]), -S[i]);
 }
 
+// Read bandwidth of a device buffer: a grid-stride loop of 16-byte loads that
+// bypass L1 (ld.global.cg), four independent loads in flight per thread, the
+// whole buffer `passes` times.  A buffer that fits L2 is served from L2 after
+// the first pass, so the kernel measures the L2 read bandwidth the step
+// kernel's rows come from; a larger one measures HBM.  The xor of the words
+// is stored only when it equals an arbitrary constant (so that no load can be
+// dropped).
+__device__ __forceinline__ uint4 ld_cg(const uint4* p)
+{
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__global__ void read_bw_kernel(const uint4* __restrict__ p, long long n16, int passes, unsigned* sink)
+{
+    uint32_t acc = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (int k = 0; k < passes; ++k) {
+        long long i = t0;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            const uint4 a = ld_cg(p + i), b = ld_cg(p + i + stride), c = ld_cg(p + i + 2 * stride),
+                        d = ld_cg(p + i + 3 * stride);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+        }
+        for (; i < n16; i += stride) {
+            const uint4 a = ld_cg(p + i);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w;
+        }
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;
+}
+
 thread_local std::string g_diag_err;
 
 template <typename Fn>
@@ -199,4 +235,50 @@ extern "C" da_status da_diag_bounded_wait(int64_t ns, int64_t* out3)
     return run(sizeof(zero), 3 * sizeof(unsigned long long), &zero, out3, [&](void*, void* b) {
         wait_probe_kernel<<<1, 32>>>((unsigned long long)ns, static_cast<unsigned long long*>(b));
     });
+}
+
+extern "C" da_status da_diag_read_bandwidth(const void* buf, int64_t bytes, int32_t passes, double* seconds)
+{
+    if (!buf || !seconds || bytes < 16 || bytes % 16 != 0 || passes < 1 ||
+        reinterpret_cast<uintptr_t>(buf) % 16 != 0)
+        return DA_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DA_ECUDA;
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    unsigned* sink = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(unsigned));
+    const long long n16 = bytes / 16;
+    const unsigned blocks = (unsigned)sms * 8u;
+    const uint4* p = static_cast<const uint4*>(buf);
+    if (e == cudaSuccess) {
+        read_bw_kernel<<<blocks, 256, 0, st>>>(p, n16, 1, sink);   // brings an L2-sized buffer into L2
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+        read_bw_kernel<<<blocks, 256, 0, st>>>(p, n16, passes, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DA_ECUDA;
+    }
+    *seconds = ms * 1e-3;
+    return DA_OK;
 }

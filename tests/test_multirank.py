@@ -47,3 +47,22 @@ def test_two_gloo_ranks_replicas_only():
     assert len(seeds) == world
     assert all(res[r][1] == 1.5 for r in range(world))       # max over ranks of 0.5 and 1.5
     assert res[0][2] != res[1][2]                              # independent replica sets
+
+
+def test_bench_spawns_its_ranks_for_gpus_n():
+    """`bench.py --gpus 2` without a launcher starts two ranks itself (torch.distributed.run);
+    with the reference arm, rank 0 alone runs and prints one line that names 2 GPUs."""
+    import json
+    import subprocess
+    import sys
+    import oracle
+    oracle.build()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
