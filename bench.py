@@ -53,15 +53,35 @@ def step_source_sha():
     return h.hexdigest()[:16]
 
 
-def issue_roofline(replica_steps_per_launch, launch_s):
-    """Issue-slot roofline of the step kernel: warp instructions per launch (from the ncu count per
-    replica-step) over the launch time, against 4 issue slots per SM per cycle x 152 SMs x 2.07 GHz."""
-    if step_source_sha() != STEP_TRAFFIC["source_sha256_16"]:
-        return None
+def issue_roofline(replica_steps_per_launch, launch_s, sms, sm_ghz):
+    """Issue-slot roofline of the step kernel (the resource that binds it: a chain of dependent
+    instructions per step, no contraction, a few KB of row reads per replica-step from L2): warp
+    instructions per launch (the ncu count per replica-step of this kernel source) over the launch
+    time, against 4 warp-instructions per cycle per SM (one per scheduler) x SMs x the SM clock."""
     achieved = STEP_INST_PER_REPLICA_STEP * replica_steps_per_launch / launch_s / 1e9
-    peak = 152 * 4 * 2.07
-    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s", "frac": achieved / peak,
+    peak = sms * 4 * sm_ghz
+    fresh = step_source_sha() == STEP_TRAFFIC["source_sha256_16"]
+    if not fresh:
+        print("bench.py: the step kernel changed since its instruction count was taken; the issue "
+              "roofline uses the old count", file=sys.stderr)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s", "frac": achieved / peak,
+            "traffic": STEP_TRAFFIC["bytes_per_launch"] if fresh else None,
+            "inst_per_replica_step": STEP_INST_PER_REPLICA_STEP, "count_matches_source": fresh,
+            "peak_source": f"4 warp-instructions / cycle / SM x {sms} SMs x {sm_ghz:.3f} GHz (median SM clock "
+                           "sampled during the timed region)",
             "basis": "ncu smsp__inst_executed.sum per replica-step x replica-steps per launch / launch time"}
+
+
+def read_bandwidths(da, dev):
+    """L2 read bandwidth measured on this GPU with the library's read kernel: a buffer of the size of
+    the headline W (4 MB, the rows the step kernel reads) and one spread over every L2 slice (64 MB)."""
+    import torch
+    out = {}
+    for key, mb in (("w_sized_4mb", 4), ("l2_64mb", 64)):
+        buf = torch.zeros(mb << 20, dtype=torch.uint8, device=dev)
+        out[key] = max(da.da_diag_read_bandwidth(buf, max(1, 4096 // mb)) for _ in range(3)) / 1e9
+        del buf
+    return out
 
 
 def recompute_roofline(peaks, peak_src, N, R, n_recompute, rest_s):
@@ -175,10 +195,23 @@ def _tts_from_best(best_E, tau_run):
     return tts99(np.asarray(best_E), tau_run)
 
 
-def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_T=400):
+def _hits_tts(best, E_ref, tau_run):
+    """TTS99 of one form on one instance against a given reference energy (Jeffreys posterior)."""
+    tol = 1e-6 * max(1.0, abs(E_ref))
+    y = int(np.sum(np.asarray(best) <= E_ref + tol))
+    r = len(best)
+    theta = (y + 0.5) / (r + 1.0)
+    R99 = max(1.0, math.log(1 - 0.99) / math.log(1 - theta)) if theta < 1 else 1.0
+    return dict(hits=y, runs=r, theta=theta, tts99_s=tau_run * R99)
+
+
+def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
     """Batched launch: n_inst fully connected instances, N uniform in {64..1024}, half bimodal (int8),
     half Gaussian (fp32, exact recompute every 1024 steps), R replicas each, one persistent CUDA-graph
-    launch; compared with the plain one-launch-per-step form run instance after instance."""
+    launch.  Compared with the plain one-launch-per-step form run by itself, instance after instance,
+    on a sample of the same instances (plain_per_class per coupling type and size) for the full T
+    steps with the same schedules and seeds: trials/s of both, and TTS99 of both at the hit rate each
+    measures against the instance's best energy over the runs of both forms."""
     rng = np.random.default_rng(1234)
     sizes = rng.choice([64, 128, 256, 512, 1024], n_inst)
     jobs, meta = [], []
@@ -192,26 +225,41 @@ def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_T=400):
     da.da_batch_anneal(jobs[:8])                      # warm-up (and autotuning of the classes it touches)
     outs, el = da.da_batch_anneal(jobs)
     trials = sum(R * T * N for _, N in meta)
-    # plain form: per-step time of each (coupling, size) class from a short run, one instance at a time
-    per_step = {}
-    for (bim, N) in sorted(set(meta)):
-        i = meta.index((bim, N))
-        da.da_anneal_plain(jobs[i]["ctx"], jobs[i]["beta"][:16], jobs[i]["offset_inc"], R, 0)
-        r = da.da_anneal_plain(jobs[i]["ctx"], jobs[i]["beta"][:plain_T], jobs[i]["offset_inc"], R, 0)
-        per_step[(bim, N)] = r["elapsed_s"] / plain_T
-    plain_time = sum(T * per_step[m] for m in meta)
     tau_b = el / (n_inst * R)
-    tts_b = [_tts_from_best(o["best_E"], tau_b)["tts99_s"] for o in outs]
-    tts_p = [_tts_from_best(o["best_E"], T * per_step[m] / R)["tts99_s"] for o, m in zip(outs, meta)]
+    # the plain form itself on a sample of the instances, full length
+    sample = []
+    for cls in sorted(set(meta)):
+        sample += [i for i, m in enumerate(meta) if m == cls][:plain_per_class]
+    j0 = jobs[sample[0]]
+    da.da_anneal_plain(j0["ctx"], j0["beta"][:64], j0["offset_inc"], R, 0)   # warm-up
+    p_time, p_trials, b_trials, rows = 0.0, 0, 0, []
+    for i in sample:
+        j = jobs[i]
+        rp = da.da_anneal_plain(j["ctx"], j["beta"], j["offset_inc"], R, j["seed"])
+        p_time += rp["elapsed_s"]
+        p_trials += R * T * meta[i][1]
+        b_trials += R * T * meta[i][1]
+        E_ref = float(min(outs[i]["best_E"].min(), rp["best_E"].min()))
+        tb = _hits_tts(outs[i]["best_E"], E_ref, tau_b)
+        tp = _hits_tts(rp["best_E"], E_ref, rp["elapsed_s"] / R)
+        rows.append((meta[i], tb, tp))
+    plain_value = p_trials / p_time
+    tts_b = [r[1]["tts99_s"] for r in rows]
+    tts_p = [r[2]["tts99_s"] for r in rows]
     return {"workload": f"{n_inst} SK instances, N in {{64,128,256,512,1024}}, half bimodal int8 / half "
                         f"Gaussian fp32, {R} replicas, {T} steps, one persistent CUDA-graph launch",
             "value": trials / el, "unit": UNIT, "seconds": el,
-            "plain_gpu": {"value": trials / plain_time, "unit": UNIT,
-                          "basis": f"per-step time of each class from {plain_T}-step plain runs, "
-                                   "instances one after another"},
-            "speedup_vs_plain": plain_time / el,
+            "plain_gpu": {"value": plain_value, "unit": UNIT, "instances": len(sample),
+                          "basis": f"the plain form run by itself on {len(sample)} of the instances "
+                                   f"({plain_per_class} per coupling type and size), full {T} steps, same seeds"},
+            "speedup_vs_plain": (trials / el) / plain_value,
             "tts99_median_s": float(np.median(tts_b)), "tts99_median_plain_s": float(np.median(tts_p)),
-            "tts99_basis": "per instance: reference = best energy over its runs, same hit rate for both forms"}
+            "tts99_speedup_median": float(np.median(np.array(tts_p) / np.array(tts_b))),
+            "hit_fraction_mean": {"batched": float(np.mean([r[1]["hits"] / r[1]["runs"] for r in rows])),
+                                  "plain": float(np.mean([r[2]["hits"] / r[2]["runs"] for r in rows]))},
+            "tts99_basis": "sampled instances; reference = best energy over the runs of both forms; "
+                           "theta per form from its own hits (Jeffreys); tau = batched graph time / all runs, "
+                           "plain time / R"}
 
 
 def run_ptda(da, instances, L=32, K=32, sweeps=100):
@@ -302,22 +350,12 @@ def run_fixed_point(da, instances, R=1024, T=200_000):
             "relative_gap_of_means": float((Ei.mean() - Ef.mean()) / abs(Ef.mean()))}
 
 
-def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30):
-    """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
-    [256, 8192], half bimodal / half Gaussian, R replicas, T steps, HBM budget 120 GB."""
-    import threading
-    rng = np.random.default_rng(99)
-    pool = []
-    for i in range(24):
-        N = int(round(np.exp(rng.uniform(np.log(256), np.log(8192)))))
-        bim = i % 2 == 0
-        pool.append(instances.sk_bimodal(N, 3000 + i) if bim else instances.sk_gaussian(N, 3000 + i))
-    betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
-    picks = rng.integers(0, len(pool), n_req)
-    gaps = rng.exponential(1.0 / rate, n_req)
+def _serve_stream(da, pool, betas, picks, gaps, R, T, budget):
+    """Submit requests pool[picks[k]] at the inter-arrival gaps, wait for all; per-request results."""
     srv = da.Server(budget, 1024)
     warm = da.da_submit(srv, pool[0].Q, betas[pool[0].bimodal][:100], 0.0, 4, 0)
     da.da_poll(warm, 60_000_000)
+    n_req = len(picks)
     reqs = [None] * n_req
     t0 = time.perf_counter()
 
@@ -335,21 +373,81 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
     th = threading.Thread(target=feed)
     th.start()
     th.join()
-    lat = []
-    for k in range(n_req):
-        o = da.da_poll(reqs[k], 600_000_000)
-        lat.append(o["latency_s"])
+    res = [da.da_poll(reqs[k], 600_000_000) for k in range(n_req)]
     t1 = time.perf_counter()
     stats = srv.stats()
     srv.close()
+    return res, t1 - t0, stats
+
+
+def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30, sustained_req=512,
+               sustained_rate=40.0, plain_max=6):
+    """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
+    [256, 8192], half bimodal / half Gaussian, R replicas, T steps, HBM budget 120 GB.  Beside the
+    burst at `rate`, a longer stream at a rate the GPU sustains, and the plain one-launch-per-step
+    form on the requests it can take (N <= 1024), run one after another with the same seeds:
+    trials/s and per-request TTS99 of both forms against the best energy of both."""
+    rng = np.random.default_rng(99)
+    pool = []
+    for i in range(24):
+        N = int(round(np.exp(rng.uniform(np.log(256), np.log(8192)))))
+        bim = i % 2 == 0
+        pool.append(instances.sk_bimodal(N, 3000 + i) if bim else instances.sk_gaussian(N, 3000 + i))
+    betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
+    picks = rng.integers(0, len(pool), n_req)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    res, makespan, stats = _serve_stream(da, pool, betas, picks, gaps, R, T, budget)
     trials = sum(R * T * pool[i].N for i in picks)
-    lat = np.array(lat)
-    return {"workload": f"{n_req} requests, Poisson {rate:.0f} req/s, N log-uniform 256-8192 (pool of 24 "
-                        f"instances), half bimodal / half Gaussian, {R} replicas, {T} steps, HBM budget "
-                        f"{budget >> 30} GB",
-            "value": trials / (t1 - t0), "unit": UNIT, "makespan_s": t1 - t0,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"]}
+    lat = np.array([o["latency_s"] for o in res])
+    out = {"workload": f"{n_req} requests, Poisson {rate:.0f} req/s, N log-uniform 256-8192 (pool of 24 "
+                       f"instances), half bimodal / half Gaussian, {R} replicas, {T} steps, HBM budget "
+                       f"{budget >> 30} GB",
+           "value": trials / makespan, "unit": UNIT, "makespan_s": makespan,
+           "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+           "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"]}
+    # a longer stream at a rate the GPU sustains (the burst above is beyond one GPU's throughput, so
+    # its latencies are mostly queueing)
+    picks2 = rng.integers(0, len(pool), sustained_req)
+    gaps2 = rng.exponential(1.0 / sustained_rate, sustained_req)
+    res2, makespan2, _ = _serve_stream(da, pool, betas, picks2, gaps2, R, T, budget)
+    lat2 = np.array([o["latency_s"] for o in res2])
+    out["sustained"] = {"requests": sustained_req, "rate_req_s": sustained_rate,
+                        "value": sum(R * T * pool[i].N for i in picks2) / makespan2, "unit": UNIT,
+                        "makespan_s": makespan2, "p50_latency_s": float(np.percentile(lat2, 50)),
+                        "p99_latency_s": float(np.percentile(lat2, 99))}
+    # the plain form on requests of the sustained stream with at most 1024 variables (its limit), one
+    # after another, same instance, schedule and seed as the request
+    small, seen = [], set()
+    for k, i in enumerate(picks2):
+        if pool[i].N <= 1024 and i not in seen:
+            small.append((k, i))
+            seen.add(i)
+    small = small[:plain_max]
+    if small:
+        q0 = pool[small[0][1]]
+        c0 = da.da_create(q0.Q)
+        da.da_anneal_plain(c0, betas[q0.bimodal][:64], 0.0, R, 0)      # warm-up
+        da.da_destroy(c0)
+        p_time, p_trials, tts_s, tts_p = 0.0, 0, [], []
+        for k, i in small:
+            q = pool[i]
+            ctx = da.da_create(q.Q)
+            rp = da.da_anneal_plain(ctx, betas[q.bimodal], 1.0 if q.bimodal else 0.0, R, k)
+            da.da_destroy(ctx)
+            p_time += rp["elapsed_s"]
+            p_trials += R * T * q.N
+            E_ref = float(min(res2[k]["best_E"].min(), rp["best_E"].min()))
+            tts_s.append(_hits_tts(res2[k]["best_E"], E_ref, lat2[k] / R)["tts99_s"])
+            tts_p.append(_hits_tts(rp["best_E"], E_ref, rp["elapsed_s"] / R)["tts99_s"])
+        out["plain_gpu"] = {"value": p_trials / p_time, "unit": UNIT, "requests": len(small),
+                            "basis": f"the plain form on {len(small)} requests of the sustained stream with "
+                                     "N <= 1024, one after another, same instances, schedules and seeds"}
+        out["tts99_median_s"] = float(np.median(tts_s))
+        out["tts99_median_plain_s"] = float(np.median(tts_p))
+        out["tts99_basis"] = ("requests of the sustained stream; reference = best energy over the runs of both "
+                              "forms; tau = request latency / R (served, submit to result, including queueing) "
+                              "and device time / R (plain, run alone)")
+    return out
 
 
 def cpu_baseline(sample_R=None, sample_T=32768):
@@ -547,14 +645,34 @@ def main():
                  "sample": f"first {Tp} steps of the schedule, {R} replicas, one launch per step",
                  "speedup_of_value": value / (world * R * Tp * N / rp["elapsed_s"])}
 
-    # roofline of the step kernel: nominal bytes per replica-step = one fp32 column of W
-    # (4N) plus the replica state (fields 4N + state bits N/8)
+    # rooflines of the step kernel: the issue slots it is bound by, and its bytes.  Algorithmic
+    # bytes per replica-step: one fp32 row of W (4N) for every applied flip; the nominal figure
+    # adds the replica state (fields 4N + state bits N/8) that stays in registers
     peaks, peak_src = load_peaks()
     hbm = hbm_peak(peaks)
+    bw = read_bandwidths(da, dev)
     per_launch_steps = min(P, T)
-    bytes_per_launch = R * per_launch_steps * (4 * N + 4 * N + N // 8)
+    replica_steps = R * per_launch_steps
     avg_launch_s = (step_ms / 1e3) / max(launches, 1)
-    achieved_gbs = bytes_per_launch / avg_launch_s / 1e9
+    flip_frac = float(out["flips"].sum().item()) / (R * T)
+    algo_bytes = replica_steps * flip_frac * 4 * N
+    nominal_bytes = replica_steps * (4 * N + 4 * N + N // 8)
+    algo_gbs = algo_bytes / avg_launch_s / 1e9
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_ghz = (clk["sm_mhz"] if clk and clk.get("sm_mhz") else 2070.0) / 1e3
+    roofline = issue_roofline(replica_steps, avg_launch_s, sms, sm_ghz)
+    roofline["kernel"] = "step_kernel_g1<float,V=32>"
+    roofline["memory"] = {
+        "algorithmic_bytes_per_launch": algo_bytes, "flips_per_replica_step": flip_frac,
+        "achieved_gbs": algo_gbs,
+        "l2_w_sized_gbs": bw["w_sized_4mb"], "frac_l2_w_sized": algo_gbs / bw["w_sized_4mb"],
+        "l2_peak_gbs": bw["l2_64mb"], "frac_l2_peak": algo_gbs / bw["l2_64mb"],
+        "hbm_gbs": hbm, "frac_hbm": algo_gbs / hbm, "hbm_source": peak_src,
+        "nominal_bytes_per_launch": nominal_bytes, "nominal_gbs": nominal_bytes / avg_launch_s / 1e9,
+        "nominal_frac_hbm": nominal_bytes / avg_launch_s / 1e9 / hbm,
+        "basis": "algorithmic: one 4N-byte row of W per applied flip (replica state stays in registers); "
+                 "nominal: row + fields + state bits every replica-step; L2 bandwidths measured here with "
+                 "16-byte L1-bypassing reads (da_diag_read_bandwidth), HBM from the measured copy peak"}
     n_step_launches = math.ceil(T / P)
     n_recompute = T // P
     # init, step launches, 3 per recompute (state expansion, tensor-core recompute, energy sum), the same 3
@@ -572,13 +690,7 @@ def main():
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(q.Q.nbytes + beta.nbytes),
                 "d2h_bytes_per_step": int(res_bytes)},
         "gpu_launches": gpu_launches * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm,
-                     "traffic": STEP_TRAFFIC["bytes_per_launch"]
-                     if step_source_sha() == STEP_TRAFFIC["source_sha256_16"] else None,
-                     "kernel": "step_kernel_g1<float,V=32>", "peak_source": peak_src,
-                     "basis": "nominal bytes per replica-step: fp32 column of W + fields + state bits"},
-        "roofline_issue": issue_roofline(R * per_launch_steps, avg_launch_s),
+        "roofline": roofline,
         "step_kernel": {"launches": launches, "avg_launch_ms": avg_launch_s * 1e3,
                         "share_of_step": (step_ms / 1e3) / (t_step * args.steps)},
         "roofline_recompute": recompute_roofline(peaks, peak_src, N, R, n_recompute,
