@@ -222,8 +222,9 @@ def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
         jobs.append(dict(ctx=da.da_create(q.Q), beta=beta, offset_inc=1.0 if bim else 0.0, replicas=R, seed=i,
                          recompute_every=0 if bim else 1024))
         meta.append((bim, int(N)))
-    da.da_batch_anneal(jobs[:8])                      # warm-up (and autotuning of the classes it touches)
-    outs, el = da.da_batch_anneal(jobs)
+    da.da_batch_anneal(jobs[:8])                      # warm-up
+    outs, el = da.da_batch_anneal(jobs)               # (the tuner probes each class before the graph runs)
+    config = da.da_batch_describe()
     trials = sum(R * T * N for _, N in meta)
     tau_b = el / (n_inst * R)
     # the plain form itself on a sample of the instances, full length
@@ -248,7 +249,7 @@ def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
     tts_p = [r[2]["tts99_s"] for r in rows]
     return {"workload": f"{n_inst} SK instances, N in {{64,128,256,512,1024}}, half bimodal int8 / half "
                         f"Gaussian fp32, {R} replicas, {T} steps, one persistent CUDA-graph launch",
-            "value": trials / el, "unit": UNIT, "seconds": el,
+            "value": trials / el, "unit": UNIT, "seconds": el, "configuration": config,
             "plain_gpu": {"value": plain_value, "unit": UNIT, "instances": len(sample),
                           "basis": f"the plain form run by itself on {len(sample)} of the instances "
                                    f"({plain_per_class} per coupling type and size), full {T} steps, same seeds"},
@@ -569,6 +570,7 @@ def main():
     beta = instances.beta_linear(C3["beta0"], C3["beta1"], T)
     seed = rank_seed(rank)              # weak scaling: each rank anneals its own 1024 replicas
     ctx = da.da_create(q.Q)
+    shape = da.da_tune_shape(ctx, R)    # the autotuner's launch shape for this instance class
     beta_dev = torch.from_numpy(beta).to(dev)
     Wd = da.da_words(N)
     out = dict(final_E=torch.zeros(R, dtype=torch.float64, device=dev),
@@ -685,7 +687,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "sk_gaussian_N1024_R1024_T2e5", "N": N, "replicas": R, "steps_per_anneal": T,
                    "recompute_every": P, "beta": f"linear {C3['beta0']} -> {C3['beta1']}",
-                   "offset_inc": C3["inc"], "parallelism": f"replicas x{world}",
+                   "offset_inc": C3["inc"], "parallelism": f"replicas x{world}", "launch_shape": shape,
                    "l2": "flushed (256 MB write) before every timed step"},
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(q.Q.nbytes + beta.nbytes),
                 "d2h_bytes_per_step": int(res_bytes)},

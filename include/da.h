@@ -162,6 +162,19 @@ da_status da_ctx_info(const da_ctx* ctx, int64_t* N, da_dtype* dtype);
  * step and replica).  Errors: DA_EINVAL. */
 da_status da_set_launch_shape(da_ctx* ctx, int32_t V, int32_t G, int32_t rpb);
 
+/* Autotune the step kernel's launch shape for this context's instance and R
+ * replicas: every supported shape that covers N (for each G in 1, 2, 4, 8 the
+ * narrowest lane width V, every allowed rpb, and for G = 1 the producer-warp
+ * form) runs probe_steps steps from x = 0 with beta = 0 (every step flips), the
+ * fastest (CUDA events, best of two runs) is written to *V, *G, *rpb,
+ * *draw_warp (each may be NULL) and kept in a process-wide cache keyed by
+ * (device, coupling type, N, R) that every context's later anneals use unless
+ * a shape was fixed with da_set_launch_shape.  Results of an anneal do not
+ * depend on the shape.  Blocking; uses the context's workspace.  Errors:
+ * DA_EINVAL, DA_ENOMEM, DA_ECUDA. */
+da_status da_tune_shape(da_ctx* ctx, int32_t replicas, int64_t probe_steps, int32_t* V, int32_t* G, int32_t* rpb,
+                        int32_t* draw_warp);
+
 /* For shapes with G = 1 (the automatic choice up to N = 1024): on = 1 runs
  * each replica as an annealer warp plus a producer warp that computes the
  * acceptance draws of the coming steps (Philox words as log2 u) into shared
@@ -229,11 +242,28 @@ typedef struct da_batch_item {
  * (coupling type, size class) pull units from a device queue until none are left;
  * all launches and the exact final evaluation form one CUDA graph.  Each item's
  * results are identical to da_anneal on that item alone (the random numbers are
- * keyed by the item's seed and replica index).  The block shape of each class's
- * kernel is chosen by an autotuner that times short probes of the class's own
- * units once per process and device.  *elapsed_s receives the device time of the
- * graph.  Errors: DA_EINVAL (bad item, N > 1024), DA_ENOMEM, DA_ECUDA. */
+ * keyed by the item's seed and replica index).  Each class's configuration is
+ * chosen by an autotuner that times short probes (256 steps) of the class's own
+ * units once per process, device and class: warps per block (1, 2, 4), and,
+ * where the class's largest instance fits (N x 32V x 4 bytes <= 227 KB, V <= 8),
+ * W staged in shared memory, where each block takes a group of replicas of one
+ * instance (2, 4, 8 or 16, one per warp), copies that instance's W once and
+ * reads every row from there instead of from L2.  *elapsed_s receives the
+ * device time of the graph.  Errors: DA_EINVAL (bad item, N > 1024), DA_ENOMEM,
+ * DA_ECUDA. */
 da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s);
+
+/* The configuration the last da_batch_anneal on the calling thread used for
+ * each class, with the tuner's probe times, as text (at most len - 1 bytes and
+ * a terminating 0 written to buf).  Errors: DA_EINVAL. */
+da_status da_batch_describe(char* buf, int64_t len);
+
+/* Override the tuner of da_batch_anneal for the calls that follow, process
+ * wide (for tests and measurements): staging -1 = the tuner's choice, 0 = rows
+ * of W from L2, 1 = W staged in shared memory where the class allows it (else
+ * L2); warps_per_block 0 = the tuner's choice, else 1, 2 or 4 (2, 4, 8 or 16
+ * when staged).  da_batch_force(-1, 0) restores the tuner.  Errors: DA_EINVAL. */
+da_status da_batch_force(int32_t staging, int32_t warps_per_block);
 
 /* ---- Request loop (continuous batching) ------------------------------------
  * A server runs each admitted request on a CUDA stream of its own: requests that

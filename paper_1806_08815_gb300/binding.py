@@ -114,6 +114,12 @@ def lib() -> ctypes.CDLL:
         getattr(L, name).restype = ctypes.c_int
     L.da_batch_anneal.argtypes = [ctypes.POINTER(da_batch_item), i32, ctypes.POINTER(ctypes.c_double)]
     L.da_batch_anneal.restype = ctypes.c_int
+    L.da_tune_shape.argtypes = [_P, i32, i64] + [ctypes.POINTER(i32)] * 4
+    L.da_tune_shape.restype = ctypes.c_int
+    L.da_batch_describe.argtypes = [ctypes.c_char_p, i64]
+    L.da_batch_describe.restype = ctypes.c_int
+    L.da_batch_force.argtypes = [i32, i32]
+    L.da_batch_force.restype = ctypes.c_int
     L.da_anneal_plain.argtypes = [_P, _P, i64, f32, i32, u64, ctypes.POINTER(da_result)]
     L.da_anneal_plain.restype = ctypes.c_int
     L.da_anneal_static.argtypes = [_P, _P, i64, i64, _P, i64, f32, i32, u64, ctypes.POINTER(da_dev_result), _P]
@@ -440,6 +446,26 @@ def da_batch_anneal(jobs: list) -> tuple:
     el = ctypes.c_double()
     _check(lib().da_batch_anneal(arr, n, ctypes.byref(el)))
     return outs, el.value
+
+
+def da_tune_shape(ctx: Context, replicas: int, probe_steps: int = 256) -> dict:
+    """Time every launch shape for this instance and replica count; the fastest is used from now
+    on by every context of the process with the same coupling type, N and replica count."""
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib().da_tune_shape(ctx.handle, int(replicas), int(probe_steps), *(ctypes.byref(x) for x in v)))
+    return dict(V=v[0].value, G=v[1].value, rpb=v[2].value, draw_warp=v[3].value)
+
+
+def da_batch_describe() -> str:
+    """The configuration each class of the last da_batch_anneal on this thread used."""
+    buf = ctypes.create_string_buffer(8192)
+    _check(lib().da_batch_describe(buf, len(buf)))
+    return buf.value.decode()
+
+
+def da_batch_force(staging: int = -1, warps_per_block: int = 0) -> None:
+    """Override the batched launch's tuner (staging -1 auto / 0 L2 / 1 shared memory)."""
+    _check(lib().da_batch_force(int(staging), int(warps_per_block)))
 
 
 class Server:

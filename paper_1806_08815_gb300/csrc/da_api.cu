@@ -13,8 +13,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "da.h"
@@ -106,9 +108,24 @@ StepShape auto_shape(int N, int R)
     return s;
 }
 
+// Launch shapes chosen by da_tune_shape, per (device, step coupling form, N,
+// replicas), for every context of the process.
+std::mutex g_shape_mu;
+std::map<std::tuple<int, int, int, int>, StepShape> g_shape_cache;
+
 StepShape shape_for(const da_ctx* c, int R)
 {
-    StepShape s = c->forced.V > 0 ? c->forced : auto_shape(c->N, R);
+    if (c->forced.V > 0) {
+        StepShape s = c->forced;
+        s.ws = s.ws || (s.G == 1 && c->draw_warp);
+        return s;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        auto f = g_shape_cache.find(std::make_tuple(c->device, step_wtype(c), c->N, R));
+        if (f != g_shape_cache.end()) return f->second;
+    }
+    StepShape s = auto_shape(c->N, R);
     s.ws = s.G == 1 && c->draw_warp;
     return s;
 }
@@ -887,3 +904,81 @@ da_status da_field_recompute(da_ctx* c, const uint32_t* x, int32_t R, void* h)
 }
 
 }  // extern "C"
+
+extern "C" da_status da_tune_shape(da_ctx* c, int32_t R, int64_t probe_steps, int32_t* V, int32_t* G, int32_t* rpb,
+                                   int32_t* draw_warp)
+{
+    g_err.clear();
+    if (da_status e = check_ctx(c)) return e;
+    if (R < 1 || probe_steps < 1 || probe_steps > (1 << 20)) return fail(DA_EINVAL, "need R >= 1 and 1 <= probe_steps <= 2^20");
+    CtxLock lock(c);
+    // candidates: for each group size G the narrowest supported lane width that covers N, every
+    // replicas-per-block the shape allows, and for G = 1 the producer-warp form
+    std::vector<StepShape> cands;
+    for (int g = 1; g <= 8; g *= 2) {
+        StepShape s;
+        s.G = g;
+        for (int v = 4; v <= 32; v *= 2) {
+            s.V = v;
+            s.rpb = 1;
+            if (da::step_shape_supported(s) && s.npad() >= c->N) break;
+            s.V = 0;
+        }
+        if (s.V == 0) continue;
+        if (s.npad() >= 4 * c->N && s.npad() > 128) continue;   // mostly idle lanes
+        for (int r = 1; r <= 4; r *= 2) {
+            s.rpb = r;
+            if (!da::step_shape_supported(s)) continue;
+            cands.push_back(s);
+        }
+        if (g == 1) {
+            s.rpb = 1;
+            s.ws = true;
+            cands.push_back(s);
+        }
+    }
+    if (cands.empty()) return fail(DA_EINVAL, "no launch shape covers N");
+    const cudaStream_t st = c->stream;
+    // probe schedule beta = 0: every trial is accepted, so every step flips (the common case of an
+    // anneal over most of its schedule)
+    const std::vector<float> beta((size_t)probe_steps, 0.0f);
+    StepShape best = cands.front();
+    float best_ms = 1e30f;
+    for (const StepShape& s : cands) {
+        const Layout L = plan(c, s, R, probe_steps, true, false, 0);
+        if (da_status e = ensure_ws(c, L.total)) return e;
+        RunBuffers b{static_cast<char*>(c->ws), L, s, R};
+        DA_CU(cudaMemcpyAsync(b.base + L.beta, beta.data(), (size_t)probe_steps * 4, cudaMemcpyHostToDevice, st));
+        const float* beta_dev = reinterpret_cast<const float*>(b.base + L.beta);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run also loads and configures the kernel
+            if (da_status e = reset_state(c, b, st)) return e;
+            StepParams p = base_params(c, b);
+            p.beta = beta_dev;
+            da::set_seed(p, 0x5eed);
+            p.t0 = 0;
+            p.t1 = probe_steps;
+            DA_CU(cudaEventRecord(c->ev0, st));
+            DA_CU(da::launch_step(step_wtype(c), s, p, false, st));
+            DA_CU(cudaEventRecord(c->ev1, st));
+            DA_CU(cudaEventSynchronize(c->ev1));
+            float t = 0.f;
+            DA_CU(cudaEventElapsedTime(&t, c->ev0, c->ev1));
+            ms = std::min(ms, t);
+        }
+        if (da_status e = check_kernel_flag(c)) return e;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        g_shape_cache[std::make_tuple(c->device, step_wtype(c), c->N, (int)R)] = best;
+    }
+    if (V) *V = best.V;
+    if (G) *G = best.G;
+    if (rpb) *rpb = best.rpb;
+    if (draw_warp) *draw_warp = best.ws ? 1 : 0;
+    return DA_OK;
+}

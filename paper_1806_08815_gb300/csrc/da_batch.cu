@@ -7,9 +7,15 @@
 // GPU without a wave per instance.  fp32 units recompute their fields exactly
 // inside the warp every `recompute_every` steps.  Units are grouped by
 // (coupling type, V = variables per lane); each group is one persistent kernel
-// whose block shape is chosen by a small autotuner that times short probes of
-// the real work and caches the winner per device and class.
+// whose configuration is chosen by a small autotuner that times short probes
+// of the real work and caches the winner per device and class: warps per
+// block, and where the rows of W come from.  A class whose instances are small
+// enough can stage W in shared memory: each block then takes a group of
+// replicas of one instance (one per warp), copies that instance's W into
+// shared memory once, and runs the group's anneals reading rows from there
+// instead of from L2.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <chrono>
 #include <cmath>
@@ -48,18 +54,73 @@ struct BatchClassParams {
     long long total_units;
     unsigned long long* head;   // work counter
     long long t_limit;          // > 0: run only this many steps per unit (autotuner probes)
+    const int2* groups;         // shared-memory staging: (item, first replica) of each group
+    long long n_groups;
+    int pitch;                  // shared-memory staging: row pitch of the staged W (32 V entries)
 };
 
 namespace {
 
 using step_detail::WarpReplica;
 
+// One work unit: replica r of item it, all of its steps, by the calling warp;
+// W points at the item's couplings (global memory, row pitch ldw) or at a
+// copy staged in shared memory (SW, row pitch ldw = 32 V).
+template <typename Tw, int V, bool SW>
+__device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw* W, int ldw, long long t_limit)
+{
+    using R_ = WarpReplica<Tw, V, SW>;
+    using A = step_detail::Arith<Tw>;
+    using H = typename R_::H;
+    constexpr int nw = V;   // state words per replica (the padded width 32V / 32)
+    const int lane = threadIdx.x & 31;
+    R_ rp;
+    rp.init(W, it.N, ldw, (uint32_t)r, it.xs + ((size_t)it.R + r) * nw);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if constexpr (std::is_same<Tw, step_detail::f32e>::value)   // int32 diagonal, exact in fp32
+            rp.h[v] = ((rp.valid >> v) & 1u) ? __int2float_rn(static_cast<const int32_t*>(it.diag)[rp.base + v]) : 0.f;
+        else
+            rp.h[v] = ((rp.valid >> v) & 1u) ? static_cast<const H*>(it.diag)[rp.base + v] : H(0);
+    }
+    rp.xm = 0;
+    rp.m = 0;
+    rp.Ecur = 0;
+    rp.Ebest = 0;
+    rp.flips = 0;
+    const PhiloxKeys keys(it.seed);
+    const long long T = t_limit > 0 ? std::min(t_limit, it.T) : it.T;
+    if (T > 0) rp.draw(0u, keys);
+    float beta_next = T > 0 ? it.beta[0] : 0.f;
+    for (long long t = 0; t < T; ++t) {
+        const float beta = beta_next;
+        if (t + 1 < T) beta_next = it.beta[t + 1];
+        const int k = rp.template step<false>(t, t + 1 < T, beta, it.inc, keys);
+        if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
+        if constexpr (std::is_same<Tw, float>::value) {
+            if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
+                rp.recompute(static_cast<const float*>(it.diag), it.S);
+                if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
+            }
+        }
+    }
+    rp.flush_best();
+    const uint32_t word = rp.word();
+    if (lane % R_::P == 0) it.xs[(size_t)r * nw + (rp.base >> 5)] = word;
+    if (lane == 0) {
+        ReplicaScalars s;
+        s.E = A::store_e(rp.Ecur);
+        s.best = A::store_e(rp.Ebest);
+        s.flips = rp.flips;
+        s.m = rp.m;
+        s.check = 0;
+        it.sc[r] = s;
+    }
+}
+
 template <typename Tw, int V>
 __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ BatchClassParams bp)
 {
-    using R_ = WarpReplica<Tw, V>;
-    using A = step_detail::Arith<Tw>;
-    using H = typename R_::H;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long unit = 0;
@@ -75,53 +136,59 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
         }
         const BatchItemDev it = bp.items[lo];
         const int r = (int)(unit - (unsigned long long)it.unit0);
-        constexpr int nw = V;   // state words per replica (the padded width 32V / 32)
-        R_ rp;
-        rp.init(static_cast<const Tw*>(it.W), it.N, it.ldw, (uint32_t)r, it.xs + ((size_t)it.R + r) * nw);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            if constexpr (std::is_same<Tw, step_detail::f32e>::value)   // int32 diagonal, exact in fp32
-                rp.h[v] = ((rp.valid >> v) & 1u) ? __int2float_rn(static_cast<const int32_t*>(it.diag)[rp.base + v]) : 0.f;
-            else
-                rp.h[v] = ((rp.valid >> v) & 1u) ? static_cast<const H*>(it.diag)[rp.base + v] : H(0);
+        run_unit<Tw, V, false>(it, r, static_cast<const Tw*>(it.W), it.ldw, bp.t_limit);
+    }
+}
+
+// Shared-memory staging: the block takes group g = (item, r0) from the
+// counter, copies rows 0..N-1 of the item's W into shared memory (row pitch
+// 32 V, zeros beyond column N), and warp w runs replica r0 + w.
+template <typename Tw, int V>
+__global__ void __launch_bounds__(512) batch_kernel_smem(const __grid_constant__ BatchClassParams bp)
+{
+    extern __shared__ __align__(16) unsigned char wsm_raw[];
+    Tw* Ws = reinterpret_cast<Tw*>(wsm_raw);
+    __shared__ long long s_group;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();   // every warp is done with the previous group's copy
+        if (threadIdx.x == 0) s_group = (long long)atomicAdd(bp.head, 1ull);
+        __syncthreads();
+        const long long g = s_group;
+        if (g >= bp.n_groups) break;
+        const int2 gi = bp.groups[g];
+        const BatchItemDev it = bp.items[gi.x];
+        const Tw* Wg = static_cast<const Tw*>(it.W);
+        const int cols = bp.pitch;
+        for (int e = threadIdx.x; e < it.N * cols; e += blockDim.x) {
+            const int row = e / cols, col = e - row * cols;
+            Tw v{};
+            if (col < it.N) v = Wg[(size_t)row * it.ldw + col];
+            Ws[e] = v;
         }
-        rp.xm = 0;
-        rp.m = 0;
-        rp.Ecur = 0;
-        rp.Ebest = 0;
-        rp.flips = 0;
-        const PhiloxKeys keys(it.seed);
-        const long long T = bp.t_limit > 0 ? std::min(bp.t_limit, it.T) : it.T;
-        if (T > 0) rp.draw(0u, keys);
-        float beta_next = T > 0 ? it.beta[0] : 0.f;
-        for (long long t = 0; t < T; ++t) {
-            const float beta = beta_next;
-            if (t + 1 < T) beta_next = it.beta[t + 1];
-            const int k = rp.template step<false>(t, t + 1 < T, beta, it.inc, keys);
-            if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
-            if constexpr (std::is_same<Tw, float>::value) {
-                if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
-                    rp.recompute(static_cast<const float*>(it.diag), it.S);
-                    if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
-                }
-            }
-        }
-        rp.flush_best();
-        const uint32_t word = rp.word();
-        if (lane % R_::P == 0) it.xs[(size_t)r * nw + (rp.base >> 5)] = word;
-        if (lane == 0) {
-            ReplicaScalars s;
-            s.E = A::store_e(rp.Ecur);
-            s.best = A::store_e(rp.Ebest);
-            s.flips = rp.flips;
-            s.m = rp.m;
-            s.check = 0;
-            it.sc[r] = s;
-        }
+        __syncthreads();
+        const int r = gi.y + warp;
+        if (r < it.R) run_unit<Tw, V, true>(it, r, Ws, cols, bp.t_limit);
     }
 }
 
 typedef void (*BatchKernel)(BatchClassParams);
+
+BatchKernel smem_kernel_for(bool int8, int V)
+{
+    if (int8) {
+        switch (V) {
+        case 4: return batch_kernel_smem<step_detail::f32e, 4>;
+        case 8: return batch_kernel_smem<step_detail::f32e, 8>;
+        }
+    } else {
+        switch (V) {
+        case 4: return batch_kernel_smem<float, 4>;
+        case 8: return batch_kernel_smem<float, 8>;
+        }
+    }
+    return nullptr;
+}
 
 BatchKernel kernel_for(bool int8, int V)
 {
@@ -159,16 +226,27 @@ __global__ void batch_finalize_kernel(bool int8, int R, const ReplicaScalars* sc
 
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
-// Autotuner: warps per block of the persistent kernel of one class, chosen by
-// timing probes of the class's own first units; cached per (device, class).
+// Autotuner: the configuration of the persistent kernel of one class (where
+// rows of W come from, warps per block), chosen by timing probes of the class's
+// own first units; cached per (device, class, whether staging fits, size of
+// the probe: a class too small to fill the GPU is tuned again when it grows).
+struct BatchConfig {
+    bool smem = false;
+    int warps_per_block = 4;
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, bool, int>, int> g_tune_cache;
+std::map<std::tuple<int, bool, int, bool, int>, BatchConfig> g_tune_cache;
+std::map<std::tuple<int, bool, int, bool, int>, std::string> g_tune_log;   // the probes behind each entry
+thread_local std::string g_batch_desc;
 
-int blocks_for(BatchKernel k, int warps_per_block, int sms)
+// Largest dynamic shared memory a block may ask for on sm_100-class GPUs.
+constexpr size_t kMaxStagedBytes = 227u * 1024u;
+
+int blocks_for(BatchKernel k, int warps_per_block, int sms, size_t smem)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(k), warps_per_block * 32, 0) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(k), warps_per_block * 32,
+                                                      smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -187,43 +265,122 @@ struct BatchClass {
     int n_items;
     long long units;
     unsigned long long* head;
-    int warps_per_block;
+    int2* groups_dev;            // room for the groups of 2 replicas (the smallest staged group)
+    int max_N;
+    BatchConfig cfg;
+    std::string probes;          // the tuner's measurements, for da_batch_describe
+    size_t staged_bytes() const { return (size_t)max_N * 32 * V * 4; }
+    bool can_stage() const { return smem_kernel_for(int8, V) != nullptr && staged_bytes() <= kMaxStagedBytes; }
 };
 
-int tune_class(BatchClass& c, int dev, int sms, cudaStream_t st)
+// Groups of `wpb` replicas, each within one item, covering the first `units` units.
+std::vector<int2> make_groups(const std::vector<int>& replicas_per_item, int wpb, long long units)
 {
-    const auto key = std::make_tuple(dev, c.int8, c.V);
+    std::vector<int2> g;
+    long long covered = 0;
+    for (int i = 0; i < (int)replicas_per_item.size() && covered < units; ++i)
+        for (int r0 = 0; r0 < replicas_per_item[i] && covered < units; r0 += wpb) {
+            g.push_back(make_int2(i, r0));
+            covered += std::min(wpb, replicas_per_item[i] - r0);
+        }
+    return g;
+}
+
+// One launch of a class's kernel in configuration cfg over its first `units`
+// units (all of them for the real run), t_limit steps per unit (0: all).
+cudaError_t launch_class(const BatchClass& c, const std::vector<int>& reps, const BatchConfig& cfg, long long units,
+                         long long t_limit, int sms, cudaStream_t st, bool upload_groups)
+{
+    BatchClassParams bp{c.items_dev, c.n_items, units, c.head, t_limit, nullptr, 0, 0};
+    if (!cfg.smem) {
+        BatchKernel k = kernel_for(c.int8, c.V);
+        k<<<blocks_for(k, cfg.warps_per_block, sms, 0), cfg.warps_per_block * 32, 0, st>>>(bp);
+        return cudaGetLastError();
+    }
+    BatchKernel k = smem_kernel_for(c.int8, c.V);
+    const size_t bytes = c.staged_bytes();
+    cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    const std::vector<int2> groups = make_groups(reps, cfg.warps_per_block, units);
+    if (upload_groups) {
+        e = cudaMemcpyAsync(c.groups_dev, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    bp.groups = c.groups_dev;
+    bp.n_groups = (long long)groups.size();
+    bp.pitch = 32 * c.V;
+    k<<<blocks_for(k, cfg.warps_per_block, sms, bytes), cfg.warps_per_block * 32, bytes, st>>>(bp);
+    return cudaGetLastError();
+}
+
+// da_batch_force: staging -1 = the tuner's choice, 0 = rows from L2, 1 = staged where
+// the class allows; warps per block 0 = the tuner's choice.
+std::atomic<int> g_force_staging{-1}, g_force_wpb{0};
+
+BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int sms, cudaStream_t st)
+{
+    const int fs = g_force_staging.load(), fw = g_force_wpb.load();
+    if (fs >= 0 || fw > 0) {
+        BatchConfig cfg;
+        cfg.smem = fs == 1 && c.can_stage();
+        cfg.warps_per_block = fw > 0 ? fw : (cfg.smem ? 8 : 4);
+        if (!cfg.smem) cfg.warps_per_block = std::min(cfg.warps_per_block, 4);   // the L2 kernel's block limit
+        if (cfg.smem) cfg.warps_per_block = std::max(cfg.warps_per_block, 2);
+        c.probes = "forced";
+        return cfg;
+    }
+    const long long units = std::min<long long>(c.units, (long long)sms * 16);
+    int ubits = 0;
+    while ((2ll << ubits) <= units) ++ubits;   // floor(log2(probe units))
+    const auto key = std::make_tuple(dev, c.int8, c.V, c.can_stage(), ubits);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto f = g_tune_cache.find(key);
-        if (f != g_tune_cache.end()) return f->second;
+        if (f != g_tune_cache.end()) {
+            c.probes = "cached; " + g_tune_log[key];
+            return f->second;
+        }
     }
-    BatchKernel k = kernel_for(c.int8, c.V);
-    int best = 4;
+    std::vector<BatchConfig> cands;
+    for (int wpb : {1, 2, 4}) cands.push_back(BatchConfig{false, wpb});
+    if (c.can_stage())
+        for (int wpb : {2, 4, 8, 16}) cands.push_back(BatchConfig{true, wpb});
+    BatchConfig best = cands.front();
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
-    for (int wpb : {1, 2, 4}) {
-        BatchClassParams bp{c.items_dev, c.n_items, std::min<long long>(c.units, (long long)sms * 16), c.head, 256};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return best;
+    }
+    std::string log;
+    for (const BatchConfig& cfg : cands) {
         cudaMemsetAsync(c.head, 0, 8, st);
         cudaEventRecord(e0, st);
-        k<<<blocks_for(k, wpb, sms), wpb * 32, 0, st>>>(bp);
+        cudaError_t le = launch_class(c, reps, cfg, units, 256, sms, st, true);
         cudaEventRecord(e1, st);
-        if (cudaStreamSynchronize(st) != cudaSuccess) {
+        if (le == cudaSuccess) le = cudaStreamSynchronize(st);
+        if (le != cudaSuccess) {
             cudaGetLastError();
+            log += std::string(log.empty() ? "" : ", ") + (cfg.smem ? "smem" : "l2") + "x" +
+                   std::to_string(cfg.warps_per_block) + " failed: " + cudaGetErrorString(le);
             continue;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        log += std::string(log.empty() ? "" : ", ") + (cfg.smem ? "smem" : "l2") + "x" +
+               std::to_string(cfg.warps_per_block) + " " + std::to_string(ms).substr(0, 6) + " ms";
         if (ms < best_ms) {
             best_ms = ms;
-            best = wpb;
+            best = cfg;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    c.probes = "probes (" + std::to_string(units) + " replicas x 256 steps): " + log;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best;
+    g_tune_log[key] = c.probes;
     return best;
 }
 
@@ -301,12 +458,21 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         auto& c = classes[{hi[i].int8, hi[i].V}];
         c.int8 = hi[i].int8;
         c.V = hi[i].V;
+        c.max_N = std::max(c.max_N, hi[i].N);
         c.item_idx.push_back(i);
     }
     const size_t o_desc = off;
     off += da::al((size_t)n * sizeof(BatchItemDev));
     const size_t o_heads = off;
     off += da::al(classes.size() * 8);
+    // per class: room for its groups of two replicas (the smallest group a staged launch uses)
+    std::map<std::pair<bool, int>, size_t> o_groups;
+    for (auto& kv : classes) {
+        size_t g = 0;
+        for (int i : kv.second.item_idx) g += (size_t)(items[i].replicas + 1) / 2;
+        o_groups[kv.first] = off;
+        off += da::al(g * sizeof(int2));
+    }
     char* base = nullptr;
     if (da::dev_malloc(reinterpret_cast<void**>(&base), off) != cudaSuccess) {
         cudaGetLastError();
@@ -348,6 +514,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
             c.items_dev = reinterpret_cast<BatchItemDev*>(base + o_desc) + di;
             c.n_items = (int)c.item_idx.size();
             c.head = reinterpret_cast<unsigned long long*>(base + o_heads) + ci;
+            c.groups_dev = reinterpret_cast<int2*>(base + o_groups[kv.first]);
             for (int i : c.item_idx) {
                 const da_batch_item& it = items[i];
                 BatchItemDev d{};
@@ -388,21 +555,45 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     for (int i = 0; i < n; ++i)
         DA_B(cudaMemsetAsync(base + o_xs[i], 0, (size_t)2 * items[i].replicas * hi[i].V * 4, st));
     DA_B(cudaStreamSynchronize(st));
-    for (auto& kv : classes) kv.second.warps_per_block = da::tune_class(kv.second, dev, sms, st);
+    // replicas of each class's items, in the class's item order (for the staged groups)
+    std::map<std::pair<bool, int>, std::vector<int>> reps;
+    for (auto& kv : classes)
+        for (int i : kv.second.item_idx) reps[kv.first].push_back(items[i].replicas);
+    std::string desc_text;
+    for (auto& kv : classes) {
+        BatchClass& c = kv.second;
+        c.cfg = da::tune_class(c, reps[kv.first], dev, sms, st);
+        desc_text += std::string(desc_text.empty() ? "" : "; ") + (c.int8 ? "int8" : "fp32") + " V=" +
+                     std::to_string(c.V) + " (N <= " + std::to_string(c.max_N) + ", " + std::to_string(c.n_items) +
+                     " instances, " + std::to_string(c.units) + " replicas): " +
+                     (c.cfg.smem ? "W staged in shared memory" : "rows of W from L2") + ", " +
+                     std::to_string(c.cfg.warps_per_block) + " warps per block [" + c.probes + "]";
+    }
+    da::g_batch_desc = desc_text;
     for (int i = 0; i < n; ++i)
         DA_B(cudaMemsetAsync(base + o_xs[i], 0, (size_t)2 * items[i].replicas * hi[i].V * 4, st));
+    // the staged classes' group tables for the whole run (uploaded before the capture)
+    for (auto& kv : classes) {
+        const BatchClass& c = kv.second;
+        if (!c.cfg.smem) continue;
+        const std::vector<int2> groups = da::make_groups(reps[kv.first], c.cfg.warps_per_block, c.units);
+        DA_B(cudaMemcpyAsync(c.groups_dev, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        DA_B(cudaStreamSynchronize(st));
+    }
     DA_B(cudaStreamSynchronize(st));
 
     // the graph: persistent kernel per class, then the exact evaluation of every item
     DA_B(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     bool capture_ok = true;
     DA_B(cudaMemsetAsync(base + o_heads, 0, classes.size() * 8, st));
+    std::string launch_err;
     for (auto& kv : classes) {
-        BatchClass& c = kv.second;
-        da::BatchKernel k = da::kernel_for(c.int8, c.V);
-        da::BatchClassParams bp{c.items_dev, c.n_items, c.units, c.head, 0};
-        k<<<da::blocks_for(k, c.warps_per_block, sms), c.warps_per_block * 32, 0, st>>>(bp);
-        if (cudaGetLastError() != cudaSuccess) capture_ok = false;
+        const BatchClass& c = kv.second;
+        const cudaError_t le = da::launch_class(c, reps[kv.first], c.cfg, c.units, 0, sms, st, false);
+        if (le != cudaSuccess) {
+            if (capture_ok) launch_err = std::string(" (class launch: ") + cudaGetErrorString(le) + ")";
+            capture_ok = false;
+        }
     }
     for (auto& kv : classes) {
         for (int i : kv.second.item_idx) {
@@ -419,7 +610,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     }
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (ce != cudaSuccess || !capture_ok) {
-        status = bfail(DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        status = bfail(DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce) + launch_err);
         cudaGetLastError();
         cleanup();
         return status;
@@ -467,4 +658,31 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     cleanup();
     return DA_OK;
 #undef DA_B
+}
+
+extern "C" da_status da_batch_describe(char* buf, int64_t len)
+{
+    if (!buf || len < 1) return DA_EINVAL;
+    const std::string& d = da::g_batch_desc;
+    const size_t n = std::min<size_t>(d.size(), (size_t)len - 1);
+    std::memcpy(buf, d.data(), n);
+    buf[n] = 0;
+    return DA_OK;
+}
+
+extern "C" da_status da_batch_force(int32_t staging, int32_t warps_per_block)
+{
+    const bool wpb_ok = warps_per_block == 0 || warps_per_block == 1 || warps_per_block == 2 ||
+                        warps_per_block == 4 || warps_per_block == 8 || warps_per_block == 16;
+    if (staging < -1 || staging > 1 || !wpb_ok || (staging != 1 && warps_per_block > 4)) {
+        da::set_last_error("staging in {-1, 0, 1}; warps per block in {0, 1, 2, 4} (up to 16 when staged)");
+        return DA_EINVAL;
+    }
+    if (staging == 1 && warps_per_block == 1) {
+        da::set_last_error("a staged block runs at least 2 warps");
+        return DA_EINVAL;
+    }
+    da::g_force_staging = staging;
+    da::g_force_wpb = warps_per_block;
+    return DA_OK;
 }

@@ -17,7 +17,9 @@
 namespace da {
 namespace step_detail {
 
-template <typename Tw, int V>
+// SW: the rows of W are read from a copy staged in shared memory (W points
+// there) instead of from global memory.
+template <typename Tw, int V, bool SW = false>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -71,6 +73,12 @@ struct WarpReplica {
     }
 
     __device__ __forceinline__ uint32_t word() const { return gather_word<V>(xm, lane); }
+
+    static __device__ __forceinline__ void load_row(const Tw* p, Tw (&c)[V])
+    {
+        if constexpr (SW) RowShared<Tw, V>::load(p, c);
+        else Row<Tw, V>::load(p, c);
+    }
 
     __device__ __forceinline__ void snapshot()
     {
@@ -167,7 +175,7 @@ struct WarpReplica {
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
-        if (FULL || base < N) Row<Tw, V>::load(W + (size_t)k * ldw + base, cv);
+        if (FULL || base < N) load_row(W + (size_t)k * ldw + base, cv);
         overlap();
         if (FULL || base < N) {
             const typename A::Sign sg = A::sign(xold);
@@ -203,7 +211,7 @@ struct WarpReplica {
                 const int j = wi * 32 + b;
                 if (base < N) {
                     Tw cv[V];
-                    Row<Tw, V>::load(W + (size_t)j * ldw + base, cv);
+                    load_row(W + (size_t)j * ldw + base, cv);
 #pragma unroll
                     for (int v = 0; v < V; ++v) acc[v] += fixed_of_f32(cv[v], S);
                 }

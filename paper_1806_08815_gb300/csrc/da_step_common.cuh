@@ -131,7 +131,9 @@ __device__ __forceinline__ T ldx(const T* p)
 }
 
 // Row k of W at the V consecutive entries of this lane (16-byte loads where
-// the lane's slice allows).
+// the lane's slice allows).  load() reads global memory through the read-only
+// path; load_shared() reads a copy of W staged in shared memory (fp32 forms
+// only).
 template <typename Tw, int V> struct Row;
 template <int V> struct Row<float, V> {
     static __device__ __forceinline__ void load(const float* p, float (&c)[V])
@@ -152,6 +154,27 @@ template <int V> struct Row<f32e, V> {
         for (int q = 0; q < V / 4; ++q) {
             const float4 f = ldx(reinterpret_cast<const float4*>(p) + q);
             c[4 * q].f = f.x; c[4 * q + 1].f = f.y; c[4 * q + 2].f = f.z; c[4 * q + 3].f = f.w;
+        }
+    }
+};
+
+// 16-byte loads from shared memory (p points into the block's staged copy).
+template <typename Tw, int V> struct RowShared {
+    static __device__ __forceinline__ void load(const Tw* p, Tw (&c)[V])
+    {
+        static_assert(sizeof(Tw) == 4 && V % 4 == 0, "fp32 forms only");
+        const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) {
+            float x, y, z, w;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(x), "=f"(y), "=f"(z), "=f"(w)
+                         : "r"(a + 16u * q)
+                         : "memory");
+            reinterpret_cast<float*>(&c[4 * q])[0] = x;
+            reinterpret_cast<float*>(&c[4 * q + 1])[0] = y;
+            reinterpret_cast<float*>(&c[4 * q + 2])[0] = z;
+            reinterpret_cast<float*>(&c[4 * q + 3])[0] = w;
         }
     }
 };

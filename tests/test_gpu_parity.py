@@ -448,6 +448,61 @@ def test_batched_launch_matches_single_instances(da, inst):
     assert np.array_equal(outs[1]["trace"], ref["trace"])
 
 
+@pytest.mark.parametrize("staging,wpb", [(0, 1), (0, 4), (1, 2), (1, 8), (1, 16), (-1, 0)])
+def test_batched_configurations_match_single_instances(da, inst, staging, wpb):
+    """Every configuration the batched launch's tuner can choose (rows of W from L2 at 1 or 4
+    warps per block; W staged in shared memory with groups of 2, 8 or 16 replicas; the tuner
+    itself) gives each item the results of its own da_anneal run, bit for bit.  Sizes that
+    stage (V = 4 and V = 8 classes up to N = 221) and that do not, ragged replica counts."""
+    rng = np.random.default_rng(7)
+    jobs, refs = [], []
+    sizes = [64, 100, 128, 200, 221, 256, 40, 1024]
+    for n, N in enumerate(sizes):
+        q = inst.sk_bimodal(N, 50 + n) if n % 2 == 0 else inst.sk_gaussian(N, 50 + n)
+        T = int(rng.integers(150, 600))
+        beta = inst.beta_linear(0.1, 3.0, T)
+        ctx = da.da_create(q.Q)
+        R = int(rng.integers(3, 23))
+        P = 0 if q.bimodal else 100
+        jobs.append(dict(ctx=ctx, beta=beta, offset_inc=0.5, replicas=R, seed=300 + n, recompute_every=P,
+                         trace=True))
+        refs.append(da.da_anneal(ctx, beta, 0.5, R, 300 + n, recompute_every=P, trace=True))
+    da.binding.da_batch_force(staging, wpb)
+    try:
+        outs, el = da.binding.da_batch_anneal(jobs)
+        desc = da.binding.da_batch_describe()
+    finally:
+        da.binding.da_batch_force(-1, 0)
+    assert el > 0
+    if staging == 1:
+        assert "shared memory" in desc, desc
+    for o, r in zip(outs, refs):
+        for k in ("trace", "final_x", "best_x", "flips", "final_E", "best_E", "max_drift"):
+            assert np.array_equal(o[k], r[k]), (k, desc)
+
+
+@pytest.mark.parametrize("N,R,kind", [(300, 40, "f32"), (97, 9, "i8"), (1500, 16, "f32"), (2100, 8, "i8")])
+def test_tuned_launch_shape_keeps_results(da, inst, N, R, kind):
+    """da_tune_shape picks the fastest launch shape for (instance, replicas) and every later
+    anneal of that class uses it: the trajectories stay those of the oracle, bit for bit."""
+    import oracle
+    q = inst.sk_bimodal(N, 9) if kind == "i8" else inst.sk_gaussian(N, 9)
+    ctx = da.da_create(q.Q)
+    shape = da.binding.da_tune_shape(ctx, R, 64)
+    assert shape["G"] in (1, 2, 4, 8) and 32 * shape["V"] * shape["G"] >= N, shape
+    beta = inst.beta_linear(0.1, 4.0, 300)
+    P = 0 if kind == "i8" else 64
+    inc = 1.0 if kind == "i8" else 0.25
+    got = da.da_anneal(ctx, beta, inc, R, 21, recompute_every=P, trace=True)
+    ref = oracle.da_anneal(q.Q, beta, R=R, seed=21, inc=inc, recompute_every=P, trace=True, nthreads=NT)
+    assert np.array_equal(got["trace"], ref["trace"]), shape
+    assert np.array_equal(got["final_x"], ref["x_final"]), shape
+    # a second context of the same class picks the tuned shape up from the process cache
+    ctx2 = da.da_create(q.Q)
+    got2 = da.da_anneal(ctx2, beta, inc, R, 21, recompute_every=P, trace=True)
+    assert np.array_equal(got2["trace"], got["trace"])
+
+
 @pytest.mark.parametrize("dtype", ["i8", "f32"])
 def test_move_energy_percentiles_match_brute_force(da, inst, dtype):
     """The temperature grid's input: percentiles of the energy rises of all single-flip
