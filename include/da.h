@@ -124,9 +124,9 @@ const char* da_last_error(void);
  *          Delta E beyond 2^24 enters the acceptance test rounded to fp32, as
  *          every Delta E does); DA_FP32 requires finite values.
  *          DA_INT16 contexts serve da_anneal, da_anneal_async, da_pt,
- *          da_pt_adaptive, da_energy, da_field_recompute and
- *          da_move_energy_percentiles (not the batched, plain, allocation-free
- *          or request-loop forms).
+ *          da_pt_adaptive, da_batch_anneal, da_energy, da_field_recompute and
+ *          da_move_energy_percentiles, and da_submit takes DA_INT16 jobs (the
+ *          plain and allocation-free forms take DA_INT8 / DA_FP32 and DA_INT8).
  * The library stores W (symmetric, zero diagonal) and diag(Q) in device
  * memory.  Errors: DA_EINVAL (bad N, dtype, range), DA_ENOMEM, DA_ECUDA. */
 da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out);

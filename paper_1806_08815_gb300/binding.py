@@ -507,11 +507,13 @@ class Request:
 
 
 def da_submit(srv: Server, Q: np.ndarray, beta: np.ndarray, offset_inc: float, replicas: int, seed: int,
-              recompute_every: int = 0) -> Request:
+              recompute_every: int = 0, dtype: int | None = None) -> Request:
+    """Queue a request (integer Q -> DA_INT8, or DA_INT16 when asked; float32 Q -> DA_FP32)."""
     Q = np.asarray(Q)
     N = Q.shape[0]
-    dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
-    Qc = np.ascontiguousarray(Q, dtype=np.int32 if dtype == DA_INT8 else np.float32)
+    if dtype is None:
+        dtype = DA_INT8 if np.issubdtype(Q.dtype, np.integer) else DA_FP32
+    Qc = np.ascontiguousarray(Q, dtype=np.float32 if dtype == DA_FP32 else np.int32)
     b = np.ascontiguousarray(beta, dtype=np.float32)
     job = da_job(_ptr(Qc), N, dtype, _ptr(b), b.size, float(offset_inc), int(replicas), int(seed) & (2 ** 64 - 1),
                  int(recompute_every))

@@ -388,6 +388,8 @@ size_t instance_W_bytes(int n, int dtype)
 StepShape default_shape(int N, int R) { return auto_shape(N, R); }
 
 void set_last_error(const std::string& msg) { g_err = msg; }
+const TcOperand& ctx_tc_operand(const da_ctx* c) { return c->tc; }
+
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S, const void** Wstep)
 {
     *W = c->W;

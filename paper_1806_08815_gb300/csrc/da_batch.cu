@@ -174,9 +174,13 @@ __global__ void __launch_bounds__(512) batch_kernel_smem(const __grid_constant__
 
 typedef void (*BatchKernel)(BatchClassParams);
 
-BatchKernel smem_kernel_for(bool int8, int V)
+// Kernels per step coupling form wk: kWInt8AsF32 (int8 instances, exact fp32
+// couplings), kWFp32, kWInt16 (16-bit couplings, int32 fields; rows from L2
+// only: the staged copy holds 4-byte entries).
+BatchKernel smem_kernel_for(int wk, int V)
 {
-    if (int8) {
+    if (wk == kWInt16) return nullptr;
+    if (wk == kWInt8AsF32) {
         switch (V) {
         case 4: return batch_kernel_smem<step_detail::f32e, 4>;
         case 8: return batch_kernel_smem<step_detail::f32e, 8>;
@@ -190,9 +194,16 @@ BatchKernel smem_kernel_for(bool int8, int V)
     return nullptr;
 }
 
-BatchKernel kernel_for(bool int8, int V)
+BatchKernel kernel_for(int wk, int V)
 {
-    if (int8) {
+    if (wk == kWInt16) {
+        switch (V) {
+        case 4: return batch_kernel<int16_t, 4>;
+        case 8: return batch_kernel<int16_t, 8>;
+        case 16: return batch_kernel<int16_t, 16>;
+        case 32: return batch_kernel<int16_t, 32>;
+        }
+    } else if (wk == kWInt8AsF32) {
         switch (V) {
         case 4: return batch_kernel<step_detail::f32e, 4>;
         case 8: return batch_kernel<step_detail::f32e, 8>;
@@ -208,6 +219,16 @@ BatchKernel kernel_for(bool int8, int V)
         }
     }
     return nullptr;
+}
+
+// OR of the items' tensor-core error flags (a bounded wait inside an exact
+// evaluation that gave up) into *out.
+__global__ void collect_flags_kernel(int* const* flags, int n, int* out)
+{
+    int any = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) any |= *flags[i];
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) *out = any;
 }
 
 __global__ void batch_finalize_kernel(bool int8, int R, const ReplicaScalars* sc, const long long* eex,
@@ -235,8 +256,8 @@ struct BatchConfig {
     int warps_per_block = 4;
 };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, bool, int, bool, int>, BatchConfig> g_tune_cache;
-std::map<std::tuple<int, bool, int, bool, int>, std::string> g_tune_log;   // the probes behind each entry
+std::map<std::tuple<int, int, int, bool, int>, BatchConfig> g_tune_cache;
+std::map<std::tuple<int, int, int, bool, int>, std::string> g_tune_log;   // the probes behind each entry
 thread_local std::string g_batch_desc;
 
 // Largest dynamic shared memory a block may ask for on sm_100-class GPUs.
@@ -258,7 +279,7 @@ int blocks_for(BatchKernel k, int warps_per_block, int sms, size_t smem)
 
 // Host side of one class: items already laid out in device memory.
 struct BatchClass {
-    bool int8;
+    int wk;                      // step coupling form (kWInt8AsF32, kWFp32, kWInt16)
     int V;
     std::vector<int> item_idx;   // indices into the caller's item array
     BatchItemDev* items_dev;
@@ -270,7 +291,7 @@ struct BatchClass {
     BatchConfig cfg;
     std::string probes;          // the tuner's measurements, for da_batch_describe
     size_t staged_bytes() const { return (size_t)max_N * 32 * V * 4; }
-    bool can_stage() const { return smem_kernel_for(int8, V) != nullptr && staged_bytes() <= kMaxStagedBytes; }
+    bool can_stage() const { return smem_kernel_for(wk, V) != nullptr && staged_bytes() <= kMaxStagedBytes; }
 };
 
 // Groups of `wpb` replicas, each within one item, covering the first `units` units.
@@ -293,11 +314,11 @@ cudaError_t launch_class(const BatchClass& c, const std::vector<int>& reps, cons
 {
     BatchClassParams bp{c.items_dev, c.n_items, units, c.head, t_limit, nullptr, 0, 0};
     if (!cfg.smem) {
-        BatchKernel k = kernel_for(c.int8, c.V);
+        BatchKernel k = kernel_for(c.wk, c.V);
         k<<<blocks_for(k, cfg.warps_per_block, sms, 0), cfg.warps_per_block * 32, 0, st>>>(bp);
         return cudaGetLastError();
     }
-    BatchKernel k = smem_kernel_for(c.int8, c.V);
+    BatchKernel k = smem_kernel_for(c.wk, c.V);
     const size_t bytes = c.staged_bytes();
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -333,7 +354,7 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
     const long long units = std::min<long long>(c.units, (long long)sms * 16);
     int ubits = 0;
     while ((2ll << ubits) <= units) ++ubits;   // floor(log2(probe units))
-    const auto key = std::make_tuple(dev, c.int8, c.V, c.can_stage(), ubits);
+    const auto key = std::make_tuple(dev, c.wk, c.V, c.can_stage(), ubits);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto f = g_tune_cache.find(key);
@@ -408,6 +429,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     struct Host {
         const void* W;       // couplings for the exact evaluation
         const void* Wstep;   // couplings in the step kernel's form (int8 instances: exact fp32)
+        int dtype;           // da_dtype of the instance
         const void* diag;
         int N, ldw, S;
         bool int8;
@@ -420,8 +442,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         da_dtype dt;
         if (!it.ctx || da_ctx_info(it.ctx, &N, &dt) != DA_OK) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad context");
         if (N > 1024) return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes N <= 1024");
-        if (dt != DA_INT8 && dt != DA_FP32)
-            return bfail(DA_EINVAL, "item " + std::to_string(i) + ": the batched launch takes DA_INT8 or DA_FP32");
+
         if (it.replicas < 1 || it.steps < 0 || it.steps >= (1ll << 32) || (it.steps > 0 && !it.beta))
             return bfail(DA_EINVAL, "item " + std::to_string(i) + ": bad replicas/steps/schedule");
         if (it.steps > 0 && !da::schedule_ok(it.beta, it.steps))
@@ -434,14 +455,15 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         h.N = (int)N;
         h.ldw = ldw;
         h.S = S;
-        h.int8 = dt == DA_INT8;
+        h.int8 = dt != DA_FP32;   // integer couplings: exact fields and energies
+        h.dtype = (int)dt;
         int V = 4;
         while (32 * V < h.N) V *= 2;
         h.V = V;
         hi[i] = h;
     }
     // device layout: per item betas, states, scalars, traces, results; per class descriptors
-    std::vector<size_t> o_beta(n), o_xs(n), o_sc(n), o_tr(n), o_eex(n), o_part(n), o_res(n);
+    std::vector<size_t> o_beta(n), o_xs(n), o_sc(n), o_tr(n), o_eex(n), o_part(n), o_res(n), o_tcs(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         const int R = items[i].replicas, nw = hi[i].V;
@@ -452,11 +474,13 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         o_eex[i] = off; off += da::al((size_t)2 * R * 8);
         o_part[i] = off; off += da::al((size_t)16 * ((hi[i].N + 63) / 64) * 2 * R);
         o_res[i] = off; off += da::al((size_t)4 * R * 8);
+        o_tcs[i] = off; off += da::al(da::tc_state_bytes(hi[i].N, 2 * R));   // states of the exact evaluation
     }
-    std::map<std::pair<bool, int>, BatchClass> classes;
+    std::map<std::pair<int, int>, BatchClass> classes;
     for (int i = 0; i < n; ++i) {
-        auto& c = classes[{hi[i].int8, hi[i].V}];
-        c.int8 = hi[i].int8;
+        const int wk = hi[i].dtype == DA_INT8 ? da::kWInt8AsF32 : hi[i].dtype;
+        auto& c = classes[{wk, hi[i].V}];
+        c.wk = wk;
         c.V = hi[i].V;
         c.max_N = std::max(c.max_N, hi[i].N);
         c.item_idx.push_back(i);
@@ -465,8 +489,10 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     off += da::al((size_t)n * sizeof(BatchItemDev));
     const size_t o_heads = off;
     off += da::al(classes.size() * 8);
+    const size_t o_flags = off;   // the items' error-flag pointers, then their OR
+    off += da::al((size_t)n * sizeof(int*) + sizeof(int));
     // per class: room for its groups of two replicas (the smallest group a staged launch uses)
-    std::map<std::pair<bool, int>, size_t> o_groups;
+    std::map<std::pair<int, int>, size_t> o_groups;
     for (auto& kv : classes) {
         size_t g = 0;
         for (int i : kv.second.item_idx) g += (size_t)(items[i].replicas + 1) / 2;
@@ -540,7 +566,13 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
             ++ci;
         }
     }
-    // uploads (outside the graph: the schedules and descriptors)
+    // uploads (outside the graph: the schedules, descriptors and error-flag pointers)
+    {
+        std::vector<int*> fl((size_t)n);
+        for (int i = 0; i < n; ++i) fl[i] = da::ctx_tc_operand(items[i].ctx).err;
+        DA_B(cudaMemcpyAsync(base + o_flags, fl.data(), fl.size() * sizeof(int*), cudaMemcpyHostToDevice, st));
+        DA_B(cudaStreamSynchronize(st));
+    }
     for (int i = 0; i < n; ++i)
         if (items[i].steps > 0)
             DA_B(cudaMemcpyAsync(base + o_beta[i], items[i].beta, (size_t)items[i].steps * 4, cudaMemcpyHostToDevice, st));
@@ -556,14 +588,14 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         DA_B(cudaMemsetAsync(base + o_xs[i], 0, (size_t)2 * items[i].replicas * hi[i].V * 4, st));
     DA_B(cudaStreamSynchronize(st));
     // replicas of each class's items, in the class's item order (for the staged groups)
-    std::map<std::pair<bool, int>, std::vector<int>> reps;
+    std::map<std::pair<int, int>, std::vector<int>> reps;
     for (auto& kv : classes)
         for (int i : kv.second.item_idx) reps[kv.first].push_back(items[i].replicas);
     std::string desc_text;
     for (auto& kv : classes) {
         BatchClass& c = kv.second;
         c.cfg = da::tune_class(c, reps[kv.first], dev, sms, st);
-        desc_text += std::string(desc_text.empty() ? "" : "; ") + (c.int8 ? "int8" : "fp32") + " V=" +
+        desc_text += std::string(desc_text.empty() ? "" : "; ") + (c.wk == da::kWFp32 ? "fp32" : c.wk == da::kWInt16 ? "int16" : "int8") + " V=" +
                      std::to_string(c.V) + " (N <= " + std::to_string(c.max_N) + ", " + std::to_string(c.n_items) +
                      " instances, " + std::to_string(c.units) + " replicas): " +
                      (c.cfg.smem ? "W staged in shared memory" : "rows of W from L2") + ", " +
@@ -599,15 +631,20 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         for (int i : kv.second.item_idx) {
             const int R = items[i].replicas, nw = hi[i].V;
             long long* eex = reinterpret_cast<long long*>(base + o_eex[i]);
-            if (da::launch_recompute(hi[i].int8, hi[i].W, hi[i].diag, hi[i].N, hi[i].ldw, hi[i].S,
-                                     reinterpret_cast<uint32_t*>(base + o_xs[i]), nw, 2 * R, nullptr, hi[i].N, eex, 1, st,
-                                     reinterpret_cast<long long*>(base + o_part[i])) != cudaSuccess)
+            // the exact evaluation of final and best states on the tensor cores (the item's
+            // context holds the operand of its couplings)
+            if (da::launch_recompute_tc(hi[i].int8, da::ctx_tc_operand(items[i].ctx), hi[i].diag, hi[i].N, hi[i].S,
+                                        reinterpret_cast<uint32_t*>(base + o_xs[i]), nw, 2 * R, nullptr, hi[i].N, eex,
+                                        1, st, reinterpret_cast<long long*>(base + o_part[i]),
+                                        base + o_tcs[i]) != cudaSuccess)
                 capture_ok = false;
             da::batch_finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(
                 hi[i].int8, R, reinterpret_cast<da::ReplicaScalars*>(base + o_sc[i]), eex,
                 reinterpret_cast<double*>(base + o_res[i]));
         }
     }
+    int* flag_out = reinterpret_cast<int*>(base + o_flags + (size_t)n * sizeof(int*));
+    da::collect_flags_kernel<<<1, 256, 0, st>>>(reinterpret_cast<int* const*>(base + o_flags), n, flag_out);
     cudaError_t ce = cudaStreamEndCapture(st, &graph);
     if (ce != cudaSuccess || !capture_ok) {
         status = bfail(DA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce) + launch_err);
@@ -639,7 +676,16 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         res[i].resize((size_t)4 * items[i].replicas);
         DA_B(cudaMemcpyAsync(res[i].data(), base + o_res[i], res[i].size() * 8, cudaMemcpyDeviceToHost, st));
     }
+    int flag = 0;
+    DA_B(cudaMemcpyAsync(&flag, flag_out, sizeof(int), cudaMemcpyDeviceToHost, st));
     DA_B(cudaStreamSynchronize(st));
+    if (flag) {
+        for (int i = 0; i < n; ++i) cudaMemsetAsync(da::ctx_tc_operand(items[i].ctx).err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        status = bfail(DA_ETIMEOUT, "a bounded wait inside an exact evaluation gave up; the results are invalid");
+        cleanup();
+        return status;
+    }
     float ms = 0.f;
     DA_B(cudaEventElapsedTime(&ms, e0, e1));
     if (elapsed_s) *elapsed_s = ms * 1e-3;

@@ -6,7 +6,7 @@
 // the calculation of the initial N effective fields").  This library
 // recomputes them only to bound the drift of the fp32 fields (one rounding per
 // update) and to evaluate final and best states exactly:
-//   int8 couplings:  g_i = Q_ii + sum_j W_ij x_j in integers (exact);
+//   integer couplings (int8, int16):  g_i = Q_ii + sum_j W_ij x_j in integers (exact);
 //   fp32 couplings:  Q_ii and every W_ij are put on the grid 2^-S (S from
 //                    max(|W|, |Q_ii|) and N, so that no sum can overflow),
 //                    summed exactly in int64, and g_i is the single fp32
@@ -35,17 +35,19 @@ constexpr int kStatesPerWarp = 4;
 constexpr int kWarps = 8;
 constexpr int kStates = kWarps * kStatesPerWarp;
 
-template <bool INT8>
+// Coupling types of the recompute: the da_dtype values (kWInt8, kWFp32, kWInt16).
+template <int K>
 __device__ __forceinline__ long long fixed_of(const void* a, size_t idx, int S)
 {
-    if constexpr (INT8) return (long long)static_cast<const int8_t*>(a)[idx];
+    if constexpr (K == kWInt8) return (long long)static_cast<const int8_t*>(a)[idx];
+    else if constexpr (K == kWInt16) return (long long)static_cast<const int16_t*>(a)[idx];
     else return fixed_of_f32(static_cast<const float*>(a)[idx], S);
 }
 
-template <bool INT8>
+template <int K>
 __device__ __forceinline__ long long fixed_diag(const void* diag, int i, int S)
 {
-    if constexpr (INT8) return (long long)static_cast<const int32_t*>(diag)[i];
+    if constexpr (K != kWFp32) return (long long)static_cast<const int32_t*>(diag)[i];
     else return fixed_of_f32(static_cast<const float*>(diag)[i], S);
 }
 
@@ -78,7 +80,7 @@ __device__ __forceinline__ I128 warp_sum(I128 v)
 
 // Fields of states xs[R][nw] for rows [64 bx, 64 bx + 64); partial energy
 // sums of those rows into part[bx][R] (two 64-bit words each).
-template <bool INT8>
+template <int K>
 __global__ void __launch_bounds__(kWarps * 32) recompute_kernel(const void* __restrict__ Wv,
                                                                 const void* __restrict__ diag, int N, int ldw, int S,
                                                                 const uint32_t* __restrict__ xs, int nw, int R,
@@ -91,8 +93,9 @@ __global__ void __launch_bounds__(kWarps * 32) recompute_kernel(const void* __re
     const int r0 = blockIdx.y * kStates + warp * kStatesPerWarp;
     const int ia = i0 + lane, ib = i0 + 32 + lane;
     long long acc[kStatesPerWarp][2];
-    const long long da_ = ia < N ? fixed_diag<INT8>(diag, ia, S) : 0ll;
-    const long long db_ = ib < N ? fixed_diag<INT8>(diag, ib, S) : 0ll;
+    constexpr bool INT8 = K != kWFp32;   // integer fields and energies
+    const long long da_ = ia < N ? fixed_diag<K>(diag, ia, S) : 0ll;
+    const long long db_ = ib < N ? fixed_diag<K>(diag, ib, S) : 0ll;
 #pragma unroll
     for (int q = 0; q < kStatesPerWarp; ++q) { acc[q][0] = da_; acc[q][1] = db_; }
 
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(kWarps * 32) recompute_kernel(const void* __re
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int i = i0 + sc + c;
-            M[sj][sc + c] = (j < N && i < N) ? fixed_of<INT8>(Wv, (size_t)j * ldw + i, S) : 0ll;
+            M[sj][sc + c] = (j < N && i < N) ? fixed_of<K>(Wv, (size_t)j * ldw + i, S) : 0ll;
         }
         __syncthreads();
 #pragma unroll
@@ -278,8 +281,9 @@ cudaError_t prepare_field_kernels()
     prefer_shared<init_state_kernel<1>>();
     prefer_shared<init_state_kernel<2>>();
     prefer_shared<best_fixup_kernel>();
-    prefer_shared<recompute_kernel<true>>();
-    prefer_shared<recompute_kernel<false>>();
+    prefer_shared<recompute_kernel<kWInt8>>();
+    prefer_shared<recompute_kernel<kWInt16>>();
+    prefer_shared<recompute_kernel<kWFp32>>();
     prefer_shared<energy_kernel<true>>();
     prefer_shared<energy_kernel<false>>();
     return cudaGetLastError();
@@ -346,25 +350,36 @@ cudaError_t launch_energy_sum(bool is_int8, const long long* part, int tiles, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
-                             const uint32_t* xs, int nw, int R, void* hout, int npad,
-                             long long* E, int Estride, cudaStream_t st, long long* scratch)
+cudaError_t launch_recompute_w(int wtype, const void* W, const void* diag, int N, int ldw, int S,
+                               const uint32_t* xs, int nw, int R, void* hout, int npad,
+                               long long* E, int Estride, cudaStream_t st, long long* scratch)
 {
     if (R <= 0) return cudaSuccess;
     const int rows = hout ? std::max(npad, N) : N;
     const int tiles = (rows + kRows - 1) / kRows;
     dim3 grid(tiles, (R + kStates - 1) / kStates);
     I128* part = E ? reinterpret_cast<I128*>(scratch) : nullptr;
-    if (is_int8) {
-        prefer_shared<recompute_kernel<true>>();
-        recompute_kernel<true><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
+    if (wtype == kWInt8) {
+        prefer_shared<recompute_kernel<kWInt8>>();
+        recompute_kernel<kWInt8><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
+    } else if (wtype == kWInt16) {
+        prefer_shared<recompute_kernel<kWInt16>>();
+        recompute_kernel<kWInt16><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
     } else {
-        prefer_shared<recompute_kernel<false>>();
-        recompute_kernel<false><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
+        prefer_shared<recompute_kernel<kWFp32>>();
+        recompute_kernel<kWFp32><<<grid, kWarps * 32, 0, st>>>(W, diag, N, ldw, S, xs, nw, R, hout, npad, part);
     }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess || !E) return err;
-    return launch_energy_sum(is_int8, scratch, tiles, R, S, E, Estride, st);
+    return launch_energy_sum(wtype != kWFp32, scratch, tiles, R, S, E, Estride, st);
+}
+
+cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int N, int ldw, int S,
+                             const uint32_t* xs, int nw, int R, void* hout, int npad,
+                             long long* E, int Estride, cudaStream_t st, long long* scratch)
+{
+    return launch_recompute_w(is_int8 ? kWInt8 : kWFp32, W, diag, N, ldw, S, xs, nw, R, hout, npad, E, Estride, st,
+                              scratch);
 }
 
 }  // namespace da

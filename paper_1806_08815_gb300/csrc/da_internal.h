@@ -105,6 +105,12 @@ cudaError_t launch_recompute(bool is_int8, const void* W, const void* diag, int 
                              const uint32_t* xs, int nw, int R, void* hout, int npad,
                              long long* E, int Estride, cudaStream_t st, long long* scratch);
 
+// The same for couplings of type wtype (kWInt8, kWFp32 or kWInt16; the integer
+// types give int32 fields and int64 energies).
+cudaError_t launch_recompute_w(int wtype, const void* W, const void* diag, int N, int ldw, int S,
+                               const uint32_t* xs, int nw, int R, void* hout, int npad,
+                               long long* E, int Estride, cudaStream_t st, long long* scratch);
+
 // E[r * Estride] from the 128-bit partial sums part[tiles][R] of a recompute:
 // the energy sum / 2^(S+1) (int64, or the fp64 bit pattern of its single
 // rounding for fp32) (da_fields.cu).
@@ -126,7 +132,12 @@ struct TcOperand {
 void tc_digits(int wtype, int N, int* bits, int* limbs);
 cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
                              cudaStream_t st);
-void tc_operand_free(TcOperand* op);
+void tc_operand_free(TcOperand* op);   // for operands from tc_operand_build
+// The same operand built in caller-provided device memory (tc_operand_bytes(wtype,
+// N) bytes, 256-byte aligned), nothing allocated; the caller frees mem.
+size_t tc_operand_bytes(int wtype, int N);
+cudaError_t tc_operand_build_in(int wtype, const void* W, const void* diag, int N, int ldw, int S, void* mem,
+                                TcOperand* op, cudaStream_t st);
 // Workspace for R states expanded to f16 (state_ws of launch_recompute_tc).
 size_t tc_state_bytes(int N, int R);
 // Arguments as launch_recompute (is_int8: integer couplings of either width,
@@ -177,6 +188,7 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st);
 // first use while other kernels run may wait for them.
 cudaError_t prepare_step(int wtype);
 cudaError_t prepare_field_kernels();
+cudaError_t prepare_tc_kernels();   // da_mma.cu: the tensor-core recompute and its operand build
 
 // An SM runs blocks of several kernels at once only under one split of its
 // on-chip memory between L1 and shared memory.  Kernels that run beside the
@@ -227,6 +239,8 @@ void set_last_error(const std::string& msg);
 // fp32, kWInt8AsF32; otherwise W).
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S,
                      const void** Wstep = nullptr);
+// The context's tensor-core operand of W (built by da_create).
+const TcOperand& ctx_tc_operand(const da_ctx* c);
 
 // Fixed-point scale of the fp32 recompute for amax = max(|W_ij|, |diag_i|)
 // and N variables (N + 1 terms per sum).

@@ -381,17 +381,59 @@ size_t tc_state_bytes(int N, int R)
     return rtiles * kchunks * kATile;
 }
 
+// Bytes of the operand's three parts: digit planes, fixed-point diagonal, error flag.
+static void tc_operand_parts(int wtype, int N, size_t* b_bytes, size_t* d_bytes)
+{
+    int bits = 0, limbs = 0;
+    tc_digits(wtype, N, &bits, &limbs);
+    const size_t kchunks = (size_t)(N + kBK - 1) / kBK;
+    const size_t itiles = (size_t)(N + kBN - 1) / kBN;
+    *b_bytes = itiles * kchunks * (size_t)limbs * kBTile;
+    *d_bytes = kchunks * kBK * sizeof(long long);
+}
+
+size_t tc_operand_bytes(int wtype, int N)
+{
+    size_t b = 0, d = 0;
+    tc_operand_parts(wtype, N, &b, &d);
+    return (b + 255) / 256 * 256 + (d + 255) / 256 * 256 + 256;
+}
+
+static cudaError_t tc_operand_fill(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+                                   cudaStream_t st);
+
+cudaError_t tc_operand_build_in(int wtype, const void* W, const void* diag, int N, int ldw, int S, void* mem,
+                                TcOperand* op, cudaStream_t st)
+{
+    size_t b = 0, d = 0;
+    tc_operand_parts(wtype, N, &b, &d);
+    char* m = static_cast<char*>(mem);
+    op->B = m;
+    op->dfix = reinterpret_cast<long long*>(m + (b + 255) / 256 * 256);
+    op->err = reinterpret_cast<int*>(m + (b + 255) / 256 * 256 + (d + 255) / 256 * 256);
+    return tc_operand_fill(wtype, W, diag, N, ldw, S, op, st);
+}
+
 cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
                              cudaStream_t st)
+{
+    size_t b = 0, d = 0;
+    tc_operand_parts(wtype, N, &b, &d);
+    cudaError_t e = dev_malloc(&op->B, b);
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->err), sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->dfix), d);
+    if (e != cudaSuccess) return e;
+    return tc_operand_fill(wtype, W, diag, N, ldw, S, op, st);
+}
+
+// The digit planes and diagonal of W into op's buffers, and the error flag cleared.
+static cudaError_t tc_operand_fill(int wtype, const void* W, const void* diag, int N, int ldw, int S, TcOperand* op,
+                                   cudaStream_t st)
 {
     tc_digits(wtype, N, &op->bits, &op->limbs);
     op->kchunks = (N + kBK - 1) / kBK;
     const int itiles = (N + kBN - 1) / kBN;
-    const size_t bytes = (size_t)itiles * op->kchunks * op->limbs * kBTile;
-    cudaError_t e = dev_malloc(&op->B, bytes);
-    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->err), sizeof(int));
-    if (e == cudaSuccess) e = dev_malloc(reinterpret_cast<void**>(&op->dfix), (size_t)op->kchunks * kBK * sizeof(long long));
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     e = cudaMemsetAsync(op->err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const long long total = (long long)itiles * op->kchunks * kBN * 8;
@@ -399,6 +441,12 @@ cudaError_t tc_operand_build(int wtype, const void* W, const void* diag, int N, 
     const unsigned blocks = (unsigned)((total + tb - 1) / tb);
     const int nd = op->kchunks * kBK;
     __half* B = static_cast<__half*>(op->B);
+    // the request loop builds operands beside running kernels: the carveout of the rest of its kernels
+    prefer_shared<build_digits_kernel<int8_t>>();
+    prefer_shared<build_digits_kernel<int16_t>>();
+    prefer_shared<build_digits_kernel<float>>();
+    prefer_shared<build_dfix_kernel<false>>();
+    prefer_shared<build_dfix_kernel<true>>();
     if (wtype == kWInt8)
         build_digits_kernel<int8_t><<<blocks, tb, 0, st>>>(W, N, ldw, S, op->bits, op->limbs, op->kchunks, B, total);
     else if (wtype == kWInt16)
@@ -418,6 +466,24 @@ void tc_operand_free(TcOperand* op)
     if (op->err) dev_free(op->err);
     if (op->dfix) dev_free(op->dfix);
     *op = TcOperand{};
+}
+
+cudaError_t prepare_tc_kernels()
+{
+    prefer_shared<build_digits_kernel<int8_t>>();
+    prefer_shared<build_digits_kernel<int16_t>>();
+    prefer_shared<build_digits_kernel<float>>();
+    prefer_shared<build_dfix_kernel<false>>();
+    prefer_shared<build_dfix_kernel<true>>();
+    prefer_shared<expand_states_kernel>();
+    prefer_shared<recompute_tc_kernel<false>>();
+    prefer_shared<recompute_tc_kernel<true>>();
+    cudaError_t e = cudaFuncSetAttribute(recompute_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes(kMaxLimbs));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(recompute_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes(2));
+    return e;
 }
 
 cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
@@ -450,6 +516,7 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
     const long long total = (long long)rtiles * op.kchunks * kBM * 8;
     const int tb = 256;
     __half* A = static_cast<__half*>(state_ws);
+    prefer_shared<expand_states_kernel>();
     expand_states_kernel<<<(unsigned)((total + tb - 1) / tb), tb, 0, st>>>(xs, nw, N, R, op.kchunks, A, total);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

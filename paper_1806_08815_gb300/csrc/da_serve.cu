@@ -6,8 +6,9 @@
 // host synchronisation: allocation from the server's memory pool, the upload
 // of Q and the schedule, the instance build, the anneal as chunked step
 // launches (the same kernels and launch shapes as a context; fp32 fields
-// recomputed every recompute_every steps), the exact evaluation of the final
-// and best states, and an event.  Requests run concurrently, each on its own
+// recomputed every recompute_every steps on the tensor cores, from an operand
+// built in the request's own memory), the exact evaluation of the final and
+// best states, and an event.  Requests run concurrently, each on its own
 // stream, so one that arrives while others are on the GPU starts at once on
 // the SMs they leave free (continuous batching at the granularity of kernels).
 //
@@ -74,7 +75,8 @@ enum class ReqState { Queued, Running, Done, Failed };
 struct Req {
     da_job job;
     int N = 0;
-    bool int8 = false;
+    bool integer = false;             // DA_INT8 or DA_INT16: exact fields and energies
+    int dtype = DA_FP32;
     da::StepShape shape;              // launch shape of the step kernel
     da::HostInstance inst;            // checked at submit (ldw, S); W and diag built on the device at admission
     size_t bytes = 0;                 // device bytes charged to the budget
@@ -88,7 +90,9 @@ struct Req {
     char* dmem = nullptr;
     // offsets into dmem
     size_t o_W = 0, o_Wf = 0, o_diag = 0, o_beta = 0, o_h = 0, o_xs = 0, o_sc = 0, o_part = 0, o_eex = 0, o_E = 0,
-           o_flips = 0;
+           o_flips = 0, o_tc = 0, o_tcs = 0;
+    da::TcOperand tc;                 // fp32 requests: the tensor-core operand of W (in dmem)
+    int tc_err = 0;                   // its bounded-wait flag, read back with the results
     int xs_stride = 0;                // words per replica in xs
     // results on the host
     std::vector<double> E;            // [3R]
@@ -159,10 +163,10 @@ void plan_request(Req& q)
     const da::StepShape& sh = q.shape;
     size_t o = 0;
     auto take = [&](size_t b) { size_t at = o; o += al256(b); return at; };
-    // W: fp32 couplings, or the int8 form that the exact final evaluation
-    // reads; int8 requests anneal on the same couplings held as exact fp32 (Wf)
-    q.o_W = take(da::instance_W_bytes(q.N, q.int8 ? DA_INT8 : DA_FP32));
-    if (q.int8) q.o_Wf = take(da::instance_W_bytes(q.N, DA_FP32));
+    // W in the request's coupling type (what the exact final evaluation reads);
+    // int8 requests anneal on the same couplings held as exact fp32 (Wf)
+    q.o_W = take(da::instance_W_bytes(q.N, q.dtype));
+    if (q.dtype == DA_INT8) q.o_Wf = take(da::instance_W_bytes(q.N, DA_FP32));
     q.o_diag = take((size_t)q.N * 4);
     q.o_beta = take((size_t)q.job.steps * 4);
     q.xs_stride = sh.nwords();
@@ -173,6 +177,10 @@ void plan_request(Req& q)
     q.o_eex = take((size_t)2 * R * 8);
     q.o_E = take((size_t)3 * R * 8);
     q.o_flips = take((size_t)R * 8);
+    if (!q.integer) {   // the tensor-core recompute: operand of W, states of up to 2R replicas
+        q.o_tc = take(da::tc_operand_bytes(da::kWFp32, q.N));
+        q.o_tcs = take(da::tc_state_bytes(q.N, 2 * R));
+    }
     q.bytes = o;
     q.qcopy = al256((size_t)q.N * q.N * 4);
 }
@@ -214,7 +222,7 @@ bool admit(da_server* s, Req& q, long long& launches)
     }
     const int R = q.job.replicas;
     void* W = q.dmem + q.o_W;
-    void* Wf = q.int8 ? q.dmem + q.o_Wf : nullptr;
+    void* Wf = q.dtype == DA_INT8 ? q.dmem + q.o_Wf : nullptr;
     void* diag = q.dmem + q.o_diag;
     // W and diag from a transient device copy of Q (the caller keeps Q valid)
     {
@@ -227,12 +235,18 @@ bool admit(da_server* s, Req& q, long long& launches)
             return false;
         }
         bool ok = cu_ok(cudaMemcpyAsync(qd, q.job.Q, qbytes, cudaMemcpyHostToDevice, st), q, "upload Q");
-        ok = ok && cu_ok(da::launch_expand_instance(qd, q.N, q.inst.ldw, q.int8 ? DA_INT8 : DA_FP32, W,
+        ok = ok && cu_ok(da::launch_expand_instance(qd, q.N, q.inst.ldw, q.dtype, W,
                                                     static_cast<float*>(Wf), diag, st),
                          q, "build instance");
         launches += 3;
         da::pool_free_async(qd, st);
         if (!ok || !cu_ok(cudaEventRecord(q.built_ev, st), q, "event")) return false;
+    }
+    if (!q.integer) {
+        if (!cu_ok(da::tc_operand_build_in(da::kWFp32, W, diag, q.N, q.inst.ldw, q.inst.S, q.dmem + q.o_tc, &q.tc, st),
+                   q, "tensor-core operand"))
+            return false;
+        launches += 2;
     }
     if (q.job.steps > 0 &&
         !cu_ok(cudaMemcpyAsync(q.dmem + q.o_beta, q.job.beta, (size_t)q.job.steps * 4, cudaMemcpyHostToDevice, st), q,
@@ -246,13 +260,14 @@ bool admit(da_server* s, Req& q, long long& launches)
     long long* eex = reinterpret_cast<long long*>(q.dmem + q.o_eex);
     double* E = reinterpret_cast<double*>(q.dmem + q.o_E);
     long long* flips = reinterpret_cast<long long*>(q.dmem + q.o_flips);
-    // int8 fields are held as exact fp32, as the steps on Wf expect
-    if (!cu_ok(da::launch_init_state(q.int8, diag, q.N, R, h, sh.npad(), st, q.int8), q, "init")) return false;
+    // int8 fields are held as exact fp32, as the steps on Wf expect; int16 fields are int32
+    if (!cu_ok(da::launch_init_state(q.integer, diag, q.N, R, h, sh.npad(), st, q.dtype == DA_INT8), q, "init"))
+        return false;
     if (!cu_ok(da::launch_zero(xs, (size_t)2 * R * q.xs_stride * 4, st), q, "init")) return false;
     if (!cu_ok(da::launch_zero(sc, (size_t)R * sizeof(da::ReplicaScalars), st), q, "init")) return false;
     launches += 3;
     da::StepParams p;
-    p.W = q.int8 ? Wf : W;
+    p.W = q.dtype == DA_INT8 ? Wf : W;
     p.diag = diag;
     p.N = q.N;
     p.ldw = q.inst.ldw;
@@ -267,30 +282,36 @@ bool admit(da_server* s, Req& q, long long& launches)
     p.inc = q.job.offset_inc;
     p.stop = s->stop + q.slot;
     da::set_seed(p, q.job.seed);
-    const long long T = q.job.steps, P = q.int8 ? 0 : q.job.recompute_every;
+    const long long T = q.job.steps, P = q.integer ? 0 : q.job.recompute_every;
+    const int wstep = q.dtype == DA_INT8 ? da::kWInt8AsF32 : q.dtype;
     for (long long t0 = 0; t0 < T; t0 = p.t1) {
         p.t0 = t0;
         p.t1 = std::min(T, t0 + (1ll << 14));
         if (P > 0) p.t1 = std::min(p.t1, (t0 / P + 1) * P);
-        if (!cu_ok(da::launch_step(q.int8 ? da::kWInt8AsF32 : da::kWFp32, sh, p, false, st), q, "step")) return false;
+        if (!cu_ok(da::launch_step(wstep, sh, p, false, st), q, "step")) return false;
         ++launches;
         if (P > 0 && p.t1 % P == 0) {
-            if (!cu_ok(da::launch_recompute(false, W, diag, q.N, q.inst.ldw, q.inst.S, xs, sh.nwords(), R, h,
-                                            sh.npad(), reinterpret_cast<long long*>(sc),
-                                            (int)(sizeof(da::ReplicaScalars) / 8), st, part),
+            if (!cu_ok(da::launch_recompute_tc(false, q.tc, diag, q.N, q.inst.S, xs, sh.nwords(), R, h, sh.npad(),
+                                               reinterpret_cast<long long*>(sc), (int)(sizeof(da::ReplicaScalars) / 8),
+                                               st, part, q.dmem + q.o_tcs),
                        q, "recompute"))
                 return false;
-            launches += 2;
+            launches += 3;
         }
     }
-    if (!cu_ok(da::launch_best_fixup(R, sc, q.int8, xs, xs + (size_t)R * q.xs_stride, q.xs_stride, st), q, "fixup"))
+    if (!cu_ok(da::launch_best_fixup(R, sc, q.integer, xs, xs + (size_t)R * q.xs_stride, q.xs_stride, st), q,
+               "fixup"))
         return false;
-    if (!cu_ok(da::launch_recompute(q.int8, W, diag, q.N, q.inst.ldw, q.inst.S, xs, sh.nwords(), 2 * R, nullptr,
-                                    sh.npad(), eex, 1, st, part),
-               q, "evaluate"))
-        return false;
+    const bool ev_ok =
+        q.integer ? cu_ok(da::launch_recompute_w(q.dtype, W, diag, q.N, q.inst.ldw, q.inst.S, xs, sh.nwords(), 2 * R,
+                                                 nullptr, sh.npad(), eex, 1, st, part),
+                          q, "evaluate")
+                  : cu_ok(da::launch_recompute_tc(false, q.tc, diag, q.N, q.inst.S, xs, sh.nwords(), 2 * R, nullptr,
+                                                  sh.npad(), eex, 1, st, part, q.dmem + q.o_tcs),
+                          q, "evaluate");
+    if (!ev_ok) return false;
     da::prefer_shared<da::serve_finalize_kernel>();
-    da::serve_finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(q.int8, R, sc, eex, E, flips);
+    da::serve_finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(q.integer, R, sc, eex, E, flips);
     if (!cu_ok(cudaGetLastError(), q, "finalize")) return false;
     launches += 4;
     return cu_ok(cudaEventRecord(q.done_ev, st), q, "event");
@@ -338,7 +359,16 @@ bool finish(Req& q)
     ok = ok && cu_ok(cudaMemcpyAsync(q.flips.data(), q.dmem + q.o_flips, q.flips.size() * 8, cudaMemcpyDeviceToHost,
                                      st),
                      q, "results");
-    return ok && cu_ok(cudaStreamSynchronize(st), q, "results");
+    q.tc_err = 0;
+    if (!q.integer)
+        ok = ok && cu_ok(cudaMemcpyAsync(&q.tc_err, q.tc.err, sizeof(int), cudaMemcpyDeviceToHost, st), q, "results");
+    ok = ok && cu_ok(cudaStreamSynchronize(st), q, "results");
+    if (ok && q.tc_err) {
+        q.err = DA_ETIMEOUT;
+        q.msg = "a bounded wait inside the tensor-core recompute gave up; the results are invalid";
+        return false;
+    }
+    return ok;
 }
 
 void worker_loop(da_server* s)
@@ -466,7 +496,9 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
     for (int i = max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);
     cudaError_t e = da::prepare_step(da::kWFp32);
     if (e == cudaSuccess) e = da::prepare_step(da::kWInt8AsF32);
+    if (e == cudaSuccess) e = da::prepare_step(da::kWInt16);
     if (e == cudaSuccess) e = da::prepare_field_kernels();
+    if (e == cudaSuccess) e = da::prepare_tc_kernels();
     if (e == cudaSuccess) {
         da::prefer_shared<da::serve_finalize_kernel>();
         e = cudaGetLastError();
@@ -505,8 +537,8 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     if (!s || !job || !out) return sfail(DA_EINVAL, "null argument");
     *out = nullptr;
     if (!job->Q || job->N < 1 || job->N > 8192) return sfail(DA_EINVAL, "need Q and 1 <= N <= 8192");
-    if (job->dtype != DA_INT8 && job->dtype != DA_FP32)
-        return sfail(DA_EINVAL, "the request loop takes DA_INT8 or DA_FP32 jobs");
+    if (job->dtype != DA_INT8 && job->dtype != DA_FP32 && job->dtype != DA_INT16)
+        return sfail(DA_EINVAL, "unknown dtype");
     if (job->steps < 0 || job->steps >= (1ll << 32) || (job->steps > 0 && !job->beta))
         return sfail(DA_EINVAL, "bad schedule");
     if (job->steps > 0 && !da::schedule_ok(job->beta, job->steps))
@@ -517,7 +549,8 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     auto q = std::make_shared<Req>();
     q->job = *job;
     q->N = (int)job->N;
-    q->int8 = job->dtype == DA_INT8;
+    q->dtype = (int)job->dtype;
+    q->integer = job->dtype != DA_FP32;
     std::string why;
     if (!da::build_instance(job->Q, q->N, job->dtype, q->inst, why)) return sfail(DA_EINVAL, why);
     // a context's launch shape: measured on a mix of concurrent requests it

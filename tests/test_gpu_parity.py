@@ -456,14 +456,20 @@ def test_batched_configurations_match_single_instances(da, inst, staging, wpb):
     stage (V = 4 and V = 8 classes up to N = 221) and that do not, ragged replica counts."""
     rng = np.random.default_rng(7)
     jobs, refs = [], []
-    sizes = [64, 100, 128, 200, 221, 256, 40, 1024]
+    sizes = [64, 100, 128, 200, 221, 256, 40, 1024, 90, 520]
     for n, N in enumerate(sizes):
         q = inst.sk_bimodal(N, 50 + n) if n % 2 == 0 else inst.sk_gaussian(N, 50 + n)
         T = int(rng.integers(150, 600))
         beta = inst.beta_linear(0.1, 3.0, T)
-        ctx = da.da_create(q.Q)
+        if n >= 8:   # the DA's 16-bit couplers (da_quantize), beta divided by the scale
+            Qi, scale = da.binding.da_quantize(inst.sk_gaussian(N, 50 + n).Q)
+            ctx = da.da_create(Qi, da.DA_INT16)
+            beta = (beta / scale).astype(np.float32)
+            P = 0
+        else:
+            ctx = da.da_create(q.Q)
+            P = 0 if q.bimodal else 100
         R = int(rng.integers(3, 23))
-        P = 0 if q.bimodal else 100
         jobs.append(dict(ctx=ctx, beta=beta, offset_inc=0.5, replicas=R, seed=300 + n, recompute_every=P,
                          trace=True))
         refs.append(da.da_anneal(ctx, beta, 0.5, R, 300 + n, recompute_every=P, trace=True))

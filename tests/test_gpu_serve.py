@@ -115,3 +115,30 @@ def test_degenerate_and_largest_requests(da):
     srv.close()
     for j, o in zip(jobs, outs):
         _same(o, _alone(da, j))
+
+
+def test_fixed_point_requests_in_the_mix(da):
+    """DA_INT16 requests (the DA's 16-bit couplers: Gaussian instances scaled by da_quantize,
+    beta divided by the scale) run in the request loop beside int8 and fp32 requests, and each
+    equals da_anneal on a DA_INT16 context bit for bit."""
+    from paper_1806_08815_gb300 import instances as inst
+    jobs = []
+    for n, N in enumerate([96, 700, 1300, 3000]):
+        q = inst.sk_gaussian(N, 40 + n)
+        Qi, scale = da.da_quantize(q.Q)
+        beta = (inst.beta_linear(0.1, 6.0, 500 + 100 * n) / scale).astype(np.float32)
+        jobs.append(dict(Q=Qi, beta=beta, inc=0.0 if n % 2 else 2000.0, R=5 + 3 * n, seed=70 + n))
+    mix = _jobs(inst)[:3]
+    srv = da.Server(8 << 30, 64)
+    reqs = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], 0, dtype=da.DA_INT16) for j in jobs]
+    reqs_mix = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], j["P"]) for j in mix]
+    outs = [da.da_poll(r, 60_000_000) for r in reqs]
+    outs_mix = [da.da_poll(r, 60_000_000) for r in reqs_mix]
+    srv.close()
+    for j, o in zip(jobs, outs):
+        ctx = da.da_create(j["Q"], da.DA_INT16)
+        ref = da.da_anneal(ctx, j["beta"], j["inc"], j["R"], j["seed"])
+        _same(o, ref)
+        assert np.all(o["max_drift"] == 0)
+    for j, o in zip(mix, outs_mix):
+        _same(o, _alone(da, j))
