@@ -67,3 +67,13 @@ def test_tts99_closed_form():
     # every run a hit: theta = (r + 1/2) / (r + 1) > 0.99 for r >= 50, R99 clamps to one run
     t = bench.tts99(np.full(100, -3.0), tau_run=0.5)
     assert t["R99"] == 1.0 and t["tts99_s"] == 0.5
+
+
+def test_recorded_step_counts_match_the_kernel_source():
+    """The instruction count and DRAM traffic bench.py reports for the step kernel come from an ncu
+    capture of one kernel source; a change to that source must come with a new capture (this
+    test fails until the recorded hash is updated with the new counts)."""
+    import bench
+    assert bench.step_source_sha() == bench.STEP_TRAFFIC["source_sha256_16"], (
+        "the step kernel changed since its ncu counts were recorded: capture it again and update "
+        "STEP_INST_PER_REPLICA_STEP and STEP_TRAFFIC")
