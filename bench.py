@@ -351,9 +351,10 @@ def run_fixed_point(da, instances, R=1024, T=200_000):
             "relative_gap_of_means": float((Ei.mean() - Ef.mean()) / abs(Ef.mean()))}
 
 
-def _serve_stream(da, pool, betas, picks, gaps, R, T, budget):
+def _serve_stream(da, pool, betas, picks, gaps, R, T, budget, resident_max_n=0):
     """Submit requests pool[picks[k]] at the inter-arrival gaps, wait for all; per-request results."""
     srv = da.Server(budget, 1024)
+    srv.resident(resident_max_n)
     warm = da.da_submit(srv, pool[0].Q, betas[pool[0].bimodal][:100], 0.0, 4, 0)
     da.da_poll(warm, 60_000_000)
     n_req = len(picks)
@@ -382,7 +383,7 @@ def _serve_stream(da, pool, betas, picks, gaps, R, T, budget):
 
 
 def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30, sustained_req=512,
-               sustained_rate=40.0, plain_max=6):
+               sustained_rate=40.0, plain_max=6, resident_max_n=0):
     """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
     [256, 8192], half bimodal / half Gaussian, R replicas, T steps, HBM budget 120 GB.  Beside the
     burst at `rate`, a longer stream at a rate the GPU sustains, and the plain one-launch-per-step
@@ -397,7 +398,7 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
     betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
     picks = rng.integers(0, len(pool), n_req)
     gaps = rng.exponential(1.0 / rate, n_req)
-    res, makespan, stats = _serve_stream(da, pool, betas, picks, gaps, R, T, budget)
+    res, makespan, stats = _serve_stream(da, pool, betas, picks, gaps, R, T, budget, resident_max_n)
     trials = sum(R * T * pool[i].N for i in picks)
     lat = np.array([o["latency_s"] for o in res])
     out = {"workload": f"{n_req} requests, Poisson {rate:.0f} req/s, N log-uniform 256-8192 (pool of 24 "
@@ -405,14 +406,15 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
                        f"{budget >> 30} GB",
            "value": trials / makespan, "unit": UNIT, "makespan_s": makespan,
            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-           "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"]}
+           "mean_latency_s": float(lat.mean()), "kernel_launches": stats["kernel_launches"],
+           "resident_max_n": resident_max_n}
     if sustained_req < 1:
         return out
     # a longer stream at a rate the GPU sustains (the burst above is beyond one GPU's throughput, so
     # its latencies are mostly queueing)
     picks2 = rng.integers(0, len(pool), sustained_req)
     gaps2 = rng.exponential(1.0 / sustained_rate, sustained_req)
-    res2, makespan2, _ = _serve_stream(da, pool, betas, picks2, gaps2, R, T, budget)
+    res2, makespan2, _ = _serve_stream(da, pool, betas, picks2, gaps2, R, T, budget, resident_max_n)
     lat2 = np.array([o["latency_s"] for o in res2])
     out["sustained"] = {"requests": sustained_req, "rate_req_s": sustained_rate,
                         "value": sum(R * T * pool[i].N for i in picks2) / makespan2, "unit": UNIT,

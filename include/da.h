@@ -332,6 +332,15 @@ void da_req_free(da_req* req);
  * Errors: DA_EINVAL (null request). */
 da_status da_cancel(da_req* req);
 
+/* Requests of at most max_n variables (0 <= max_n <= 1024) submitted from now
+ * on run resident: the whole anneal is one launch in which each replica's warp
+ * keeps its state in registers from the first step to the last (fp32 fields
+ * recomputed exactly by the warp itself every recompute_every steps; a
+ * cancelled request leaves at its next multiple of 1024 steps).  Larger
+ * requests, and all of them with max_n = 0, run as chunked step launches.
+ * Results are the same either way.  Errors: DA_EINVAL. */
+da_status da_server_resident(da_server* srv, int32_t max_n);
+
 /* Requests completed, kernels queued so far (all requests), device bytes in use. */
 da_status da_server_stats(da_server* srv, int64_t* completed, int64_t* kernel_launches, int64_t* bytes_in_use);
 

@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
     L.da_diag_live_allocations.restype = ctypes.c_int
     L.da_server_destroy.argtypes = [_P]
     L.da_server_destroy.restype = None
+    L.da_server_resident.argtypes = [_P, i32]
+    L.da_server_resident.restype = ctypes.c_int
     L.da_server_stats.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     for name in ("da_server_create", "da_submit", "da_poll", "da_server_stats"):
         getattr(L, name).restype = ctypes.c_int
@@ -486,6 +488,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def resident(self, max_n: int) -> None:
+        """Requests of at most max_n variables run as one resident launch (0: all chunked)."""
+        _check(lib().da_server_resident(self.handle, int(max_n)))
 
     def stats(self):
         a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -32,22 +32,6 @@
 
 namespace da {
 
-struct BatchItemDev {
-    const void* W;
-    const void* diag;
-    const float* beta;
-    uint32_t* xs;         // [2R][nw]: final states, then best states
-    ReplicaScalars* sc;   // [R]
-    int* trace;           // [R][T] or null
-    long long T;
-    long long recompute_every;
-    long long unit0;      // first unit of this item in its class
-    uint64_t seed;
-    int N, ldw, S, R;
-    float inc;
-    int pad;
-};
-
 struct BatchClassParams {
     const BatchItemDev* items;
     int n_items;
@@ -97,6 +81,7 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
         if (t + 1 < T) beta_next = it.beta[t + 1];
         const int k = rp.template step<false>(t, t + 1 < T, beta, it.inc, keys);
         if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
+        if (it.stop && (t & 1023) == 1023 && *reinterpret_cast<const volatile int*>(it.stop)) break;
         if constexpr (std::is_same<Tw, float>::value) {
             if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
                 rp.recompute(static_cast<const float*>(it.diag), it.S);
@@ -732,3 +717,27 @@ extern "C" da_status da_batch_force(int32_t staging, int32_t warps_per_block)
     da::g_force_wpb = warps_per_block;
     return DA_OK;
 }
+
+namespace da {
+
+cudaError_t launch_resident_anneal(int wk, int V, const BatchItemDev* item_dev, unsigned long long* head_dev, int R,
+                                   cudaStream_t st)
+{
+    BatchKernel k = kernel_for(wk, V);
+    if (!k) return cudaErrorInvalidValue;
+    prefer_shared_fn(reinterpret_cast<const void*>(k));
+    cudaError_t e = cudaMemsetAsync(head_dev, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    BatchClassParams bp{item_dev, 1, R, head_dev, 0, nullptr, 0, 0};
+    k<<<R, 32, 0, st>>>(bp);   // one warp per replica, each SM it lands on shared with other requests
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_resident_kernels()
+{
+    for (int wk : {kWInt8AsF32, kWFp32, kWInt16})
+        for (int V : {4, 8, 16, 32}) prefer_shared_fn(reinterpret_cast<const void*>(kernel_for(wk, V)));
+    return cudaGetLastError();
+}
+
+}  // namespace da

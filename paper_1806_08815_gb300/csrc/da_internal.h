@@ -230,6 +230,42 @@ cudaError_t dev_free(void* p);
 cudaError_t pool_malloc_async(void** p, size_t bytes, cudaMemPool_t pool, cudaStream_t st);
 cudaError_t pool_free_async(void* p, cudaStream_t st);
 
+// One instance of a batched launch as its kernel sees it (da_batch.cu); the
+// request loop uses one item for a request that runs resident.
+struct BatchItemDev {
+    const void* W;          // couplings in the step kernel's form
+    const void* diag;
+    const float* beta;
+    uint32_t* xs;           // [2R][nw]: final states, then best states
+    ReplicaScalars* sc;     // [R]
+    int* trace;             // [R][T] or null
+    long long T;
+    long long recompute_every;
+    long long unit0;        // first unit of this item in its class
+    uint64_t seed;
+    int N, ldw, S, R;
+    float inc;
+    int pad;
+    const int* stop;        // optional (host-mapped): set, the anneal leaves at its next multiple of 1024 steps
+};
+
+// A whole anneal of R replicas of one item by one launch of the batched
+// kernel (da_batch.cu): one warp per replica keeps its state in registers from
+// the first step to the last (fp32 fields recomputed by the warp itself every
+// recompute_every steps); writes xs and sc as the chunked launches do.
+// wk: the step coupling form (kWInt8AsF32, kWFp32, kWInt16), V: lanes' width.
+cudaError_t launch_resident_anneal(int wk, int V, const BatchItemDev* item_dev, unsigned long long* head_dev, int R,
+                                   cudaStream_t st);
+cudaError_t prepare_resident_kernels();
+
+// The carveout of prefer_shared for a kernel given by address.
+inline void prefer_shared_fn(const void* k)
+{
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
+        cudaGetLastError();
+}
+
 // Error text returned by da_last_error() on the calling thread (da_api.cu).
 void set_last_error(const std::string& msg);
 

@@ -24,6 +24,7 @@
 // return at once (a host-mapped stop flag per request slot that every step
 // launch reads when it starts).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -90,7 +91,9 @@ struct Req {
     char* dmem = nullptr;
     // offsets into dmem
     size_t o_W = 0, o_Wf = 0, o_diag = 0, o_beta = 0, o_h = 0, o_xs = 0, o_sc = 0, o_part = 0, o_eex = 0, o_E = 0,
-           o_flips = 0, o_tc = 0, o_tcs = 0;
+           o_flips = 0, o_tc = 0, o_tcs = 0, o_item = 0;
+    bool resident = false;            // the whole anneal in one launch, replica state in registers
+    da::BatchItemDev item{};          // its descriptor (copied to dmem + o_item)
     da::TcOperand tc;                 // fp32 requests: the tensor-core operand of W (in dmem)
     int tc_err = 0;                   // its bounded-wait flag, read back with the results
     int xs_stride = 0;                // words per replica in xs
@@ -118,6 +121,7 @@ struct da_server {
     // once (a request is admitted alone whatever its size)
     long long warps = 0, warp_cap = 0;
     int max_slots = 0;
+    std::atomic<int> resident_max_n{0};   // requests of at most this many variables run resident
     std::vector<int> free_slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -177,6 +181,7 @@ void plan_request(Req& q)
     q.o_eex = take((size_t)2 * R * 8);
     q.o_E = take((size_t)3 * R * 8);
     q.o_flips = take((size_t)R * 8);
+    if (q.resident) q.o_item = take(sizeof(da::BatchItemDev) + 16);   // descriptor, then the work counter
     if (!q.integer) {   // the tensor-core recompute: operand of W, states of up to 2R replicas
         q.o_tc = take(da::tc_operand_bytes(da::kWFp32, q.N));
         q.o_tcs = take(da::tc_state_bytes(q.N, 2 * R));
@@ -284,7 +289,32 @@ bool admit(da_server* s, Req& q, long long& launches)
     da::set_seed(p, q.job.seed);
     const long long T = q.job.steps, P = q.integer ? 0 : q.job.recompute_every;
     const int wstep = q.dtype == DA_INT8 ? da::kWInt8AsF32 : q.dtype;
-    for (long long t0 = 0; t0 < T; t0 = p.t1) {
+    if (q.resident && T > 0) {
+        da::BatchItemDev& d = q.item;
+        d.W = p.W;
+        d.diag = diag;
+        d.beta = p.beta;
+        d.xs = xs;
+        d.sc = sc;
+        d.trace = nullptr;
+        d.T = T;
+        d.recompute_every = P;
+        d.unit0 = 0;
+        d.seed = q.job.seed;
+        d.N = q.N;
+        d.ldw = q.inst.ldw;
+        d.S = q.inst.S;
+        d.R = R;
+        d.inc = q.job.offset_inc;
+        d.stop = s->stop + q.slot;
+        auto* item_dev = reinterpret_cast<da::BatchItemDev*>(q.dmem + q.o_item);
+        auto* head_dev = reinterpret_cast<unsigned long long*>(q.dmem + q.o_item + sizeof(da::BatchItemDev));
+        if (!cu_ok(cudaMemcpyAsync(item_dev, &d, sizeof(d), cudaMemcpyHostToDevice, st), q, "descriptor")) return false;
+        if (!cu_ok(da::launch_resident_anneal(wstep, sh.V, item_dev, head_dev, R, st), q, "resident anneal"))
+            return false;
+        launches += 2;
+    }
+    for (long long t0 = 0; t0 < T && !q.resident; t0 = p.t1) {
         p.t0 = t0;
         p.t1 = std::min(T, t0 + (1ll << 14));
         if (P > 0) p.t1 = std::min(p.t1, (t0 / P + 1) * P);
@@ -499,6 +529,7 @@ da_status da_server_create(int64_t hbm_budget_bytes, int32_t max_requests, da_se
     if (e == cudaSuccess) e = da::prepare_step(da::kWInt16);
     if (e == cudaSuccess) e = da::prepare_field_kernels();
     if (e == cudaSuccess) e = da::prepare_tc_kernels();
+    if (e == cudaSuccess) e = da::prepare_resident_kernels();
     if (e == cudaSuccess) {
         da::prefer_shared<da::serve_finalize_kernel>();
         e = cudaGetLastError();
@@ -556,6 +587,7 @@ da_status da_submit(da_server* s, const da_job* job, da_req** out)
     // a context's launch shape: measured on a mix of concurrent requests it
     // gives more trials per second than the fewest warps per replica
     q->shape = da::default_shape(q->N, job->replicas);
+    q->resident = q->N <= s->resident_max_n && q->shape.G == 1;
     plan_request(*q);
     if ((int64_t)peak_bytes(*q) > s->budget)
         return sfail(DA_EBUDGET, "request needs " + std::to_string(peak_bytes(*q)) +
@@ -628,6 +660,13 @@ da_status da_cancel(da_req* req)
     }
     s->cv_done.notify_all();
     s->cv_work.notify_all();
+    return DA_OK;
+}
+
+da_status da_server_resident(da_server* s, int32_t max_n)
+{
+    if (!s || max_n < 0 || max_n > 1024) return sfail(DA_EINVAL, "need a server and 0 <= max_n <= 1024");
+    s->resident_max_n = max_n;
     return DA_OK;
 }
 

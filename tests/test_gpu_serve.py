@@ -142,3 +142,27 @@ def test_fixed_point_requests_in_the_mix(da):
         assert np.all(o["max_drift"] == 0)
     for j, o in zip(mix, outs_mix):
         _same(o, _alone(da, j))
+
+
+def test_resident_requests_equal_chunked_ones(da):
+    """Requests of at most 1024 variables run resident (one launch for the whole anneal, replica
+    state in registers, fp32 fields recomputed by each warp) beside larger chunked ones: every
+    result equals da_anneal bit for bit; a cancelled resident request stops within 1024 steps."""
+    import time
+    from paper_1806_08815_gb300 import instances as inst
+    jobs = _jobs(inst)
+    srv = da.Server(8 << 30, 64)
+    srv.resident(1024)
+    reqs = [da.da_submit(srv, j["Q"], j["beta"], j["inc"], j["R"], j["seed"], j["P"]) for j in jobs]
+    outs = [da.da_poll(r, 60_000_000) for r in reqs]
+    for j, o in zip(jobs, outs):
+        _same(o, _alone(da, j))
+    q = inst.sk_bimodal(1024, 8)
+    long_req = da.da_submit(srv, q.Q, np.full(3_000_000, 1.0, np.float32), 1.0, 32, 1)
+    time.sleep(0.2)
+    t0 = time.perf_counter()
+    da.da_cancel(long_req)
+    with pytest.raises(da.DAError) as e:
+        da.da_poll(long_req, 60_000_000)
+    assert e.value.status == 8 and time.perf_counter() - t0 < 1.5
+    srv.close()
