@@ -243,12 +243,13 @@ typedef struct da_batch_item {
  * all launches and the exact final evaluation form one CUDA graph.  Each item's
  * results are identical to da_anneal on that item alone (the random numbers are
  * keyed by the item's seed and replica index).  Each class's configuration is
- * chosen by an autotuner that times short probes (256 steps) of the class's own
+ * chosen by an autotuner that times short probes (1024 steps) of the class's own
  * units once per process, device and class: warps per block (1, 2, 4), and,
  * where the class's largest instance fits (N x 32V x 4 bytes <= 227 KB, V <= 8),
  * W staged in shared memory, where each block takes a group of replicas of one
  * instance (2, 4, 8 or 16, one per warp), copies that instance's W once and
- * reads every row from there instead of from L2.  *elapsed_s receives the
+ * reads every row from there instead of from L2 (taken only when its probe is
+ * more than 3 % faster than the best L2 one).  *elapsed_s receives the
  * device time of the graph.  Errors: DA_EINVAL (bad item, N > 1024), DA_ENOMEM,
  * DA_ECUDA. */
 da_status da_batch_anneal(const da_batch_item* items, int32_t n, double* elapsed_s);

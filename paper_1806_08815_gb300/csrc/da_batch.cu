@@ -245,6 +245,9 @@ std::map<std::tuple<int, int, int, bool, int>, BatchConfig> g_tune_cache;
 std::map<std::tuple<int, int, int, bool, int>, std::string> g_tune_log;   // the probes behind each entry
 thread_local std::string g_batch_desc;
 
+// Steps per unit of a tuner probe.
+constexpr long long kProbeSteps = 1024;
+
 // Largest dynamic shared memory a block may ask for on sm_100-class GPUs.
 constexpr size_t kMaxStagedBytes = 227u * 1024u;
 
@@ -353,7 +356,8 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
     if (c.can_stage())
         for (int wpb : {2, 4, 8, 16}) cands.push_back(BatchConfig{true, wpb});
     BatchConfig best = cands.front();
-    float best_ms = 1e30f;
+    float best_l2 = 1e30f, best_staged = 1e30f;
+    BatchConfig cfg_l2 = cands.front(), cfg_staged = cands.front();
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -363,7 +367,7 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
     for (const BatchConfig& cfg : cands) {
         cudaMemsetAsync(c.head, 0, 8, st);
         cudaEventRecord(e0, st);
-        cudaError_t le = launch_class(c, reps, cfg, units, 256, sms, st, true);
+        cudaError_t le = launch_class(c, reps, cfg, units, kProbeSteps, sms, st, true);
         cudaEventRecord(e1, st);
         if (le == cudaSuccess) le = cudaStreamSynchronize(st);
         if (le != cudaSuccess) {
@@ -376,14 +380,22 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
         cudaEventElapsedTime(&ms, e0, e1);
         log += std::string(log.empty() ? "" : ", ") + (cfg.smem ? "smem" : "l2") + "x" +
                std::to_string(cfg.warps_per_block) + " " + std::to_string(ms).substr(0, 6) + " ms";
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = cfg;
+        if (!cfg.smem && ms < best_l2) {
+            best_l2 = ms;
+            cfg_l2 = cfg;
+        }
+        if (cfg.smem && ms < best_staged) {
+            best_staged = ms;
+            cfg_staged = cfg;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c.probes = "probes (" + std::to_string(units) + " replicas x 256 steps): " + log;
+    // staging is taken only when its probe beats the best L2 configuration by more than the
+    // run-to-run spread of these probes (3 %)
+    if (best_l2 < 1e30f) best = cfg_l2;
+    if (best_staged < 0.97f * best_l2) best = cfg_staged;
+    c.probes = "probes (" + std::to_string(units) + " replicas x " + std::to_string(kProbeSteps) + " steps): " + log;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best;
     g_tune_log[key] = c.probes;

@@ -175,3 +175,30 @@ def test_cancel_queued_and_running_requests(da):
     da.da_cancel(done)
     assert np.array_equal(r2["best_E"], ref["best_E"])
     srv.close()
+
+
+def test_batched_launch_allocation_failure(da):
+    """The batched launch's workspace cannot be allocated: DA_ENOMEM, nothing left behind, and
+    the next launch gives each item its da_anneal results."""
+    from paper_1806_08815_gb300 import instances
+    q1, q2 = instances.sk_bimodal(100, 1), instances.sk_gaussian(300, 2)
+    beta = instances.beta_linear(0.1, 3.0, 300)
+    c1, c2 = da.da_create(q1.Q), da.da_create(q2.Q)
+    jobs = [dict(ctx=c1, beta=beta, offset_inc=0.5, replicas=8, seed=3),
+            dict(ctx=c2, beta=beta, offset_inc=0.0, replicas=5, seed=4, recompute_every=64)]
+    base = _live(da)
+    da.da_diag_fail_alloc(0, 1)
+    with pytest.raises(da.DAError) as e:
+        da.da_batch_anneal(jobs)
+    assert e.value.status == 2
+    now = _live(da)
+    assert now["count"] == base["count"] and now["bytes"] == base["bytes"]
+    da.da_diag_fail_alloc(0, 0)
+    outs, _ = da.da_batch_anneal(jobs)
+    for j, o in zip(jobs, outs):
+        ref = da.da_anneal(j["ctx"], beta, j["offset_inc"], j["replicas"], j["seed"],
+                           recompute_every=j.get("recompute_every", 0))
+        for key in ("final_E", "best_E", "final_x", "best_x", "flips"):
+            assert np.array_equal(o[key], ref[key]), key
+    da.da_destroy(c1)
+    da.da_destroy(c2)
