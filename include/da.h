@@ -204,6 +204,37 @@ da_status da_set_draw_warp(da_ctx* ctx, int32_t on);
 da_status da_anneal(da_ctx* ctx, const float* beta_schedule, int64_t steps, float offset_inc,
                     int32_t replicas, uint64_t seed, int64_t recompute_every, da_result* out);
 
+/* The state of R replicas between two segments of an anneal (host arrays,
+ * caller-allocated; written by da_anneal_segment, read back by the next one).
+ * The paper has no counterpart (its runs go from x = 0 to the end); it makes a
+ * long anneal resumable. */
+typedef struct da_checkpoint {
+    uint32_t* x;       /* [R * da_words(N)] current states */
+    uint32_t* best_x;  /* [R * da_words(N)] lowest-energy states seen */
+    void* fields;      /* [R * N] effective fields g_i = Q_ii + sum_j W_ij x_j as the anneal
+                          holds them: int32_t for DA_INT8 and DA_INT16, float for DA_FP32
+                          (with its fp32 rounding since the last recompute) */
+    int64_t* scalars;  /* [R * 4] per replica: tracked energy, best tracked energy (int64
+                          for integer couplings, fp64 bit patterns for DA_FP32), accepted
+                          flips, steps without an accepted flip (E_off = that count * inc) */
+} da_checkpoint;
+
+/* Steps [t0, t1) of an anneal of `total_steps` steps (Algorithm 2), from the
+ * checkpoint `in` (NULL: from x = 0, then t0 must be 0), leaving the state after
+ * step t1 in `out` (may be NULL) and, in `res` (may be NULL; no trace), the
+ * results the anneal would report if it ended after step t1.  The random
+ * numbers are keyed by the absolute step and the fp32 recompute falls on
+ * absolute multiples of recompute_every, so running [0, T) in segments gives
+ * exactly the results of da_anneal over [0, T) with the same arguments.
+ *   beta  host, [total_steps] the whole schedule (entries [0, t1) are read).
+ * `in` must come from da_anneal_segment on a context with the same instance
+ * and the same replica count.  Blocking.  Errors: DA_EINVAL (0 <= t0 <= t1 <=
+ * total_steps < 2^32 violated, in == NULL with t0 > 0, a trace requested, ...),
+ * DA_ENOMEM, DA_ECUDA, DA_ETIMEOUT. */
+da_status da_anneal_segment(da_ctx* ctx, const float* beta, int64_t total_steps, int64_t t0, int64_t t1,
+                            float offset_inc, int32_t replicas, uint64_t seed, int64_t recompute_every,
+                            const da_checkpoint* in, da_checkpoint* out, da_result* res);
+
 /* As da_anneal, with the schedule and every output in device memory, queued
  * on `stream` (a cudaStream_t; NULL = the legacy default stream) and
  * returning without waiting.  The device schedule is not inspected: its

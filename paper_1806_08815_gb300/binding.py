@@ -32,6 +32,10 @@ class DAError(RuntimeError):
 _P = ctypes.c_void_p
 
 
+class da_checkpoint(ctypes.Structure):
+    _fields_ = [("x", _P), ("best_x", _P), ("fields", _P), ("scalars", _P)]
+
+
 class da_result(ctypes.Structure):
     _fields_ = [("final_E", _P), ("best_E", _P), ("final_x", _P), ("best_x", _P),
                 ("max_drift", _P), ("flips", _P), ("trace", _P), ("elapsed_s", ctypes.c_double)]
@@ -116,6 +120,9 @@ def lib() -> ctypes.CDLL:
         getattr(L, name).restype = ctypes.c_int
     L.da_batch_anneal.argtypes = [ctypes.POINTER(da_batch_item), i32, ctypes.POINTER(ctypes.c_double)]
     L.da_batch_anneal.restype = ctypes.c_int
+    L.da_anneal_segment.argtypes = [_P, _P, i64, i64, i64, f32, i32, u64, i64, ctypes.POINTER(da_checkpoint),
+                                    ctypes.POINTER(da_checkpoint), ctypes.POINTER(da_result)]
+    L.da_anneal_segment.restype = ctypes.c_int
     L.da_tune_shape.argtypes = [_P, i32, i64] + [ctypes.POINTER(i32)] * 4
     L.da_tune_shape.restype = ctypes.c_int
     L.da_batch_describe.argtypes = [ctypes.c_char_p, i64]
@@ -244,6 +251,32 @@ def da_anneal_plain(ctx: Context, beta: np.ndarray, offset_inc: float, replicas:
                                  ctypes.byref(res)))
     out["elapsed_s"] = res.elapsed_s
     return out
+
+
+def da_anneal_segment(ctx: Context, beta: np.ndarray, t0: int, t1: int, offset_inc: float, replicas: int,
+                      seed: int, recompute_every: int = 0, checkpoint: dict | None = None):
+    """Steps [t0, t1) of an anneal over the whole schedule `beta`, from `checkpoint` (None: from
+    x = 0, t0 = 0).  Returns (results as da_anneal would give after step t1, checkpoint)."""
+    b = np.ascontiguousarray(beta, dtype=np.float32)
+    R, W, N = int(replicas), da_words(ctx.N), ctx.N
+    out = dict(final_E=np.zeros(R), best_E=np.zeros(R), final_x=np.zeros((R, W), np.uint32),
+               best_x=np.zeros((R, W), np.uint32), max_drift=np.zeros(R), flips=np.zeros(R, np.int64))
+    res = da_result(*(_ptr(out.get(k)) for k in ("final_E", "best_E", "final_x", "best_x", "max_drift",
+                                                  "flips", "trace")), 0.0)
+    ck = dict(x=np.zeros((R, W), np.uint32), best_x=np.zeros((R, W), np.uint32),
+              fields=np.zeros((R, N), np.float32 if ctx.dtype == DA_FP32 else np.int32),
+              scalars=np.zeros((R, 4), np.int64))
+    ck_out = da_checkpoint(_ptr(ck["x"]), _ptr(ck["best_x"]), _ptr(ck["fields"]), _ptr(ck["scalars"]))
+    ck_in = None
+    if checkpoint is not None:
+        keep = {k: np.ascontiguousarray(checkpoint[k]) for k in ("x", "best_x", "fields", "scalars")}
+        ck_in = da_checkpoint(*(_ptr(keep[k]) for k in ("x", "best_x", "fields", "scalars")))
+    _check(lib().da_anneal_segment(ctx.handle, _ptr(b), b.size, int(t0), int(t1), float(offset_inc), R,
+                                   int(seed) & (2 ** 64 - 1), int(recompute_every),
+                                   ctypes.byref(ck_in) if ck_in is not None else None, ctypes.byref(ck_out),
+                                   ctypes.byref(res)))
+    out["elapsed_s"] = res.elapsed_s
+    return out, ck
 
 
 def da_anneal_async(ctx: Context, beta_dev, steps: int, offset_inc: float, replicas: int, seed: int,

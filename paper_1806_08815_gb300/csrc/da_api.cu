@@ -51,6 +51,7 @@ struct da_ctx {
     da_dtype dtype = DA_INT8;
     int ldw = 0;
     int S = 0;  // fixed-point scale of the fp32 recompute
+    bool exact_shift = false;  // fp32: every entry reaches the grid by a left shift
     int device = 0;
     void* W = nullptr;
     void* Wf = nullptr;  // DA_INT8: the couplings as exact fp32, for the step kernel
@@ -272,10 +273,11 @@ da_status prof_pair(da_ctx* c, cudaEvent_t* a, cudaEvent_t* b)
     return DA_OK;
 }
 
-// The anneal loop proper: steps [0, T) in launches that end at every
-// recompute point (fp32) or every 2^14 steps.
-da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long long T, float inc, uint64_t seed,
-                     long long recompute_every, int* trace_dev, cudaStream_t st)
+// The anneal loop proper: steps [t_begin, T) in launches that end at every
+// recompute point (fp32, absolute multiples of recompute_every) or every 2^14
+// steps; beta_dev is indexed by the absolute step.
+da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long long t_begin, long long T, float inc,
+                     uint64_t seed, long long recompute_every, int* trace_dev, cudaStream_t st)
 {
     StepParams p = base_params(c, b);
     p.beta = beta_dev;
@@ -285,7 +287,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
     p.trace = trace_dev;
     p.trace_T = T;
     const bool rec = !is_int(c) && recompute_every > 0;
-    for (long long t0 = 0; t0 < T; t0 = p.t1) {
+    for (long long t0 = t_begin; t0 < T; t0 = p.t1) {
         p.t0 = t0;
         p.t1 = std::min(T, t0 + (1ll << 14));
         if (rec) p.t1 = std::min(p.t1, (t0 / recompute_every + 1) * recompute_every);
@@ -373,6 +375,20 @@ bool build_instance(const void* Q, int n, int dtype, HostInstance& out, std::str
                 amax = std::max(amax, std::fabs(v));
             }
         out.S = fix_scale(amax, n);
+        // every nonzero entry a normal number whose grid value round(v 2^S) needs no
+        // rounding (a left shift of its significand): the warp-level recompute then
+        // converts with a shift alone
+        out.exact_shift = true;
+        for (int i = 0; i < n && out.exact_shift; ++i)
+            for (int j = i; j < n; ++j) {
+                uint32_t b;
+                std::memcpy(&b, q + (size_t)i * n + j, 4);
+                const int E = (int)((b >> 23) & 0xFFu);
+                if ((b & 0x7FFFFFFFu) != 0 && (E == 0 || E - 150 + out.S < 0)) {
+                    out.exact_shift = false;
+                    break;
+                }
+            }
     }
     return true;
 }
@@ -389,6 +405,7 @@ StepShape default_shape(int N, int R) { return auto_shape(N, R); }
 
 void set_last_error(const std::string& msg) { g_err = msg; }
 const TcOperand& ctx_tc_operand(const da_ctx* c) { return c->tc; }
+bool ctx_exact_shift(const da_ctx* c) { return c->exact_shift; }
 
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S, const void** Wstep)
 {
@@ -430,6 +447,7 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
     c->ldw = ldw;
     c->device = dev;
     c->S = hin.S;
+    c->exact_shift = hin.exact_shift;
     auto bail = [&](da_status s, const std::string& m) {
         da_destroy(c);
         return fail(s, m);
@@ -566,7 +584,7 @@ static da_status anneal_common(da_ctx* c, const float* beta, bool beta_on_host, 
     }
     if (da_status e = reset_state(c, b, st)) return e;
     int* trace_dev = want_trace ? reinterpret_cast<int*>(b.base + L.trace) : nullptr;
-    if (da_status e = run_anneal(c, b, beta_dev, steps, inc, seed, recompute_every, trace_dev, st)) return e;
+    if (da_status e = run_anneal(c, b, beta_dev, 0, steps, inc, seed, recompute_every, trace_dev, st)) return e;
     if (da_status e = evaluate(c, b, st)) return e;
     *out_b = b;
     return DA_OK;
@@ -982,5 +1000,159 @@ extern "C" da_status da_tune_shape(da_ctx* c, int32_t R, int64_t probe_steps, in
     if (G) *G = best.G;
     if (rpb) *rpb = best.rpb;
     if (draw_warp) *draw_warp = best.ws ? 1 : 0;
+    return DA_OK;
+}
+
+namespace {
+
+// A checkpoint into the workspace layout of an anneal: fields [R][npad] (zero
+// padding), state words [2R][nw] (current, then best), scalars.  Host vectors
+// that stage converted data are kept in `keep` until the stream is synchronised.
+da_status restore_state(const da_ctx* c, const RunBuffers& b, const da_checkpoint* in, cudaStream_t st,
+                        std::vector<std::vector<char>>& keep)
+{
+    const int R = b.R, N = c->N, npad = b.s.npad(), nw = b.s.nwords();
+    const size_t words = (size_t)da_words(N);
+    DA_CU(cudaMemsetAsync(b.h(), 0, (size_t)R * npad * 4, st));
+    DA_CU(cudaMemsetAsync(b.x(), 0, (size_t)2 * R * nw * 4, st));
+    const void* fsrc = in->fields;
+    if (c->dtype == DA_INT8) {   // int32 fields, held as exact fp32 by the step kernel
+        keep.emplace_back((size_t)R * N * 4);
+        float* f = reinterpret_cast<float*>(keep.back().data());
+        const int32_t* g = static_cast<const int32_t*>(in->fields);
+        for (size_t k = 0; k < (size_t)R * N; ++k) f[k] = (float)g[k];
+        fsrc = f;
+    }
+    DA_CU(cudaMemcpy2DAsync(b.h(), (size_t)npad * 4, fsrc, (size_t)N * 4, (size_t)N * 4, R, cudaMemcpyHostToDevice, st));
+    DA_CU(cudaMemcpy2DAsync(b.x(), (size_t)nw * 4, in->x, words * 4, words * 4, R, cudaMemcpyHostToDevice, st));
+    DA_CU(cudaMemcpy2DAsync(b.bestx(), (size_t)nw * 4, in->best_x, words * 4, words * 4, R, cudaMemcpyHostToDevice,
+                            st));
+    keep.emplace_back((size_t)R * sizeof(ReplicaScalars));
+    ReplicaScalars* sc = reinterpret_cast<ReplicaScalars*>(keep.back().data());
+    for (int r = 0; r < R; ++r) {
+        sc[r] = ReplicaScalars{};
+        sc[r].E = in->scalars[4 * r];
+        sc[r].best = in->scalars[4 * r + 1];
+        sc[r].flips = in->scalars[4 * r + 2];
+        sc[r].m = (uint32_t)in->scalars[4 * r + 3];
+        sc[r].check = 0;
+    }
+    DA_CU(cudaMemcpyAsync(b.sc(), sc, (size_t)R * sizeof(ReplicaScalars), cudaMemcpyHostToDevice, st));
+    return DA_OK;
+}
+
+// The workspace after a segment (its best-state test resolved) into a
+// checkpoint; the copies complete at the next synchronisation of st, then
+// finish_saved converts what the step kernel holds in another form.
+da_status save_state(const da_ctx* c, const RunBuffers& b, da_checkpoint* out, cudaStream_t st,
+                     std::vector<std::vector<char>>& keep)
+{
+    const int R = b.R, N = c->N, npad = b.s.npad(), nw = b.s.nwords();
+    const size_t words = (size_t)da_words(N);
+    if (out->fields)
+        DA_CU(cudaMemcpy2DAsync(out->fields, (size_t)N * 4, b.h(), (size_t)npad * 4, (size_t)N * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (out->x)
+        DA_CU(cudaMemcpy2DAsync(out->x, words * 4, b.x(), (size_t)nw * 4, words * 4, R, cudaMemcpyDeviceToHost, st));
+    if (out->best_x)
+        DA_CU(cudaMemcpy2DAsync(out->best_x, words * 4, b.bestx(), (size_t)nw * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (out->scalars) {
+        keep.emplace_back((size_t)R * sizeof(ReplicaScalars));
+        DA_CU(cudaMemcpyAsync(keep.back().data(), b.sc(), (size_t)R * sizeof(ReplicaScalars), cudaMemcpyDeviceToHost,
+                              st));
+    }
+    return DA_OK;
+}
+
+void finish_saved(const da_ctx* c, int R, da_checkpoint* out, const std::vector<char>* sc_bytes)
+{
+    if (out->fields && c->dtype == DA_INT8) {   // exact fp32 integers back to int32, in place
+        char* p = static_cast<char*>(out->fields);
+        for (size_t k = 0; k < (size_t)R * c->N; ++k) {
+            float f;
+            std::memcpy(&f, p + 4 * k, 4);
+            const int32_t g = (int32_t)f;
+            std::memcpy(p + 4 * k, &g, 4);
+        }
+    }
+    if (out->scalars && sc_bytes) {
+        const ReplicaScalars* sc = reinterpret_cast<const ReplicaScalars*>(sc_bytes->data());
+        for (int r = 0; r < R; ++r) {
+            out->scalars[4 * r] = sc[r].E;
+            out->scalars[4 * r + 1] = sc[r].best;
+            out->scalars[4 * r + 2] = sc[r].flips;
+            out->scalars[4 * r + 3] = (int64_t)sc[r].m;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" da_status da_anneal_segment(da_ctx* c, const float* beta, int64_t total_steps, int64_t t0, int64_t t1,
+                                       float inc, int32_t R, uint64_t seed, int64_t recompute_every,
+                                       const da_checkpoint* in, da_checkpoint* out, da_result* res)
+{
+    g_err.clear();
+    if (da_status e = check_ctx(c)) return e;
+    if (!(0 <= t0 && t0 <= t1 && t1 <= total_steps && total_steps < (1ll << 32)))
+        return fail(DA_EINVAL, "need 0 <= t0 <= t1 <= total_steps < 2^32");
+    if (!in && t0 != 0) return fail(DA_EINVAL, "a segment that does not start at step 0 needs a checkpoint");
+    if (in && (!in->x || !in->best_x || !in->fields || !in->scalars)) return fail(DA_EINVAL, "incomplete checkpoint");
+    if (res && res->trace) return fail(DA_EINVAL, "segments write no trace");
+    if (R < 1) return fail(DA_EINVAL, "replicas < 1");
+    if (t1 > 0 && !beta) return fail(DA_EINVAL, "beta schedule is null");
+    if (!(inc >= 0.f) || !std::isfinite(inc)) return fail(DA_EINVAL, "offset_inc must be finite and >= 0");
+    if (recompute_every < 0) return fail(DA_EINVAL, "recompute_every < 0");
+    if (t1 > 0 && !da::schedule_ok(beta, t1)) return fail(DA_EINVAL, "beta must be finite and >= 0");
+    CtxLock lock(c);
+    const cudaStream_t st = c->stream;
+    const StepShape s = shape_for(c, R);
+    if (s.npad() < c->N) return fail(DA_EINVAL, "launch shape too small for N");
+    const Layout L = plan(c, s, R, t1, true, false, 0);
+    if (da_status e = ensure_ws(c, L.total)) return e;
+    RunBuffers b{static_cast<char*>(c->ws), L, s, R};
+    std::vector<std::vector<char>> keep;
+    DA_CU(cudaEventRecord(c->ev0, st));
+    const float* beta_dev = reinterpret_cast<const float*>(b.base + L.beta);
+    if (t1 > 0) DA_CU(cudaMemcpyAsync(b.base + L.beta, beta, (size_t)t1 * 4, cudaMemcpyHostToDevice, st));
+    if (in) {
+        if (da_status e = restore_state(c, b, in, st, keep)) return e;
+    } else if (da_status e = reset_state(c, b, st)) {
+        return e;
+    }
+    if (da_status e = run_anneal(c, b, beta_dev, t0, t1, inc, seed, recompute_every, nullptr, st)) return e;
+    if (da_status e = evaluate(c, b, st)) return e;
+    double* resd = reinterpret_cast<double*>(b.base + L.res);
+    finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(is_int(c), R, b.sc(), b.eex(), resd, resd + R, resd + 2 * R,
+                                                     reinterpret_cast<int64_t*>(resd + 3 * R));
+    DA_CU(cudaGetLastError());
+    DA_CU(cudaEventRecord(c->ev1, st));
+    std::vector<double> hres((size_t)4 * R);
+    DA_CU(cudaMemcpyAsync(hres.data(), resd, hres.size() * 8, cudaMemcpyDeviceToHost, st));
+    const size_t words = (size_t)da_words(c->N);
+    if (res && res->final_x)
+        DA_CU(cudaMemcpy2DAsync(res->final_x, words * 4, b.x(), (size_t)s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    if (res && res->best_x)
+        DA_CU(cudaMemcpy2DAsync(res->best_x, words * 4, b.bestx(), (size_t)s.nwords() * 4, words * 4, R,
+                                cudaMemcpyDeviceToHost, st));
+    const size_t sc_idx = keep.size();
+    if (out)
+        if (da_status e = save_state(c, b, out, st, keep)) return e;
+    DA_CU(cudaStreamSynchronize(st));
+    if (da_status e = check_kernel_flag(c)) return e;
+    if (out) finish_saved(c, R, out, out->scalars ? &keep[sc_idx] : nullptr);
+    if (res) {
+        float ms = 0.f;
+        DA_CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        res->elapsed_s = ms * 1e-3;
+        for (int r = 0; r < R; ++r) {
+            if (res->final_E) res->final_E[r] = hres[r];
+            if (res->best_E) res->best_E[r] = hres[R + r];
+            if (res->max_drift) res->max_drift[r] = hres[2 * R + r];
+            if (res->flips) res->flips[r] = reinterpret_cast<const int64_t*>(hres.data() + 3 * R)[r];
+        }
+    }
     return DA_OK;
 }

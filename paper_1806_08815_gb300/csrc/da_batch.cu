@@ -84,7 +84,7 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
         if (it.stop && (t & 1023) == 1023 && *reinterpret_cast<const volatile int*>(it.stop)) break;
         if constexpr (std::is_same<Tw, float>::value) {
             if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
-                rp.recompute(static_cast<const float*>(it.diag), it.S);
+                rp.recompute(static_cast<const float*>(it.diag), it.S, it.exact_shift != 0);
                 if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
             }
         }
@@ -556,6 +556,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
                 d.S = hi[i].S;
                 d.R = it.replicas;
                 d.inc = it.offset_inc;
+                d.exact_shift = da::ctx_exact_shift(it.ctx) ? 1 : 0;
                 desc[di++] = d;
                 units += it.replicas;
             }

@@ -36,6 +36,19 @@ __device__ __forceinline__ long long fixed_of_f32(float w, int S)
     return (b >> 31) ? -(long long)mag : (long long)mag;
 }
 
+// round(w 2^S) for w = 0 or a normal number with (exponent field - 150 + S) >= 0,
+// i.e. when w 2^S is an integer (the significand shifted left): equal to
+// fixed_of_f32(w, S) there, without its rounding path.
+__device__ __forceinline__ long long fixed_of_f32_shift(float w, int S)
+{
+    const uint32_t b = __float_as_uint(w);
+    const uint32_t E = (b >> 23) & 0xFFu;
+    const uint32_t m = E ? ((b & 0x7FFFFFu) | 0x800000u) : 0u;
+    const int sh = E ? (int)E - 150 + S : 0;
+    const unsigned long long mag = (unsigned long long)m << sh;
+    return (b >> 31) ? -(long long)mag : (long long)mag;
+}
+
 // fl32(v) 2^-S: v rounded to fp32 (to nearest, ties to even), then scaled;
 // equal to ldexpf(__ll2float_rn(v), -S).  Results outside the normal range
 // are left to ldexpf.

@@ -177,6 +177,7 @@ size_t plain_workspace_bytes(int N, int R);
 // otherwise).
 struct HostInstance {
     int ldw = 0, S = 0;
+    bool exact_shift = false;   // fp32: every nonzero entry reaches the grid 2^-S by a left shift
 };
 size_t instance_W_bytes(int n, int dtype);
 // Zeroes `bytes` bytes at p (device, 16-byte aligned) with a kernel of this
@@ -245,7 +246,7 @@ struct BatchItemDev {
     uint64_t seed;
     int N, ldw, S, R;
     float inc;
-    int pad;
+    int exact_shift;        // fp32: the recompute may convert with shifts alone (HostInstance)
     const int* stop;        // optional (host-mapped): set, the anneal leaves at its next multiple of 1024 steps
 };
 
@@ -277,6 +278,8 @@ void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t
                      const void** Wstep = nullptr);
 // The context's tensor-core operand of W (built by da_create).
 const TcOperand& ctx_tc_operand(const da_ctx* c);
+// Whether the context's fp32 instance reaches its fixed-point grid by shifts alone.
+bool ctx_exact_shift(const da_ctx* c);
 
 // Fixed-point scale of the fp32 recompute for amax = max(|W_ij|, |diag_i|)
 // and N variables (N + 1 terms per sum).

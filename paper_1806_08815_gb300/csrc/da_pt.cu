@@ -51,6 +51,62 @@ __global__ void pt_exchange_kernel(const float* __restrict__ betas, int K, int L
     }
 }
 
+// The same exchange pass with one warp per ladder: the lanes stage what does
+// not depend on the order of the labels (the replicas' energies, the fp64 gaps
+// beta_p - beta_{p+1}, each pair's uniform draw) in shared memory, lane 0 makes
+// the sequential pass (the same fp64 and fp32 operations in the same order as
+// the one-thread form, so every decision is identical), and the lanes write the
+// labels, counts and trace back.  Shared memory: K * 32 bytes per ladder.
+template <bool INT8>
+__global__ void pt_exchange_warp_kernel(const float* __restrict__ betas, int K, int L,
+                                        const ReplicaScalars* __restrict__ sc, int* temp_of, int* rep_at,
+                                        long long* swaps, uint8_t* swap_trace, long long sweep, long long sweeps,
+                                        uint64_t seed)
+{
+    extern __shared__ __align__(16) unsigned char pt_smem[];
+    double* E = reinterpret_cast<double*>(pt_smem);   // [K] energy of replica r
+    double* gap = E + K;                               // [K - 1] beta_p - beta_{p+1}
+    float* u = reinterpret_cast<float*>(gap + K);      // [K - 1] the pair's uniform draw
+    int* at = reinterpret_cast<int*>(u + K);           // [K] replica at temperature index k
+    uint8_t* acc = reinterpret_cast<uint8_t*>(at + K); // [K - 1] decisions
+    const int l = blockIdx.x;
+    if (l >= L) return;
+    const int lane = threadIdx.x;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+    const ReplicaScalars* s = sc + (size_t)l * K;
+    for (int k = lane; k < K; k += 32) {
+        E[k] = energy_of<INT8>(s[k]);
+        at[k] = rep_at[(size_t)l * K + k];
+        if (k + 1 < K) {
+            gap[k] = __dsub_rn((double)betas[k], (double)betas[k + 1]);
+            u[k] = uniform01(philox4x32_10((uint32_t)k, (uint32_t)sweep, (uint32_t)l, 2u, key0, key1).x);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int p = 0; p + 1 < K; ++p) {
+            const int a = at[p], c = at[p + 1];
+            const double arg = __dmul_rn(gap[p], __dsub_rn(E[a], E[c]));
+            const bool ok = arg >= 0.0 || u[p] < exp_neg(__double2float_rn(arg));
+            acc[p] = ok ? 1 : 0;
+            if (ok) {
+                at[p] = c;
+                at[p + 1] = a;
+            }
+        }
+    }
+    __syncwarp();
+    for (int k = lane; k < K; k += 32) {
+        const int r = at[k];
+        rep_at[(size_t)l * K + k] = r;
+        temp_of[(size_t)l * K + r] = k;
+        if (k + 1 < K) {
+            if (swap_trace) swap_trace[((size_t)l * sweeps + sweep) * (K - 1) + k] = acc[k];
+            if (swaps && acc[k]) swaps[(size_t)l * (K - 1) + k] += 1;
+        }
+    }
+}
+
 // The adaptive ladder (Sec. II: highest and lowest temperature fixed, the
 // others moved towards equal exchange acceptance of neighbouring pairs):
 // win[p] = exchanges of pair p accepted over all ladders since the last
@@ -114,6 +170,19 @@ cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,
                                uint64_t seed, cudaStream_t st)
 {
     if (L <= 0 || K < 2) return cudaSuccess;
+    const size_t smem = (size_t)K * 32;
+    if (smem <= 48 * 1024) {   // one warp per ladder
+        if (is_int8) {
+            prefer_shared<pt_exchange_warp_kernel<true>>();
+            pt_exchange_warp_kernel<true><<<L, 32, smem, st>>>(betas, K, L, sc, temp_of, rep_at, swaps, swap_trace,
+                                                               sweep, sweeps, seed);
+        } else {
+            prefer_shared<pt_exchange_warp_kernel<false>>();
+            pt_exchange_warp_kernel<false><<<L, 32, smem, st>>>(betas, K, L, sc, temp_of, rep_at, swaps, swap_trace,
+                                                                sweep, sweeps, seed);
+        }
+        return cudaGetLastError();
+    }
     const int tb = 64;
     if (is_int8)
         pt_exchange_kernel<true><<<(L + tb - 1) / tb, tb, 0, st>>>(betas, K, L, sc, temp_of, rep_at, swaps,

@@ -194,13 +194,29 @@ struct WarpReplica {
     // energy (same definition as da_fields.cu): g_i = fl32(2^-S (round(d_i 2^S)
     // + sum_{x_j = 1} round(W_ij 2^S))), E = fl64(2^-(S+1) sum_{x_i = 1}
     // (round(d_i 2^S) + sum_i)).
-    __device__ __forceinline__ void recompute(const float* __restrict__ diag, int S)
+    // shift: every coupling and linear term reaches the grid by a left shift
+    // (the host checked), so fixed_of_f32_shift converts it exactly.
+    __device__ __forceinline__ void recompute(const float* __restrict__ diag, int S, bool shift = false)
+    {
+        if (shift) recompute_impl<true>(diag, S);
+        else recompute_impl<false>(diag, S);
+    }
+
+    template <bool SHIFT>
+    static __device__ __forceinline__ long long to_fixed(float w, int S)
+    {
+        if constexpr (SHIFT) return fixed_of_f32_shift(w, S);
+        else return fixed_of_f32(w, S);
+    }
+
+    template <bool SHIFT>
+    __device__ __forceinline__ void recompute_impl(const float* __restrict__ diag, int S)
     {
         static_assert(sizeof(Tw) == 4, "only the fp32 fields are recomputed");
         long long acc[V];
 #pragma unroll
         for (int v = 0; v < V; ++v)
-            acc[v] = ((valid >> v) & 1u) ? fixed_of_f32(ldx(diag + base + v), S) : 0ll;
+            acc[v] = ((valid >> v) & 1u) ? to_fixed<SHIFT>(ldx(diag + base + v), S) : 0ll;
         const uint32_t myword = word();
         const int nw = (N + 31) >> 5;
         for (int wi = 0; wi < nw; ++wi) {
@@ -213,7 +229,7 @@ struct WarpReplica {
                     Tw cv[V];
                     load_row(W + (size_t)j * ldw + base, cv);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) acc[v] += fixed_of_f32(cv[v], S);
+                    for (int v = 0; v < V; ++v) acc[v] += to_fixed<SHIFT>(cv[v], S);
                 }
             }
         }
@@ -223,7 +239,7 @@ struct WarpReplica {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             if (((valid & xm) >> v) & 1u) {
-                const long long t = fixed_of_f32(ldx(diag + base + v), S) + acc[v];
+                const long long t = to_fixed<SHIFT>(ldx(diag + base + v), S) + acc[v];
                 const unsigned long long nlo = lo + (unsigned long long)t;
                 hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
                 lo = nlo;

@@ -306,6 +306,7 @@ bool admit(da_server* s, Req& q, long long& launches)
         d.S = q.inst.S;
         d.R = R;
         d.inc = q.job.offset_inc;
+        d.exact_shift = q.inst.exact_shift ? 1 : 0;
         d.stop = s->stop + q.slot;
         auto* item_dev = reinterpret_cast<da::BatchItemDev*>(q.dmem + q.o_item);
         auto* head_dev = reinterpret_cast<unsigned long long*>(q.dmem + q.o_item + sizeof(da::BatchItemDev));

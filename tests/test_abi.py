@@ -40,7 +40,8 @@ REQUIRED = ("da_create", "da_destroy", "da_anneal", "da_anneal_async", "da_pt", 
             "da_server_destroy",
             "da_batch_anneal", "da_anneal_plain", "da_anneal_static", "da_static_pitch",
             "da_quantize", "da_move_energy_percentiles", "da_tts_bootstrap", "da_percentiles",
-            "da_diag_fail_alloc", "da_diag_live_allocations")
+            "da_diag_fail_alloc", "da_diag_live_allocations", "da_anneal_segment", "da_tune_shape",
+            "da_batch_describe", "da_batch_force", "da_server_resident", "da_diag_read_bandwidth")
 
 
 def test_header_declares_the_boundary():
@@ -105,3 +106,8 @@ def test_failure_injection_arguments(libda):
 def test_cancel_rejects_null(libda):
     from paper_1806_08815_gb300 import binding as b
     assert libda.da_cancel(None) == 1
+
+
+def test_segment_rejects_bad_ranges_without_a_device(libda):
+    """da_anneal_segment validates its arguments before touching a device."""
+    assert libda.da_anneal_segment(None, None, 0, 0, 0, ctypes.c_float(0), 1, 0, 0, None, None, None) == 1

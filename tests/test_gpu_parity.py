@@ -487,6 +487,27 @@ def test_batched_configurations_match_single_instances(da, inst, staging, wpb):
             assert np.array_equal(o[k], r[k]), (k, desc)
 
 
+def test_batched_recompute_with_and_without_shift_only_conversion(da, inst):
+    """The batched kernel's warp-level exact recompute converts couplings to the fixed-point
+    grid by a shift alone when every entry allows it (checked on the host), else through the
+    rounding path: instances of both kinds (a tiny normal coupling 1e-30 and a subnormal one
+    make the second) give their da_anneal results bit for bit."""
+    jobs, refs = [], []
+    for n, (N, tiny) in enumerate([(200, None), (200, 1e-30), (700, 1e-40), (1024, None)]):
+        q = inst.sk_gaussian(N, 80 + n).Q.copy()
+        if tiny is not None:
+            q[0, 5] = np.float32(tiny)
+            q[3, 3] = np.float32(-tiny)
+        beta = inst.beta_linear(0.1, 6.0, 700)
+        ctx = da.da_create(q)
+        jobs.append(dict(ctx=ctx, beta=beta, offset_inc=0.0, replicas=9, seed=40 + n, recompute_every=64))
+        refs.append(da.da_anneal(ctx, beta, 0.0, 9, 40 + n, recompute_every=64))
+    outs, _ = da.binding.da_batch_anneal(jobs)
+    for o, r in zip(outs, refs):
+        for k in ("final_x", "best_x", "flips", "final_E", "best_E", "max_drift"):
+            assert np.array_equal(o[k], r[k]), k
+
+
 @pytest.mark.parametrize("N,R,kind", [(300, 40, "f32"), (97, 9, "i8"), (1500, 16, "f32"), (2100, 8, "i8")])
 def test_tuned_launch_shape_keeps_results(da, inst, N, R, kind):
     """da_tune_shape picks the fastest launch shape for (instance, replicas) and every later
