@@ -455,6 +455,40 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
     return out
 
 
+def profile_case(da, instances, case):
+    """Small runs of the library's other kernels for ncu captures: `batched` (a two-class batched
+    launch: fp32 N = 1024 from L2, int8 N = 64 staged), `ptda` (SK bimodal N = 512, 32 betas,
+    20 sweeps), `plain` (the plain form, 200 steps of the headline workload), `g8` (fp32
+    N = 8192, 32 replicas: the 8-warp step kernel)."""
+    if case == "batched":
+        T = 2048
+        jobs = []
+        for i in range(64):
+            q = instances.sk_gaussian(1024, 500 + i)
+            jobs.append(dict(ctx=da.da_create(q.Q), beta=instances.beta_linear(0.1, 10.0, T), offset_inc=0.0,
+                             replicas=64, seed=i, recompute_every=1024))
+        for i in range(128):
+            q = instances.sk_bimodal(64, 700 + i)
+            jobs.append(dict(ctx=da.da_create(q.Q), beta=instances.beta_linear(0.05, 3.0, T), offset_inc=1.0,
+                             replicas=64, seed=i))
+        da.da_batch_force(1, 16)
+        _, el = da.da_batch_anneal(jobs)
+        da.da_batch_force(-1, 0)
+        return {"seconds": el, "config": da.da_batch_describe()}
+    if case == "ptda":
+        ctx = da.da_create(instances.sk_bimodal(512, 77).Q)
+        return {"seconds": da.da_pt(ctx, instances.beta_geometric(0.2, 5.0, 32), 20, 32, 1)["elapsed_s"]}
+    if case == "plain":
+        ctx = da.da_create(instances.sk_gaussian(1024, 0).Q)
+        beta = instances.beta_linear(0.1, 10.0, 200_000)[100_000:100_200]
+        return {"seconds": da.da_anneal_plain(ctx, beta, 0.0, 1024, 0)["elapsed_s"]}
+    if case == "g8":
+        ctx = da.da_create(instances.sk_gaussian(8192, 3).Q)
+        r = da.da_anneal(ctx, instances.beta_linear(0.1, 10.0, 4096), 0.0, 32, 0, recompute_every=1024)
+        return {"seconds": r["elapsed_s"]}
+    raise ValueError(case)
+
+
 def cpu_baseline(sample_R=None, sample_T=32768):
     """The oracle, as it stands, on the host cores over a bounded sample of the workload."""
     import oracle
@@ -539,6 +573,8 @@ def main():
                     help="skip the batched, PTDA and served workloads reported beside the headline")
     ap.add_argument("--kernel-case", action="store_true",
                     help="run two 2048-step anneals from the middle of the schedule and exit (for ncu captures)")
+    ap.add_argument("--profile-case", choices=["batched", "ptda", "plain", "g8"],
+                    help="run one small case of another kernel and exit (for ncu captures)")
     ap.add_argument("--served-case", action="store_true",
                     help="run the served workload once, print its figures and exit (for ncu launch lists)")
     args = ap.parse_args()
@@ -565,6 +601,9 @@ def main():
     da.lib()
 
     dev = torch.device("cuda", local)
+    if args.profile_case:
+        print(json.dumps({"profile_case": args.profile_case, **profile_case(da, instances, args.profile_case)}))
+        return
     if args.served_case:
         r = run_served(da, instances, sustained_req=0)
         print(json.dumps({"served_case": r["workload"], **{k: v for k, v in r.items() if k != "workload"}}))
