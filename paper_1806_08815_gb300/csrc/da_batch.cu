@@ -76,6 +76,9 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
     const long long T = t_limit > 0 ? std::min(t_limit, it.T) : it.T;
     if (T > 0) rp.draw(0u, keys);
     float beta_next = T > 0 ? it.beta[0] : 0.f;
+    // the next step count (t + 1) at which the fp32 fields are recomputed: a running
+    // target instead of a 64-bit remainder every step
+    long long next_rec = std::is_same<Tw, float>::value && it.recompute_every > 0 ? it.recompute_every : -1;
     for (long long t = 0; t < T; ++t) {
         const float beta = beta_next;
         if (t + 1 < T) beta_next = it.beta[t + 1];
@@ -83,8 +86,10 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
         if (it.trace && lane == 0) it.trace[(size_t)r * it.T + t] = k;
         if (it.stop && (t & 1023) == 1023 && *reinterpret_cast<const volatile int*>(it.stop)) break;
         if constexpr (std::is_same<Tw, float>::value) {
-            if (it.recompute_every > 0 && (t + 1) % it.recompute_every == 0) {
+            if (t + 1 == next_rec) {
+                next_rec += it.recompute_every;
                 rp.recompute(static_cast<const float*>(it.diag), it.S, it.exact_shift != 0);
+                // the draws of t + 1 again: lg is dead across the recompute, which frees its registers
                 if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
             }
         }
