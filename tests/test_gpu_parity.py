@@ -632,3 +632,20 @@ def test_largest_instances(da, inst, dtype, shape):
     got = da.da_anneal(ctx, beta, 0.0, 3, 21, recompute_every=rec, trace=True)
     ref = oracle.da_anneal(q.Q, beta, R=3, seed=21, inc=0.0, recompute_every=rec, trace=True, nthreads=NT)
     _compare_anneal(got, ref, q.Q, dtype == "i8")
+
+
+def test_read_bandwidth_probe(da):
+    """The read-bandwidth probe the step kernel's roofline is stated against: an L2-resident
+    buffer (64 MB) reads faster than one four times the L2 (512 MB), both at plausible
+    rates for this GPU, and misaligned or empty buffers are refused."""
+    import torch
+    small = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    large = torch.zeros(512 << 20, dtype=torch.uint8, device="cuda")
+    bw_l2 = max(da.binding.da_diag_read_bandwidth(small, 32) for _ in range(3))
+    bw_hbm = max(da.binding.da_diag_read_bandwidth(large, 4) for _ in range(3))
+    assert bw_l2 > 1.2 * bw_hbm, (bw_l2, bw_hbm)
+    assert 1e12 < bw_hbm < 2e13 and bw_l2 < 1e14
+    with pytest.raises(da.binding.DAError):
+        da.binding.da_diag_read_bandwidth(small[1:17], 1)
+    with pytest.raises(da.binding.DAError):
+        da.binding.da_diag_read_bandwidth(small[:0], 1)
