@@ -455,6 +455,37 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
     return out
 
 
+def run_configs(da, instances):
+    """The two smaller workloads of the target, each annealed once by the library and once by the
+    plain one-launch-per-step form (same schedule and seeds): trials/s and TTS99 of both at the hit
+    rate each measures against the best energy over the runs of both.
+      sk_bimodal_n64:   SK bimodal N = 64, 64 replicas, 1e4 steps, beta linear 0.05 -> 3, offset 1;
+      lattice2d_l32:    2D Gaussian spin glass on a 32 x 32 torus (N = 1024, kept dense), 128
+                        replicas, 1e5 steps, beta geometric 0.1 -> 5, offset 0.5."""
+    out = {}
+    cases = [("sk_bimodal_n64", instances.sk_bimodal(64, 0), instances.beta_linear(0.05, 3.0, 10_000), 1.0, 64, 0),
+             ("lattice2d_l32", instances.lattice2d(32, 0, True), instances.beta_geometric(0.1, 5.0, 100_000), 0.5,
+              128, 1024)]
+    for name, q, beta, inc, R, P in cases:
+        ctx = da.da_create(q.Q)
+        da.da_anneal(ctx, beta[:256], inc, R, 0, recompute_every=P)           # warm-up
+        r = da.da_anneal(ctx, beta, inc, R, 0, recompute_every=P)
+        da.da_anneal_plain(ctx, beta[:64], inc, R, 0)                          # warm-up
+        rp = da.da_anneal_plain(ctx, beta, inc, R, 0)
+        trials = R * beta.size * q.N
+        E_ref = float(min(r["best_E"].min(), rp["best_E"].min()))
+        t_lib = _hits_tts(r["best_E"], E_ref, r["elapsed_s"] / R)
+        t_plain = _hits_tts(rp["best_E"], E_ref, rp["elapsed_s"] / R)
+        out[name] = {"value": trials / r["elapsed_s"], "unit": UNIT, "seconds": r["elapsed_s"],
+                     "tts99_s": t_lib["tts99_s"], "hits": t_lib["hits"], "runs": t_lib["runs"],
+                     "mean_best_E": float(np.mean(r["best_E"])),
+                     "plain_gpu": {"value": trials / rp["elapsed_s"], "unit": UNIT, "tts99_s": t_plain["tts99_s"],
+                                   "hits": t_plain["hits"], "mean_best_E": float(np.mean(rp["best_E"]))},
+                     "E_ref": E_ref}
+        da.da_destroy(ctx)
+    return out
+
+
 def profile_case(da, instances, case):
     """Small runs of the library's other kernels for ncu captures: `batched` (a two-class batched
     launch: fp32 N = 1024 from L2, int8 N = 64 staged), `ptda` (SK bimodal N = 512, 32 betas,
@@ -754,6 +785,7 @@ def main():
         line["served"] = run_served(da, instances)
         line["density"] = run_density(da, instances)
         line["fixed_point"] = run_fixed_point(da, instances)
+        line["configs"] = run_configs(da, instances)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
