@@ -19,7 +19,10 @@ namespace step_detail {
 
 // SW: the rows of W are read from a copy staged in shared memory (W points
 // there) instead of from global memory.
-template <typename Tw, int V, bool SW = false>
+// PRE: the step-invariant part of each Philox block is computed once per launch
+// (prep_draws) and the draws of every step start from it (draw_pre); four more
+// words per block live in registers, for kernels that have them to spare.
+template <typename Tw, int V, bool SW = false, bool PRE = false>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -41,6 +44,10 @@ struct WarpReplica {
     uint32_t rep;
     const Tw* __restrict__ W;
     uint32_t* bestg;  // best-state words of this replica
+    // Step-invariant Philox words of the lane's blocks (prep_draws): kq1..kq4 per
+    // block, ku0 shared by the lane's blocks.
+    uint32_t kq1[PRE ? NQ : 1], kq2[PRE ? NQ : 1], kq3[PRE ? NQ : 1], kq4[PRE ? NQ : 1];
+    uint32_t ku0;
 
     __device__ __forceinline__ void init(const Tw* W_, int N_, int ldw_, uint32_t rep_, uint32_t* bestg_)
     {
@@ -117,14 +124,156 @@ struct WarpReplica {
         }
     }
 
+    // The acceptance block q of step t has counter (c0, t, rep, 0), c0 = base/4 + q.
+    // Following the words of Philox4x32-10 through its first rounds (round r:
+    // products pa = A c0, pb = B c2; c0 <- hi(pb) ^ c1 ^ ka_r, c1 <- lo(pb),
+    // c2 <- hi(pa) ^ c3 ^ kb_r, c3 <- lo(pa)):
+    //   after round 0: (u ^ t, lo(B rep), y2_q, y3_q) with u = hi(B rep) ^ ka_0,
+    //     y2_q = hi(A c0) ^ kb_0, y3_q = lo(A c0): only the first word depends on t;
+    //   round 1 multiplies that word (one product per lane and step, P = A (u ^ t))
+    //     and y2_q (step-invariant): after it (z0_q, z1_q, hi(P) ^ y3_q ^ kb_1, lo(P))
+    //     with z0_q, z1_q step-invariant;
+    //   round 2 multiplies z0_q (step-invariant) and the third word (per block).
+    // So a step needs one product for the lane and, per block, one product in round
+    // 2 and the full rounds 3..9: the words below are the step-invariant operands
+    // with their round keys folded in.  draw_pre returns philox4x32_10's words bit
+    // for bit.
+    template <class Keys>
+    __device__ __forceinline__ void prep_draws(const Keys& keys)
+    {
+        static_assert(PRE, "prep_draws needs PRE");
+        const uint64_t pb0 = (uint64_t)kPhiloxMulB * rep;
+        ku0 = (uint32_t)(pb0 >> 32) ^ keys.a[0];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint64_t pa0 = (uint64_t)kPhiloxMulA * ((uint32_t)(base >> 2) + q);
+            const uint64_t pb1 = (uint64_t)kPhiloxMulB * ((uint32_t)(pa0 >> 32) ^ keys.b[0]);
+            const uint64_t pa2 = (uint64_t)kPhiloxMulA * ((uint32_t)(pb1 >> 32) ^ (uint32_t)pb0 ^ keys.a[1]);
+            kq1[q] = (uint32_t)pa0 ^ keys.b[1];               // y3_q ^ kb_1
+            kq2[q] = (uint32_t)pb1 ^ keys.a[2];               // z1_q ^ ka_2
+            kq3[q] = (uint32_t)(pa2 >> 32) ^ keys.b[2];       // hi(A z0_q) ^ kb_2
+            kq4[q] = (uint32_t)pa2 ^ keys.b[3];               // lo(A z0_q) ^ kb_3
+        }
+    }
+
+    // The next step's draws in stages (PRE), so that their rounds can fill the
+    // latency of the current step's warp collectives: draw_begin (the per-step
+    // product and round 2), draw_round<R> (rounds 3..9), draw_end (log2 U of the
+    // 4 NQ words into lg).
+    uint32_t dq0[PRE ? NQ : 1], dq1[PRE ? NQ : 1], dq2[PRE ? NQ : 1], dq3[PRE ? NQ : 1];
+
+    __device__ __forceinline__ void draw_begin(uint32_t tt)
+    {
+        const uint64_t P = (uint64_t)kPhiloxMulA * (ku0 ^ tt);
+        const uint32_t hP = (uint32_t)(P >> 32), lP = (uint32_t)P;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {            // round 2
+            const uint64_t pb = (uint64_t)kPhiloxMulB * (hP ^ kq1[q]);
+            dq0[q] = (uint32_t)(pb >> 32) ^ kq2[q];
+            dq1[q] = (uint32_t)pb;
+            dq2[q] = kq3[q] ^ lP;
+            dq3[q] = kq4[q];                       // carries kb_3
+        }
+    }
+
+    template <int R, class Keys>
+    __device__ __forceinline__ void draw_round(const Keys& keys)
+    {
+        static_assert(R >= 3 && R < 10, "rounds 3..9");
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const uint64_t pa = (uint64_t)kPhiloxMulA * dq0[q];
+            const uint64_t pb = (uint64_t)kPhiloxMulB * dq2[q];
+            dq0[q] = (uint32_t)(pb >> 32) ^ dq1[q] ^ keys.a[R];
+            if constexpr (R == 3) dq2[q] = (uint32_t)(pa >> 32) ^ dq3[q];
+            else dq2[q] = (uint32_t)(pa >> 32) ^ dq3[q] ^ keys.b[R];
+            dq1[q] = (uint32_t)pb;
+            dq3[q] = (uint32_t)pa;
+        }
+    }
+
+    template <int R0, int R1, class Keys>
+    __device__ __forceinline__ void draw_rounds(const Keys& keys)
+    {
+        if constexpr (R0 < R1) {
+            draw_round<R0>(keys);
+            draw_rounds<R0 + 1, R1>(keys);
+        }
+    }
+
+    __device__ __forceinline__ void draw_end()
+    {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            lg[4 * q] = lg2_draw(dq0[q]);
+            lg[4 * q + 1] = lg2_draw(dq1[q]);
+            lg[4 * q + 2] = lg2_draw(dq2[q]);
+            lg[4 * q + 3] = lg2_draw(dq3[q]);
+        }
+    }
+
+    template <class Keys>
+    __device__ __forceinline__ void draw_pre(uint32_t tt, const Keys& keys)
+    {
+        draw_begin(tt);
+        draw_rounds<3, 10>(keys);
+        draw_end();
+    }
+
+    // Work a step places in the latency of its warp collectives (choose_and_flip):
+    // begin() after the count reduction is issued, at<I>() after collective I is
+    // issued and before its result is used (I = 0..4: the prefix-sum shuffles;
+    // 5: the owner ballot; 6: the owner's position shuffle), rest_flip() while
+    // row k is in flight, rest_none() when nothing flips.
+    template <class F>
+    struct RestOnly {      // everything under the row load (or at once)
+        F& f;
+        __device__ __forceinline__ void begin() {}
+        template <int I> __device__ __forceinline__ void at() {}
+        __device__ __forceinline__ void rest_flip() { f(); }
+        __device__ __forceinline__ void rest_none() { f(); }
+    };
+    template <class Keys>
+    struct DrawSlots {     // the next step's draws (PRE): rounds 3-5 in the prefix
+        WarpReplica& rp;   // sum, 6-7 in the choice, 8-9 and log2 under the row load
+        const Keys& keys;
+        uint32_t tt;
+        __device__ __forceinline__ void begin() { rp.draw_begin(tt); }
+        template <int I>
+        __device__ __forceinline__ void at()
+        {
+            if constexpr (I <= 2) rp.template draw_round<3 + I>(keys);
+            else if constexpr (I == 5 || I == 6) rp.template draw_round<I + 1>(keys);
+        }
+        __device__ __forceinline__ void rest_flip()
+        {
+            rp.template draw_rounds<8, 10>(keys);
+            rp.draw_end();
+        }
+        __device__ __forceinline__ void rest_none()
+        {
+            rp.template draw_rounds<6, 10>(keys);
+            rp.draw_end();
+        }
+    };
+
     // One step t (the draws of t are in lg).  If draw_next, the draws of t + 1
-    // are computed while row k is in flight.  Returns the flipped index or -1.
+    // are computed while row k is in flight (PRE: always, spread over the
+    // step's collectives as DrawSlots places them).  Returns the flipped index
+    // or -1.
     template <bool FULL, class Keys>
     __device__ __forceinline__ int step(long long t, bool draw_next, float beta, float inc, const Keys& keys)
     {
-        return step_log<FULL>(t, beta, inc, lg, keys, [&] {
-            if (draw_next) draw((uint32_t)(t + 1), keys);
-        });
+        if constexpr (PRE) {
+            DrawSlots<Keys> s{*this, keys, (uint32_t)(t + 1)};
+            return decide_and_flip<FULL>(t, beta, inc, lg, keys, s);
+        } else {
+            auto f = [&] {
+                if (draw_next) draw((uint32_t)(t + 1), keys);
+            };
+            RestOnly<decltype(f)> s{f};
+            return decide_and_flip<FULL>(t, beta, inc, lg, keys, s);
+        }
     }
 
     // One step t whose acceptance draws are L[v] = log2 U of this lane's trials
@@ -135,30 +284,53 @@ struct WarpReplica {
     __device__ __forceinline__ int step_log(long long t, float beta, float inc, const float (&L)[V], const Keys& keys,
                                             Overlap&& overlap)
     {
+        RestOnly<Overlap> s{overlap};
+        return decide_and_flip<FULL>(t, beta, inc, L, keys, s);
+    }
+
+    template <bool FULL, class Keys, class Slots>
+    __device__ __forceinline__ int decide_and_flip(long long t, float beta, float inc, const float (&L)[V],
+                                                   const Keys& keys, Slots& slots)
+    {
         const float Eoff = __fmul_rn(__uint2float_rn(m), inc);
         bool unsure;
         uint32_t accm = decide_log<A, V>(h, xm, Eoff, __fmul_rn(beta, kLog2e), L, unsure);
         if (__any_sync(0xffffffffu, unsure))
             accm = decide_exact<A, V>(h, xm, Eoff, beta, L, accm, base, (uint32_t)t, rep, keys);
-        return choose_and_flip<FULL>(t, accm, keys, overlap);
+        return choose_and_flip<FULL>(t, accm, keys, slots);
+    }
+
+    // Inclusive prefix sum over the lanes, level I..4, with slots.at<I>() in the
+    // latency of each shuffle.
+    template <int I, class Slots>
+    __device__ __forceinline__ void scan_levels(int& incl, Slots& slots)
+    {
+        if constexpr (I < 5) {
+            const int n = __shfl_up_sync(0xffffffffu, incl, 1 << I);
+            slots.template at<I>();
+            if (lane >= (1 << I)) incl += n;
+            scan_levels<I + 1>(incl, slots);
+        }
     }
 
     // (c) of a step with acceptance mask accm: the best-state test left by the
     // previous step, the uniform choice among the accepted trials, the flip
-    // and the field update; `overlap` runs while row k is in flight (or at
-    // once when nothing flips).  Returns the flipped index or -1.
-    template <bool FULL, class Keys, class Overlap>
-    __device__ __forceinline__ int choose_and_flip(long long t, uint32_t accm, const Keys& keys, Overlap&& overlap)
+    // and the field update, with `slots` placed as described above.  Returns
+    // the flipped index or -1.
+    template <bool FULL, class Keys, class Slots>
+    __device__ __forceinline__ int choose_and_flip(long long t, uint32_t accm, const Keys& keys, Slots& slots)
     {
         if constexpr (!FULL) accm &= valid;
         flush_best();
 
         const int cnt = __popc(accm);
-        const int incl = warp_inclusive_scan(cnt, lane);
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        slots.begin();
+        int incl = cnt;
+        scan_levels<0>(incl, slots);
         if (total == 0) {
             m += 1;
-            overlap();
+            slots.rest_none();
             return -1;
         }
         const long long blk = t >> 2;
@@ -169,14 +341,17 @@ struct WarpReplica {
         const int j = (int)__umulhi(pick(cr, (int)(t & 3)), (uint32_t)total);
         const int excl = incl - cnt;
         const int own = __ffs(__ballot_sync(0xffffffffu, j >= excl && j < incl)) - 1;
-        const int vk = __shfl_sync(0xffffffffu, nth_set_bit(accm, j - excl), own);
+        const int pos = nth_set_bit(accm, j - excl);
+        slots.template at<5>();
+        const int vk = __shfl_sync(0xffffffffu, pos, own);
+        slots.template at<6>();
         const uint32_t xold = (__shfl_sync(0xffffffffu, xm, own) >> vk) & 1u;
         const H gk = select_slot<H, V>(h, vk);
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
         if (FULL || base < N) load_row(W + (size_t)k * ldw + base, cv);
-        overlap();
+        slots.rest_flip();
         if (FULL || base < N) {
             const typename A::Sign sg = A::sign(xold);
 #pragma unroll

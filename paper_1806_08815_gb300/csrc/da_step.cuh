@@ -271,7 +271,7 @@ template <typename Tw, int V, bool FULL, bool TRACE>
 __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_blocks)
     step_kernel_g1(const __grid_constant__ StepParams p)
 {
-    using R_ = WarpReplica<Tw, V>;
+    using R_ = WarpReplica<Tw, V, false, true>;
     using H = typename R_::H;
     if (launch_stopped(p)) return;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_bloc
     const PhiloxKeys& keys = *reinterpret_cast<const PhiloxKeys*>(&p.round_key[0][0]);
     const bool per_rep = p.betas != nullptr;
     const float beta_rep = per_rep ? p.betas[p.temp_of[r]] : 0.f;
-    if (p.t0 < p.t1) rp.draw((uint32_t)p.t0, keys);
+    rp.prep_draws(keys);
+    if (p.t0 < p.t1) rp.draw_pre((uint32_t)p.t0, keys);
     float beta_next = (!per_rep && p.t0 < p.t1) ? p.beta[p.t0] : beta_rep;
     for (long long t = p.t0; t < p.t1; ++t) {
         const float beta = beta_next;

@@ -256,28 +256,44 @@ __device__ __forceinline__ uint32_t gather_word(uint32_t bits, int lane)
 // test (decide_exact).  With E_off = +0 (no offset, or no step without a flip
 // since the last one) the subtraction is left out: it would return delta
 // unchanged.
+// The test is made on t' = s - (24 - kLogBand), s = fma(delta, c, L), instead of
+// t = s - 24: wherever |t| < 12, s lies in [12, 36] and both subtractions are
+// exact (Sterbenz), so t' = t + kLogBand and
+//   t < -kLogBand  <=>  t' < 0      (its sign bit; t' = +0 when t = -kLogBand),
+//   |t| <= kLogBand <=> 0 <= t' <= 2 kLogBand (its bits as an unsigned integer
+//                       at most those of 2^-14: negative t' have bit 31 set);
+// elsewhere both sides agree on a sign far from the band.  The sign bits are
+// shifted into the mask and the band is one unsigned minimum per trial; pairs of
+// trials share one packed fma and one packed add (each lane of a packed
+// operation rounds as the scalar one).
 template <typename A, int V>
 __device__ __forceinline__ uint32_t decide_log(const typename A::H (&h)[V], uint32_t xm, float Eoff, float c,
                                                const float (&L)[V], bool& unsure)
 {
-    uint32_t acc = 0;
-    float tmin = 1.0f;
+    static_assert(V % 2 == 0, "trials are decided in pairs");
+    constexpr float kShift = 24.0f - kLogBand;   // 23.999969482421875, exact in fp32
+    constexpr uint32_t kBandBits = 0x38800000u;  // 2^-14 = 2 kLogBand
+    const float2 cc = make_float2(c, c), sh = make_float2(-kShift, -kShift);
+    uint32_t acc = 0, umin = 0xffffffffu;
+    auto pair = [&](int v, float d0, float d1) {
+        const float2 tp = __fadd2_rn(__ffma2_rn(make_float2(d0, d1), cc, make_float2(L[v], L[v + 1])), sh);
+        const uint32_t b0 = __float_as_uint(tp.x), b1 = __float_as_uint(tp.y);
+        acc = __funnelshift_l(b1, acc, 1);       // bit v + 1, then bit v
+        acc = __funnelshift_l(b0, acc, 1);
+        umin = min(umin, min(b0, b1));
+    };
     if (Eoff == 0.0f) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float t = __fsub_rn(__fmaf_rn(A::delta0(A::signed_field(h[v], (xm >> v) & 1u)), c, L[v]), 24.0f);
-            acc |= (uint32_t)(t < -kLogBand) << v;
-            tmin = fminf(tmin, fabsf(t));
-        }
+        for (int v = V - 2; v >= 0; v -= 2)
+            pair(v, A::delta0(A::signed_field(h[v], (xm >> v) & 1u)),
+                 A::delta0(A::signed_field(h[v + 1], (xm >> (v + 1)) & 1u)));
     } else {
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const float t = __fsub_rn(__fmaf_rn(A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff), c, L[v]), 24.0f);
-            acc |= (uint32_t)(t < -kLogBand) << v;
-            tmin = fminf(tmin, fabsf(t));
-        }
+        for (int v = V - 2; v >= 0; v -= 2)
+            pair(v, A::delta(A::signed_field(h[v], (xm >> v) & 1u), Eoff),
+                 A::delta(A::signed_field(h[v + 1], (xm >> (v + 1)) & 1u), Eoff));
     }
-    unsure = tmin <= kLogBand;
+    unsure = umin <= kBandBits;
     return acc;
 }
 
