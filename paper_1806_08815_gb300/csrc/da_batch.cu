@@ -53,7 +53,10 @@ using step_detail::WarpReplica;
 template <typename Tw, int V, bool SW>
 __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw* W, int ldw, long long t_limit)
 {
-    using R_ = WarpReplica<Tw, V, SW>;
+    // the precomputed draws (PRE) for V <= 16; the V = 32 kernel has no registers left for
+    // them (measured slower)
+    constexpr bool kPre = V <= 16;
+    using R_ = WarpReplica<Tw, V, SW, kPre>;
     using A = step_detail::Arith<Tw>;
     using H = typename R_::H;
     constexpr int nw = V;   // state words per replica (the padded width 32V / 32)
@@ -74,7 +77,12 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
     rp.flips = 0;
     const PhiloxKeys keys(it.seed);
     const long long T = t_limit > 0 ? std::min(t_limit, it.T) : it.T;
-    if (T > 0) rp.draw(0u, keys);
+    if constexpr (kPre) {
+        rp.prep_draws(keys);
+        if (T > 0) rp.draw_pre(0u, keys);
+    } else {
+        if (T > 0) rp.draw(0u, keys);
+    }
     float beta_next = T > 0 ? it.beta[0] : 0.f;
     // the next step count (t + 1) at which the fp32 fields are recomputed: a running
     // target instead of a 64-bit remainder every step
@@ -90,7 +98,10 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
                 next_rec += it.recompute_every;
                 rp.recompute(static_cast<const float*>(it.diag), it.S, it.exact_shift != 0);
                 // the draws of t + 1 again: lg is dead across the recompute, which frees its registers
-                if (t + 1 < T) rp.draw((uint32_t)(t + 1), keys);
+                if (t + 1 < T) {
+                    if constexpr (kPre) rp.draw_pre((uint32_t)(t + 1), keys);
+                    else rp.draw((uint32_t)(t + 1), keys);
+                }
             }
         }
     }

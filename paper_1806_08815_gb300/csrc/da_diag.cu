@@ -8,6 +8,7 @@
 #include "da.h"
 #include "da_device.cuh"
 #include "da_fixed.cuh"
+#include "da_step_common.cuh"
 #include "da_tc.cuh"
 
 namespace {
@@ -53,17 +54,21 @@ __global__ void log_uniform_kernel(const uint32_t* w, float* L, long long n)
     if (i < n) L[i] = da::lg2_draw(w[i]);
 }
 
-// The warp-specialised step's decision for one trial, as WarpReplica::step_log
-// makes it: bit 0 the decision, bit 1 set when it came from the exact test
-// (the trial's s fell in the band).
+// The step kernels' decision for one trial, made by their own decide_log (the
+// trial as both of a pair, x = 0, E_off = +0, so that Delta E = delta) and, when
+// it reports the band, by the exact test decide_exact applies: bit 0 the
+// decision, bit 1 set when it came from the exact test.
 __global__ void accept_log_kernel(const float* delta, const float* beta, const uint32_t* w, uint8_t* out, long long n)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float c = __fmul_rn(beta[i], da::kLog2e);
-    const float t = __fsub_rn(__fmaf_rn(delta[i], c, da::lg2_draw(w[i])), 24.0f);
-    bool acc = t < -da::kLogBand;
-    const bool band = fabsf(t) <= da::kLogBand;
+    const float lg = da::lg2_draw(w[i]);
+    const float h[2] = {delta[i], delta[i]};
+    const float L[2] = {lg, lg};
+    bool band;
+    const uint32_t m = da::step_detail::decide_log<da::step_detail::Arith<float>, 2>(h, 0u, 0.0f, c, L, band);
+    bool acc = (m & 1u) != 0;
     if (band) acc = delta[i] <= 0.0f || da::uniform01(w[i]) < da::exp_neg(-__fmul_rn(beta[i], delta[i]));
     out[i] = (uint8_t)((acc ? 1 : 0) | (band ? 2 : 0));
 }

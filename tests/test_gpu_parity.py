@@ -82,7 +82,9 @@ def test_log_uniform_error_bound(da):
 
 def test_log_domain_decision_matches_exact_test(da):
     """The step kernels decide s = delta beta log2(e) + log2 U against 24 -+ 2^-15
-    and fall back to the exact test inside that band: for trials placed
+    (their decide_log: sign bits of s - (24 - 2^-15), packed pairs, the band by an
+    unsigned minimum; called here through a diagnostic kernel) and fall back to the
+    exact test inside that band: for trials placed
     right at the acceptance boundary (relative offsets 2^-30 .. 2^-8 either side),
     random trials, delta <= 0, beta = 0 and u = 1 its decision equals
     delta <= 0 || u < exp_neg(-fl(beta delta))."""
