@@ -371,6 +371,8 @@ struct WarpReplica {
     // (round(d_i 2^S) + sum_i)).
     // shift: every coupling and linear term reaches the grid by a left shift
     // (the host checked), so fixed_of_f32_shift converts it exactly.
+    // The fields of padding variables (beyond N) are set to 0, their value at the
+    // start of an anneal, so that no old field stays live across the row loop.
     __device__ __forceinline__ void recompute(const float* __restrict__ diag, int S, bool shift = false)
     {
         if (shift) recompute_impl<true>(diag, S);
@@ -419,7 +421,7 @@ struct WarpReplica {
                 hi += (t < 0 ? -1ll : 0ll) + (nlo < lo ? 1ll : 0ll);
                 lo = nlo;
             }
-            if ((valid >> v) & 1u) h[v] = scaled_f32_of(acc[v], S);
+            h[v] = ((valid >> v) & 1u) ? scaled_f32_of(acc[v], S) : H(0);   // padding: 0, so h is dead above
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
