@@ -112,14 +112,69 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
     };
     // Acceptance draws of one step as log2 U (lg2_draw): Philox block q covers
     // variables base + 4q .. + 3.
-    auto draw_step = [&](float (&lg)[V], uint32_t tt) {
+    // The step-invariant Philox words precomputed (as WarpReplica's PRE form) where the
+    // launch bounds leave at least 128 registers a thread and V <= 16; V = 32 and the
+    // 7-blocks-per-SM shapes have no room for them.
+    constexpr int kRegCap = 65536 / (32 * G * OccupancyGV<G, V>::rpb * OccupancyGV<G, V>::min_blocks);
+    constexpr bool kPre = V <= 16 && kRegCap >= 128;
+    constexpr int NP = kPre ? NQ : 1;
+    uint32_t kq1[NP], kq2[NP], kq3[NP], kq4[NP], ku0 = 0;
+    if constexpr (kPre) {
+        const uint64_t pb0 = (uint64_t)kPhiloxMulB * rep;
+        ku0 = (uint32_t)(pb0 >> 32) ^ keys.a[0];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const u32x4 w4 = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
-            lg[4 * q] = lg2_draw(w4.x);
-            lg[4 * q + 1] = lg2_draw(w4.y);
-            lg[4 * q + 2] = lg2_draw(w4.z);
-            lg[4 * q + 3] = lg2_draw(w4.w);
+            const uint64_t pa0 = (uint64_t)kPhiloxMulA * ((uint32_t)(base >> 2) + q);
+            const uint64_t pb1 = (uint64_t)kPhiloxMulB * ((uint32_t)(pa0 >> 32) ^ keys.b[0]);
+            const uint64_t pa2 = (uint64_t)kPhiloxMulA * ((uint32_t)(pb1 >> 32) ^ (uint32_t)pb0 ^ keys.a[1]);
+            kq1[q] = (uint32_t)pa0 ^ keys.b[1];
+            kq2[q] = (uint32_t)pb1 ^ keys.a[2];
+            kq3[q] = (uint32_t)(pa2 >> 32) ^ keys.b[2];
+            kq4[q] = (uint32_t)pa2 ^ keys.b[3];
+        }
+    }
+    auto draw_step = [&](float (&lg)[V], uint32_t tt) {
+        if constexpr (kPre) {
+            const uint64_t P = (uint64_t)kPhiloxMulA * (ku0 ^ tt);
+            const uint32_t hP = (uint32_t)(P >> 32), lP = (uint32_t)P;
+            uint32_t c0[NQ], c1[NQ], c2[NQ], c3[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint64_t pb = (uint64_t)kPhiloxMulB * (hP ^ kq1[q]);
+                c0[q] = (uint32_t)(pb >> 32) ^ kq2[q];
+                c1[q] = (uint32_t)pb;
+                c2[q] = kq3[q] ^ lP;
+                c3[q] = kq4[q];
+            }
+#pragma unroll
+            for (int round = 3; round < 10; ++round) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const uint64_t pa = (uint64_t)kPhiloxMulA * c0[q];
+                    const uint64_t pb = (uint64_t)kPhiloxMulB * c2[q];
+                    c0[q] = (uint32_t)(pb >> 32) ^ c1[q] ^ keys.a[round];
+                    // kq4 carried kb_3 into c3, so round 3 adds no key to it
+                    c2[q] = (uint32_t)(pa >> 32) ^ c3[q] ^ (round == 3 ? 0u : keys.b[round]);
+                    c1[q] = (uint32_t)pb;
+                    c3[q] = (uint32_t)pa;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                lg[4 * q] = lg2_draw(c0[q]);
+                lg[4 * q + 1] = lg2_draw(c1[q]);
+                lg[4 * q + 2] = lg2_draw(c2[q]);
+                lg[4 * q + 3] = lg2_draw(c3[q]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const u32x4 w4 = philox4x32_10((uint32_t)(base >> 2) + q, tt, rep, 0u, keys);
+                lg[4 * q] = lg2_draw(w4.x);
+                lg[4 * q + 1] = lg2_draw(w4.y);
+                lg[4 * q + 2] = lg2_draw(w4.z);
+                lg[4 * q + 3] = lg2_draw(w4.w);
+            }
         }
     };
     float lg[V];
@@ -181,8 +236,8 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
             int cnt = 0;
 #pragma unroll
             for (int u = 0; u < G; ++u) { e[u] = ap[lane * G + u]; cnt += __popc(e[u]); }
+            const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
             const int incl = warp_inclusive_scan(cnt, lane);
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
             if (total == 0) {
                 m += 1;
             } else {
