@@ -85,7 +85,7 @@ def read_bandwidths(da, dev):
 
 
 def recompute_roofline(peaks, peak_src, N, R, n_recompute, rest_s):
-    """Tensor roofline of the exact field recompute (expand + tensor-core kernel + energy sum):
+    """Tensor roofline of the exact field recompute (tensor-core kernel + energy sum):
     time per recompute = (anneal time - step-kernel time) / (periodic recomputes + the final
     evaluation of 2R states, counted as 2); algorithmic work 2 N^2 R flop per recompute of R
     states, executed as 5 f16 digit planes (N = 1024)."""
@@ -98,7 +98,7 @@ def recompute_roofline(peaks, peak_src, N, R, n_recompute, rest_s):
     return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "executed_tflops": 5 * ach, "per_recompute_us": per * 1e6, "peak_source": peak_src,
             "basis": "algorithmic 2 N^2 R flop per recompute; executed = 5 digit planes; time per recompute "
-                     "from the anneal time minus the step-kernel time (includes state expansion and energy sums)"}
+                     "from the anneal time minus the step-kernel time (includes the energy sums)"}
 
 
 def load_peaks():
@@ -753,9 +753,9 @@ def main():
                  "16-byte L1-bypassing reads (da_diag_read_bandwidth), HBM from the measured copy peak"}
     n_step_launches = math.ceil(T / P)
     n_recompute = T // P
-    # init, step launches, 3 per recompute (state expansion, tensor-core recompute, energy sum), the same 3
-    # for the final evaluation, best-state fixup, finalize
-    gpu_launches = 1 + n_step_launches + 3 * n_recompute + 3 + 1 + 1
+    # init, step launches, 2 per recompute (tensor-core recompute with the states expanded in the kernel,
+    # energy sum), the same 2 for the final evaluation, best-state fixup, finalize
+    gpu_launches = 1 + n_step_launches + 2 * n_recompute + 2 + 1 + 1
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

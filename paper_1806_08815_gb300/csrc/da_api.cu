@@ -151,7 +151,7 @@ da_status ensure_ws(da_ctx* c, size_t bytes)
 
 // Workspace carve-up for one anneal-like call.
 struct Layout {
-    size_t h, xs, sc, sums, tca, eex, beta, res, trace, pt, total;
+    size_t h, xs, sc, sums, eex, beta, res, trace, pt, total;
 };
 
 Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_beta, bool with_trace, size_t pt_bytes)
@@ -162,8 +162,7 @@ Layout plan(const da_ctx* c, const StepShape& s, int R, long long T, bool with_b
     L.h = take((size_t)R * s.npad() * 4);
     L.xs = take((size_t)2 * R * s.nwords() * 4);
     L.sc = take((size_t)R * sizeof(ReplicaScalars));
-    L.sums = take((size_t)16 * ((std::max(s.npad(), c->N) + 63) / 64) * 2 * R);
-    L.tca = take(da::tc_state_bytes(c->N, 2 * R));
+    L.sums = take(da::tc_partial_bytes(std::max(s.npad(), c->N), 2 * R));
     L.eex = take((size_t)2 * R * 8);
     L.beta = take(with_beta ? (size_t)T * 4 : 0);
     L.res = take((size_t)4 * R * 8);
@@ -205,7 +204,6 @@ struct RunBuffers {
     ReplicaScalars* sc() const { return reinterpret_cast<ReplicaScalars*>(base + L.sc); }
     long long* sums() const { return reinterpret_cast<long long*>(base + L.sums); }
     long long* eex() const { return reinterpret_cast<long long*>(base + L.eex); }
-    void* tca() const { return base + L.tca; }
 };
 
 StepParams base_params(const da_ctx* c, const RunBuffers& b)
@@ -240,7 +238,7 @@ da_status reset_state(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 da_status evaluate(const da_ctx* c, const RunBuffers& b, cudaStream_t st)
 {
     DA_CU(da::launch_recompute_tc(is_int(c), c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), 2 * b.R, nullptr,
-                                  b.s.npad(), b.eex(), 1, st, b.sums(), b.tca()));
+                                  b.s.npad(), b.eex(), 1, st, b.sums()));
     return DA_OK;
 }
 
@@ -301,7 +299,7 @@ da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long
         if (rec && p.t1 % recompute_every == 0) {
             DA_CU(da::launch_recompute_tc(false, c->tc, c->diag, c->N, c->S, b.x(), b.s.nwords(), b.R, b.h(),
                                           b.s.npad(), reinterpret_cast<long long*>(b.sc()),
-                                          (int)(sizeof(ReplicaScalars) / 8), st, b.sums(), b.tca()));
+                                          (int)(sizeof(ReplicaScalars) / 8), st, b.sums()));
         }
     }
     DA_CU(da::launch_best_fixup(b.R, b.sc(), is_int(c), b.x(), b.bestx(), b.s.nwords(), st));
@@ -774,10 +772,9 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     const size_t words = (size_t)da_words(c->N);
     const size_t xb = align_up((size_t)R * words * 4, 256);
     const size_t hb = align_up((size_t)R * c->N * 4, 256);
-    const size_t sb = align_up((size_t)16 * ((c->N + 63) / 64) * R, 256);
+    const size_t sb = align_up(da::tc_partial_bytes(c->N, R), 256);
     const size_t eb = align_up((size_t)R * 8, 256);
-    const size_t ab = align_up(da::tc_state_bytes(c->N, R), 256);
-    if (da_status e = ensure_ws(c, xb + hb + sb + eb + ab)) return e;
+    if (da_status e = ensure_ws(c, xb + hb + sb + eb)) return e;
     char* base = static_cast<char*>(c->ws);
     uint32_t* xd = reinterpret_cast<uint32_t*>(base);
     void* hd = base + xb;
@@ -785,7 +782,7 @@ static da_status states_common(da_ctx* c, const uint32_t* x, int32_t R, void* h,
     long long* ed = reinterpret_cast<long long*>(base + xb + hb + sb);
     DA_CU(cudaMemcpyAsync(xd, x, (size_t)R * words * 4, cudaMemcpyHostToDevice, st));
     DA_CU(da::launch_recompute_tc(is_int(c), c->tc, c->diag, c->N, c->S, xd, (int)words, R, h ? hd : nullptr, c->N,
-                                  E ? ed : nullptr, 1, st, sums, base + xb + hb + sb + eb));
+                                  E ? ed : nullptr, 1, st, sums));
     std::vector<long long> eh(E ? (size_t)R : 0);
     if (h) DA_CU(cudaMemcpyAsync(h, hd, (size_t)R * c->N * 4, cudaMemcpyDeviceToHost, st));
     if (E) DA_CU(cudaMemcpyAsync(eh.data(), ed, (size_t)R * 8, cudaMemcpyDeviceToHost, st));

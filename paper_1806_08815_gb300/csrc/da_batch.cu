@@ -476,7 +476,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         hi[i] = h;
     }
     // device layout: per item betas, states, scalars, traces, results; per class descriptors
-    std::vector<size_t> o_beta(n), o_xs(n), o_sc(n), o_tr(n), o_eex(n), o_part(n), o_res(n), o_tcs(n);
+    std::vector<size_t> o_beta(n), o_xs(n), o_sc(n), o_tr(n), o_eex(n), o_part(n), o_res(n);
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         const int R = items[i].replicas, nw = hi[i].V;
@@ -485,9 +485,8 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         o_sc[i] = off; off += da::al((size_t)R * sizeof(da::ReplicaScalars));
         o_tr[i] = off; off += items[i].out && items[i].out->trace ? da::al((size_t)R * items[i].steps * 4) : 0;
         o_eex[i] = off; off += da::al((size_t)2 * R * 8);
-        o_part[i] = off; off += da::al((size_t)16 * ((hi[i].N + 63) / 64) * 2 * R);
+        o_part[i] = off; off += da::al(da::tc_partial_bytes(hi[i].N, 2 * R));
         o_res[i] = off; off += da::al((size_t)4 * R * 8);
-        o_tcs[i] = off; off += da::al(da::tc_state_bytes(hi[i].N, 2 * R));   // states of the exact evaluation
     }
     std::map<std::pair<int, int>, BatchClass> classes;
     for (int i = 0; i < n; ++i) {
@@ -649,8 +648,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
             // context holds the operand of its couplings)
             if (da::launch_recompute_tc(hi[i].int8, da::ctx_tc_operand(items[i].ctx), hi[i].diag, hi[i].N, hi[i].S,
                                         reinterpret_cast<uint32_t*>(base + o_xs[i]), nw, 2 * R, nullptr, hi[i].N, eex,
-                                        1, st, reinterpret_cast<long long*>(base + o_part[i]),
-                                        base + o_tcs[i]) != cudaSuccess)
+                                        1, st, reinterpret_cast<long long*>(base + o_part[i])) != cudaSuccess)
                 capture_ok = false;
             da::batch_finalize_kernel<<<(R + 127) / 128, 128, 0, st>>>(
                 hi[i].int8, R, reinterpret_cast<da::ReplicaScalars*>(base + o_sc[i]), eex,

@@ -138,13 +138,15 @@ void tc_operand_free(TcOperand* op);   // for operands from tc_operand_build
 size_t tc_operand_bytes(int wtype, int N);
 cudaError_t tc_operand_build_in(int wtype, const void* W, const void* diag, int N, int ldw, int S, void* mem,
                                 TcOperand* op, cudaStream_t st);
-// Workspace for R states expanded to f16 (state_ws of launch_recompute_tc).
-size_t tc_state_bytes(int N, int R);
+// Bytes of launch_recompute_tc's scratch for R states and `rows` = max(npad, N)
+// field columns (hout given) or N (none): one 128-bit partial energy per state and
+// 64-column tile.
+size_t tc_partial_bytes(int rows, int R);
 // Arguments as launch_recompute (is_int8: integer couplings of either width,
-// int32 fields); scratch must hold 16 * ceil(max(npad, N) / 64) * R bytes.
+// int32 fields); with E, scratch must hold tc_partial_bytes(rows, R) bytes.
 cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
                                 const uint32_t* xs, int nw, int R, void* hout, int npad, long long* E, int Estride,
-                                cudaStream_t st, long long* scratch, void* state_ws);
+                                cudaStream_t st, long long* scratch);
 
 // PT exchange (da_pt.cu).
 cudaError_t launch_pt_exchange(bool is_int8, const float* betas, int K, int L,

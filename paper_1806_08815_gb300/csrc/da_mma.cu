@@ -15,17 +15,23 @@
 // integers, adds the fixed-point diagonal and rounds once, exactly like the
 // CUDA-core form.
 //
-// Operands are laid out in HBM in the tensor core's canonical K-major layout
-// (8-row x 16-byte core matrices, [K chunk][row group][8][8] halves per tile),
-// so every pipeline stage is two contiguous bulk copies: the digit planes of
-// the instance are built once per context, the states are expanded from bits
-// to f16 before each recompute.
+// Operands use the tensor core's canonical K-major layout (8-row x 16-byte
+// core matrices, [K chunk][row group][8][8] halves per tile).  The digit planes
+// of the instance are built once per context in that layout in HBM, so a
+// pipeline stage takes them in one contiguous bulk copy; the states are not
+// staged in HBM at all: two warps of the block expand the tile's state bits
+// (2 words per state and stage) to f16 {0, 1} directly into the stage.
 //
-// Block: 4 warps.  Warp 0 allocates tensor memory and one of its threads
-// issues the bulk copies of a 3-stage ring; one thread of warp 1 issues the
+// Block: 16 warps, 128 states x 64 variables.  Warp 0 allocates tensor memory
+// and one of its threads issues the digit planes' bulk copies into a 3-stage
+// ring; warps 2-3 write the stage's state tile (the words of the next chunk
+// loaded while the current one is written); one thread of warp 1 issues the
 // MMAs (4 K-steps of 16 per stage, one per digit plane each) and commits the
-// stage back to the copier; then all 4 warps read their 32 TMEM lanes (one
-// state each) and write fields and 128-bit partial energies.
+// stage back to both producers; then all 16 warps read their TMEM lanes (warp
+// w: states 32 (w % 4).., 16 variables from 16 (w / 4)) and write fields and
+// 128-bit partial energies.  (32-variable tiles, two blocks an SM, measured
+// slower: every block expands its states again, and at 6 digit planes only one
+// block fits.)
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -44,7 +50,9 @@ constexpr int kBM = 128;   // states per tile (TMEM lanes)
 constexpr int kBN = 64;    // variables per tile (TMEM columns per digit plane)
 constexpr int kBK = 64;    // couplings per pipeline stage
 constexpr int kStages = 3;
-constexpr int kThreads = 512;   // 16 warps: warp w reads TMEM lanes 32 (w % 4).., columns 16 (w / 4)..
+constexpr int kThreads = 128 * (kBN / 16);   // warp w reads TMEM lanes 32 (w % 4).., columns 16 (w / 4)..
+constexpr int kMinBlocks = 512 / kThreads;   // blocks per SM the launch bounds plan for
+constexpr int kExpanders = 64;  // threads of warps 2-3: the state tile of each stage, 2 states each
 constexpr uint32_t kATile = kBM * kBK * 2;   // bytes of one state tile (16 KB)
 constexpr uint32_t kBTile = kBN * kBK * 2;   // bytes of one digit-plane tile (8 KB)
 constexpr uint32_t kWaitLimit = 1u << 26;    // polls of one mbarrier before giving up ...
@@ -88,8 +96,8 @@ __global__ void build_digits_kernel(const void* __restrict__ W, int N, int ldw, 
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= total) return;
     const int g = (int)(idx & 7);
-    const int row = (int)((idx >> 3) & 63);
-    const long long tile = idx >> 9;           // itile * kchunks + kchunk
+    const int row = (int)((idx >> 3) % kBN);
+    const long long tile = idx / (8 * kBN);    // itile * kchunks + kchunk
     const int kchunk = (int)(tile % kchunks);
     const int itile = (int)(tile / kchunks);
     const int i = itile * kBN + row;
@@ -116,31 +124,15 @@ __global__ void build_digits_kernel(const void* __restrict__ W, int N, int ldw, 
     }
 }
 
-// States as f16 {0, 1}: one thread per 8 variables of one state, in the
-// order of the destination (coalesced 16-byte stores).
-__global__ void expand_states_kernel(const uint32_t* __restrict__ xs, int nw, int N, int R, int kchunks,
-                                     __half* __restrict__ A, long long total)
+// Two f16 values {0, 1} from two state bits (bit 0 -> the lower half).
+__device__ __forceinline__ uint32_t half_pair(uint32_t two)
 {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int row = (int)(idx & 127);
-    const int kc = (int)((idx >> 7) & 7);
-    const long long tile = idx >> 10;          // rtile * kchunks + kchunk
-    const int kchunk = (int)(tile % kchunks);
-    const int rtile = (int)(tile / kchunks);
-    const int r = rtile * kBM + row;
-    const int j8 = kchunk * kBK + kc * 8;
-    uint32_t byte = 0;
-    if (r < R && j8 < N) {
-        byte = (xs[(size_t)r * nw + (j8 >> 5)] >> (j8 & 31)) & 0xFFu;
-        if (N - j8 < 8) byte &= (1u << (N - j8)) - 1u;
-    }
-    __align__(16) unsigned short h[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) h[e] = ((byte >> e) & 1u) ? 0x3C00 : 0;   // f16 1.0 / 0.0
-    __half* dst = A + (size_t)tile * (kBM * kBK) + core_offset(kBM, row, kc * 8);
-    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+    return (two & 1u) * 0x3C00u + (two >> 1) * 0x3C000000u;   // f16 1.0 = 0x3C00
 }
+
+// Makes this thread's shared-memory writes visible to the asynchronous proxy
+// (the tensor cores' operand reads).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 struct I128 {
     unsigned long long lo;
@@ -155,10 +147,9 @@ __device__ __forceinline__ void i128_add(I128& a, long long v)
 }
 
 struct TcParams {
-    const __half* A;        // [rtiles][kchunks] state tiles
     const __half* B;        // [ceil(N/64)][kchunks][limbs] digit-plane tiles
     const long long* dfix;  // [kchunks * 64] fixed-point diagonal, zero-padded
-    const uint32_t* xs;     // [R][nw]
+    const uint32_t* xs;     // [R][nw] state bits (x_i = bit i % 32 of word i / 32)
     void* hout;             // [R][npad] or null
     I128* part;             // [gridDim.x][R] or null
     int* err;
@@ -174,11 +165,10 @@ __device__ __forceinline__ uint32_t field_bits(long long acc, int S)
 }
 
 template <bool INT8>
-__global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_constant__ TcParams p)
+__global__ void __launch_bounds__(kThreads, kMinBlocks) recompute_tc_kernel(const __grid_constant__ TcParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_fail;
-    __shared__ I128 s_part[kThreads / kBM][kBM];   // partial energies of the 4 column groups
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int i0 = blockIdx.x * kBN;
@@ -205,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&full[s], 1 + kExpanders);   // the copier's expect_tx and every expander
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(done, 1);
@@ -223,9 +213,9 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
     const int nk = p.kchunks;
 
     if (warp == 0) {
-        if (lane == 0) {   // bulk-copy issuer
-            const __half* a_src = p.A + (size_t)blockIdx.y * nk * (kBM * kBK);
+        if (lane == 0) {   // bulk-copy issuer: the digit planes of each stage
             const __half* b_src = p.B + (size_t)blockIdx.x * nk * p.limbs * (kBN * kBK);
+            const uint32_t b_bytes = (uint32_t)p.limbs * kBTile;
             for (int c = 0; c < nk; ++c) {
                 const int s = c % kStages;
                 const uint32_t u = (uint32_t)(c / kStages);
@@ -234,10 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
                     break;
                 }
                 uint8_t* st = sm + s * stage_bytes;
-                tc::mbar_arrive_expect_tx(&full[s], stage_bytes);
-                tc::bulk_g2s(st, a_src + (size_t)c * (kBM * kBK), kATile, &full[s]);
-                tc::bulk_g2s(st + kATile, b_src + (size_t)c * p.limbs * (kBN * kBK), (uint32_t)p.limbs * kBTile,
-                             &full[s]);
+                tc::mbar_arrive_expect_tx(&full[s], b_bytes);
+                tc::bulk_g2s(st + kATile, b_src + (size_t)c * p.limbs * (kBN * kBK), b_bytes, &full[s]);
             }
         }
         __syncwarp();
@@ -269,6 +257,53 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
             tc::mma_commit(done);
         }
         __syncwarp();
+    } else if (warp == 2 || warp == 3) {
+        // the stage's state tile: thread e writes states e and e + 64 of the tile, 64
+        // couplings each (2 state words) as eight 16-byte rows of f16 {0, 1} in the
+        // canonical K-major layout; bits beyond N and states beyond R are 0
+        const int e = (int)threadIdx.x - 64;
+        // the two states' words of chunk c: loaded one chunk ahead, so that their latency
+        // overlaps the wait for the stage and the writes of the chunk before
+        auto load = [&](int c, uint32_t (&wv)[4]) {
+            const int w0 = (c * kBK) >> 5;               // < nw: c < kchunks = ceil(N / 64)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int r = blockIdx.y * kBM + e + 64 * hh;
+                const uint32_t* xr = p.xs + (size_t)r * p.nw;
+                wv[2 * hh] = r < p.R ? xr[w0] : 0u;
+                wv[2 * hh + 1] = r < p.R && w0 + 1 < p.nw ? xr[w0 + 1] : 0u;
+            }
+        };
+        uint32_t cur[4], nxt[4] = {0u, 0u, 0u, 0u};
+        load(0, cur);
+        for (int c = 0; c < nk; ++c) {
+            const int s = c % kStages;
+            const uint32_t u = (uint32_t)(c / kStages);
+            if (c + 1 < nk) load(c + 1, nxt);
+            if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1u, kWaitLimit, kWaitNs)) {
+                s_fail = 1;
+                break;
+            }
+            uint8_t* st = sm + s * stage_bytes;
+            const int nvalid = min(kBK, p.N - c * kBK);
+            const uint64_t vmask = nvalid >= 64 ? ~0ull : ((1ull << nvalid) - 1ull);
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int row = e + 64 * hh;
+                const uint64_t bits = (((uint64_t)cur[2 * hh + 1] << 32) | cur[2 * hh]) & vmask;
+#pragma unroll
+                for (int kc = 0; kc < 8; ++kc) {
+                    const uint32_t b = (uint32_t)(bits >> (8 * kc)) & 0xFFu;
+                    const uint4 v = make_uint4(half_pair(b & 3u), half_pair((b >> 2) & 3u), half_pair((b >> 4) & 3u),
+                                               half_pair(b >> 6));
+                    *reinterpret_cast<uint4*>(st + 2 * core_offset(kBM, row, kc * 8)) = v;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+            fence_proxy_async_smem();
+            tc::mbar_arrive(&full[s]);
+        }
     }
 
     // epilogue: state r = TMEM lane m, variables i0 + 16 cg .. + 15
@@ -322,6 +357,9 @@ __global__ void __launch_bounds__(kThreads, 1) recompute_tc_kernel(const __grid_
             }
         }
     }
+    // partial energies of the 2 column groups, in the first stage's memory: every bulk
+    // copy has landed and every MMA has read its operands once `done` has completed
+    I128 (*s_part)[kBM] = reinterpret_cast<I128 (*)[kBM]>(sm);
     s_part[cg][m] = esum;
 
     tc::fence_before_sync();
@@ -374,11 +412,9 @@ void tc_digits(int wtype, int N, int* bits, int* limbs)
     *limbs = (64 - L + b - 1) / b;
 }
 
-size_t tc_state_bytes(int N, int R)
+size_t tc_partial_bytes(int rows, int R)
 {
-    const size_t kchunks = (size_t)(N + kBK - 1) / kBK;
-    const size_t rtiles = (size_t)(R + kBM - 1) / kBM;
-    return rtiles * kchunks * kATile;
+    return (size_t)16 * (size_t)((rows + kBN - 1) / kBN) * (size_t)R;
 }
 
 // Bytes of the operand's three parts: digit planes, fixed-point diagonal, error flag.
@@ -475,7 +511,6 @@ cudaError_t prepare_tc_kernels()
     prefer_shared<build_digits_kernel<float>>();
     prefer_shared<build_dfix_kernel<false>>();
     prefer_shared<build_dfix_kernel<true>>();
-    prefer_shared<expand_states_kernel>();
     prefer_shared<recompute_tc_kernel<false>>();
     prefer_shared<recompute_tc_kernel<true>>();
     cudaError_t e = cudaFuncSetAttribute(recompute_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -488,7 +523,7 @@ cudaError_t prepare_tc_kernels()
 
 cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* diag, int N, int S,
                                 const uint32_t* xs, int nw, int R, void* hout, int npad, long long* E, int Estride,
-                                cudaStream_t st, long long* scratch, void* state_ws)
+                                cudaStream_t st, long long* scratch)
 {
     if (R <= 0) return cudaSuccess;
     // the dynamic shared-memory limit of each kernel form, set once per device
@@ -513,18 +548,9 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
     }
 
     const int rtiles = (R + kBM - 1) / kBM;
-    const long long total = (long long)rtiles * op.kchunks * kBM * 8;
-    const int tb = 256;
-    __half* A = static_cast<__half*>(state_ws);
-    prefer_shared<expand_states_kernel>();
-    expand_states_kernel<<<(unsigned)((total + tb - 1) / tb), tb, 0, st>>>(xs, nw, N, R, op.kchunks, A, total);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
     const int rows = hout ? std::max(npad, N) : N;
     const int itiles = (rows + kBN - 1) / kBN;
     TcParams p;
-    p.A = A;
     p.B = static_cast<const __half*>(op.B);
     p.dfix = op.dfix;
     p.xs = xs;
@@ -547,7 +573,7 @@ cudaError_t launch_recompute_tc(bool is_int8, const TcOperand& op, const void* d
         recompute_tc_kernel<true><<<grid, kThreads, smem, st>>>(p);
     else
         recompute_tc_kernel<false><<<grid, kThreads, smem, st>>>(p);
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !E) return e;
     return launch_energy_sum(is_int8, scratch, itiles, R, S, E, Estride, st);
 }

@@ -91,7 +91,7 @@ struct Req {
     char* dmem = nullptr;
     // offsets into dmem
     size_t o_W = 0, o_Wf = 0, o_diag = 0, o_beta = 0, o_h = 0, o_xs = 0, o_sc = 0, o_part = 0, o_eex = 0, o_E = 0,
-           o_flips = 0, o_tc = 0, o_tcs = 0, o_item = 0;
+           o_flips = 0, o_tc = 0, o_item = 0;
     bool resident = false;            // the whole anneal in one launch, replica state in registers
     da::BatchItemDev item{};          // its descriptor (copied to dmem + o_item)
     da::TcOperand tc;                 // fp32 requests: the tensor-core operand of W (in dmem)
@@ -177,15 +177,15 @@ void plan_request(Req& q)
     q.o_h = take((size_t)R * sh.npad() * 4);
     q.o_xs = take((size_t)2 * R * q.xs_stride * 4);
     q.o_sc = take((size_t)R * sizeof(da::ReplicaScalars));
-    q.o_part = take((size_t)16 * ((std::max(sh.npad(), q.N) + 63) / 64) * 2 * R);
+    // partial energies of the exact evaluation: 64-column tiles on the tensor cores and on the
+    // CUDA cores (integer requests)
+    q.o_part = take(da::tc_partial_bytes(std::max(sh.npad(), q.N), 2 * R));
     q.o_eex = take((size_t)2 * R * 8);
     q.o_E = take((size_t)3 * R * 8);
     q.o_flips = take((size_t)R * 8);
     if (q.resident) q.o_item = take(sizeof(da::BatchItemDev) + 16);   // descriptor, then the work counter
-    if (!q.integer) {   // the tensor-core recompute: operand of W, states of up to 2R replicas
+    if (!q.integer)     // the tensor-core recompute's operand of W
         q.o_tc = take(da::tc_operand_bytes(da::kWFp32, q.N));
-        q.o_tcs = take(da::tc_state_bytes(q.N, 2 * R));
-    }
     q.bytes = o;
     q.qcopy = al256((size_t)q.N * q.N * 4);
 }
@@ -324,10 +324,10 @@ bool admit(da_server* s, Req& q, long long& launches)
         if (P > 0 && p.t1 % P == 0) {
             if (!cu_ok(da::launch_recompute_tc(false, q.tc, diag, q.N, q.inst.S, xs, sh.nwords(), R, h, sh.npad(),
                                                reinterpret_cast<long long*>(sc), (int)(sizeof(da::ReplicaScalars) / 8),
-                                               st, part, q.dmem + q.o_tcs),
+                                               st, part),
                        q, "recompute"))
                 return false;
-            launches += 3;
+            launches += 2;
         }
     }
     if (!cu_ok(da::launch_best_fixup(R, sc, q.integer, xs, xs + (size_t)R * q.xs_stride, q.xs_stride, st), q,
@@ -338,7 +338,7 @@ bool admit(da_server* s, Req& q, long long& launches)
                                                  nullptr, sh.npad(), eex, 1, st, part),
                           q, "evaluate")
                   : cu_ok(da::launch_recompute_tc(false, q.tc, diag, q.N, q.inst.S, xs, sh.nwords(), 2 * R, nullptr,
-                                                  sh.npad(), eex, 1, st, part, q.dmem + q.o_tcs),
+                                                  sh.npad(), eex, 1, st, part),
                           q, "evaluate");
     if (!ev_ok) return false;
     da::prefer_shared<da::serve_finalize_kernel>();
