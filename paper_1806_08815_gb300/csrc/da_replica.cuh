@@ -66,9 +66,12 @@ struct WarpReplica {
 
     // The test of Algorithm 2's result: a strictly lower tracked energy than any
     // seen makes the current state the best one.  It is made one step late (x is
-    // unchanged until the next flip), while the next step's row of W is in flight
-    // (or once it is known that nothing flips), so that the fp64 compare stays off
-    // the chain from the trials to the row load; and after any recompute of the step.
+    // unchanged until the next flip), and after any recompute of the step.  For
+    // V >= 8 it runs while the next step's row of W is in flight (or once it is
+    // known that nothing flips), so that the fp64 compare stays off the chain from
+    // the trials to the row load; at V = 4, whose short row leaves no room for it
+    // there, it runs before the count (measured: the late test is slower there).
+    static constexpr bool kTestUnderRow = V >= 8;
     __device__ __forceinline__ void flush_best()
     {
         if (chk) {
@@ -316,12 +319,13 @@ struct WarpReplica {
 
     // (c) of a step with acceptance mask accm: the uniform choice among the
     // accepted trials, the best-state test left by the previous step (under the
-    // row load), the flip and the field update, with `slots` placed as described
-    // above.  Returns the flipped index or -1.
+    // row load, or first at V = 4), the flip and the field update, with `slots`
+    // placed as described above.  Returns the flipped index or -1.
     template <bool FULL, class Keys, class Slots>
     __device__ __forceinline__ int choose_and_flip(long long t, uint32_t accm, const Keys& keys, Slots& slots)
     {
         if constexpr (!FULL) accm &= valid;
+        if constexpr (!kTestUnderRow) flush_best();
 
         const int cnt = __popc(accm);
         const int total = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
@@ -330,7 +334,7 @@ struct WarpReplica {
         scan_levels<0>(incl, slots);
         if (total == 0) {
             m += 1;
-            flush_best();
+            if constexpr (kTestUnderRow) flush_best();
             slots.rest_none();
             return -1;
         }
@@ -352,7 +356,7 @@ struct WarpReplica {
         const int k = own * V + vk;
         Tw cv[V];
         if (FULL || base < N) load_row(W + (size_t)k * ldw + base, cv);
-        flush_best();      // x is still the state after the previous step
+        if constexpr (kTestUnderRow) flush_best();   // x is still the state after the previous step
         slots.rest_flip();
         if (FULL || base < N) {
             const typename A::Sign sg = A::sign(xold);
