@@ -205,13 +205,10 @@ def _hits_tts(best, E_ref, tau_run):
     return dict(hits=y, runs=r, theta=theta, tts99_s=tau_run * R99)
 
 
-def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
-    """Batched launch: n_inst fully connected instances, N uniform in {64..1024}, half bimodal (int8),
-    half Gaussian (fp32, exact recompute every 1024 steps), R replicas each, one persistent CUDA-graph
-    launch.  Compared with the plain one-launch-per-step form run by itself, instance after instance,
-    on a sample of the same instances (plain_per_class per coupling type and size) for the full T
-    steps with the same schedules and seeds: trials/s of both, and TTS99 of both at the hit rate each
-    measures against the instance's best energy over the runs of both forms."""
+def batched_jobs(da, instances, n_inst=512, R=64, T=10_000, keep_Q=False):
+    """The batched workload's items: n_inst SK instances, N uniform in {64, ..., 1024}, even items
+    bimodal (int8, beta linear 0.05 -> 3, offset 1), odd items Gaussian (fp32, beta linear 0.1 -> 10,
+    recompute every 1024), item i annealed with seed i.  Returns (jobs, [(bimodal, N)])."""
     rng = np.random.default_rng(1234)
     sizes = rng.choice([64, 128, 256, 512, 1024], n_inst)
     jobs, meta = [], []
@@ -221,7 +218,20 @@ def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
         beta = instances.beta_linear(0.05, 3.0, T) if bim else instances.beta_linear(0.1, 10.0, T)
         jobs.append(dict(ctx=da.da_create(q.Q), beta=beta, offset_inc=1.0 if bim else 0.0, replicas=R, seed=i,
                          recompute_every=0 if bim else 1024))
+        if keep_Q:
+            jobs[-1]["Q"] = q.Q
         meta.append((bim, int(N)))
+    return jobs, meta
+
+
+def run_batched(da, instances, n_inst=512, R=64, T=10_000, plain_per_class=2):
+    """Batched launch: n_inst fully connected instances, N uniform in {64..1024}, half bimodal (int8),
+    half Gaussian (fp32, exact recompute every 1024 steps), R replicas each, one persistent CUDA-graph
+    launch.  Compared with the plain one-launch-per-step form run by itself, instance after instance,
+    on a sample of the same instances (plain_per_class per coupling type and size) for the full T
+    steps with the same schedules and seeds: trials/s of both, and TTS99 of both at the hit rate each
+    measures against the instance's best energy over the runs of both forms."""
+    jobs, meta = batched_jobs(da, instances, n_inst, R, T)
     da.da_batch_anneal(jobs[:8])                      # warm-up
     outs, el = da.da_batch_anneal(jobs)               # (the tuner probes each class before the graph runs)
     config = da.da_batch_describe()
@@ -382,6 +392,20 @@ def _serve_stream(da, pool, betas, picks, gaps, R, T, budget, resident_max_n=0):
     return res, t1 - t0, stats
 
 
+def served_pool(instances, T=50_000, rng=None):
+    """The served workload's instances: 24 SK QUBOs with N log-uniform in [256, 8192], even ones
+    bimodal (int8; beta linear 0.05 -> 3, offset 1), odd ones Gaussian (fp32; beta linear 0.1 -> 10,
+    recompute every 1024).  Returns (pool, {bimodal: beta schedule})."""
+    rng = np.random.default_rng(99) if rng is None else rng
+    pool = []
+    for i in range(24):
+        N = int(round(np.exp(rng.uniform(np.log(256), np.log(8192)))))
+        bim = i % 2 == 0
+        pool.append(instances.sk_bimodal(N, 3000 + i) if bim else instances.sk_gaussian(N, 3000 + i))
+    betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
+    return pool, betas
+
+
 def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 << 30, sustained_req=512,
                sustained_rate=40.0, plain_max=6, resident_max_n=0):
     """Serving: Poisson arrivals (mean `rate` req/s) of fully connected QUBOs, N log-uniform in
@@ -390,12 +414,7 @@ def run_served(da, instances, n_req=64, rate=200.0, R=32, T=50_000, budget=120 <
     form on the requests it can take (N <= 1024), run one after another with the same seeds:
     trials/s and per-request TTS99 of both forms against the best energy of both."""
     rng = np.random.default_rng(99)
-    pool = []
-    for i in range(24):
-        N = int(round(np.exp(rng.uniform(np.log(256), np.log(8192)))))
-        bim = i % 2 == 0
-        pool.append(instances.sk_bimodal(N, 3000 + i) if bim else instances.sk_gaussian(N, 3000 + i))
-    betas = {True: instances.beta_linear(0.05, 3.0, T), False: instances.beta_linear(0.1, 10.0, T)}
+    pool, betas = served_pool(instances, T, rng)
     picks = rng.integers(0, len(pool), n_req)
     gaps = rng.exponential(1.0 / rate, n_req)
     res, makespan, stats = _serve_stream(da, pool, betas, picks, gaps, R, T, budget, resident_max_n)

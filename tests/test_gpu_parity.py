@@ -254,6 +254,7 @@ def test_full_size_sk_n1024_sampled_replicas(da, inst):
     q = inst.sk_gaussian(C3["N"], C3["instance_seed"])
     beta = inst.beta_linear(C3["beta0"], C3["beta1"], C3["steps"])
     ctx = da.da_create(q.Q)
+    da.binding.da_tune_shape(ctx, C3["replicas"])      # the launch shape the benchmark times
     got = da.da_anneal(ctx, beta, C3["inc"], C3["replicas"], C3["seed"], recompute_every=C3["recompute_every"])
     for r in (0, 777):
         ref = oracle.da_anneal(q.Q, beta, R=1, seed=C3["seed"], inc=C3["inc"], replica_base=r,
@@ -262,6 +263,40 @@ def test_full_size_sk_n1024_sampled_replicas(da, inst):
         assert np.array_equal(got["best_x"][r], ref["x_best"][0])
         assert got["flips"][r] == ref["flips"][0]
         assert abs(got["best_E"][r] - oracle.energy(q.Q, ref["x_best"])[0]) <= 1e-12 * abs(got["best_E"][r])
+
+
+def test_full_size_batched_sampled_replicas(da, inst):
+    """The benchmark's batched launch (512 instances, N in {64, ..., 1024}, half int8 / half fp32,
+    64 replicas, 10^4 steps, the tuner's configuration per class) checked on sampled replicas of
+    one item per coupling type at the smallest and largest size, each rerun alone by the oracle."""
+    import oracle
+    from bench import batched_jobs
+    import concurrent.futures
+    jobs, meta = batched_jobs(da, inst, keep_Q=True)
+    picked = [meta.index(cls) for cls in ((True, 64), (False, 64), (True, 1024), (False, 1024))]
+    sampled = [(i, r) for i in picked for r in (0, 37)]
+
+    def rerun(ir):
+        j = jobs[ir[0]]
+        return oracle.da_anneal(j["Q"], j["beta"], R=1, seed=j["seed"], inc=j["offset_inc"], replica_base=ir[1],
+                                recompute_every=j["recompute_every"])
+
+    ex = concurrent.futures.ThreadPoolExecutor(NT)     # the oracle's C calls run beside the GPU work
+    refs = {ir: ex.submit(rerun, ir) for ir in sampled}
+    outs, el = da.binding.da_batch_anneal(jobs)
+    assert el > 0
+    for i in picked:
+        j, o = jobs[i], outs[i]
+        for r in (0, 37):
+            ref = refs[(i, r)].result()
+            assert np.array_equal(o["final_x"][r], ref["x_final"][0]), (meta[i], r)
+            assert np.array_equal(o["best_x"][r], ref["x_best"][0]), (meta[i], r)
+            assert o["flips"][r] == ref["flips"][0], (meta[i], r)
+            Eb = oracle.energy(j["Q"], ref["x_best"])[0]
+            if meta[i][0]:
+                assert o["best_E"][r] == Eb
+            else:
+                assert abs(o["best_E"][r] - Eb) <= 1e-12 * max(1.0, abs(Eb))
 
 
 def test_edge_cases(da, inst):

@@ -6,6 +6,8 @@ as chunked launches on a stream of its own, concurrently with the others, in
 the launch shape the server picks for the load); each must equal da_anneal on
 the same instance, schedule and seed, bit for bit.  A budget that admits one request at a time must give the same
 results, and a request that can never fit is refused."""
+import concurrent.futures
+
 import numpy as np
 import pytest
 
@@ -166,3 +168,48 @@ def test_resident_requests_equal_chunked_ones(da):
         da.da_poll(long_req, 60_000_000)
     assert e.value.status == 8 and time.perf_counter() - t0 < 1.5
     srv.close()
+
+
+def test_full_size_served_requests_sampled_replicas(da):
+    """The served workload at full size: its largest fp32 and int8 instances and two smaller
+    ones (32 replicas, 5*10^4 steps, recompute every 1024 for fp32, HBM budget 120 GB) run
+    together through the request loop; sampled replicas of the two largest are rerun alone by
+    the oracle (final and best states, flips bit for bit; best energies exact for int8,
+    within 1e-12 relative for fp32)."""
+    import oracle
+    from bench import served_pool
+    from paper_1806_08815_gb300 import instances as inst
+    pool, betas = served_pool(inst)
+    big_f = max((i for i, q in enumerate(pool) if not q.bimodal), key=lambda i: pool[i].N)
+    big_i = max((i for i, q in enumerate(pool) if q.bimodal), key=lambda i: pool[i].N)
+    small = [i for i, q in enumerate(pool) if q.N <= 1024][:2]
+    picks = [big_f, big_i] + small
+    sampled = ((big_f, 5), (big_i, 20))
+
+    def rerun(k):
+        i, r = sampled[k]
+        q = pool[i]
+        return oracle.da_anneal(q.Q, betas[q.bimodal], R=1, seed=k, inc=1.0 if q.bimodal else 0.0,
+                                replica_base=r, recompute_every=0 if q.bimodal else 1024)
+
+    ex = concurrent.futures.ThreadPoolExecutor(2)      # the oracle's C calls run beside the GPU work
+    refs = [ex.submit(rerun, k) for k in range(len(sampled))]
+    srv = da.Server(120 << 30, 64)
+    reqs = []
+    for k, i in enumerate(picks):
+        q = pool[i]
+        reqs.append(da.da_submit(srv, q.Q, betas[q.bimodal], 1.0 if q.bimodal else 0.0, 32, k,
+                                 0 if q.bimodal else 1024))
+    outs = [da.da_poll(r, 600_000_000) for r in reqs]
+    srv.close()
+    for k, (i, r) in enumerate(sampled):
+        q, o = pool[i], outs[k]
+        ref = refs[k].result()
+        assert np.array_equal(o["final_x"][r], ref["x_final"][0]), (q.N, r)
+        assert np.array_equal(o["best_x"][r], ref["x_best"][0]), (q.N, r)
+        assert o["flips"][r] == ref["flips"][0], (q.N, r)
+        Eb = float(oracle.energy(q.Q, ref["x_best"])[0])
+        if q.bimodal:
+            assert o["best_E"][r] == Eb
+        else:
+            assert abs(o["best_E"][r] - Eb) <= 1e-12 * max(1.0, abs(Eb))
