@@ -22,7 +22,8 @@ namespace step_detail {
 // PRE: the step-invariant part of each Philox block is computed once per launch
 // (prep_draws) and the draws of every step start from it (draw_pre); four more
 // words per block live in registers, for kernels that have them to spare.
-template <typename Tw, int V, bool SW = false, bool PRE = false>
+// LATE: the best-state test is made under the row load (see flush_best).
+template <typename Tw, int V, bool SW = false, bool PRE = false, bool LATE = (V >= 8)>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -66,12 +67,14 @@ struct WarpReplica {
 
     // The test of Algorithm 2's result: a strictly lower tracked energy than any
     // seen makes the current state the best one.  It is made one step late (x is
-    // unchanged until the next flip), and after any recompute of the step.  For
-    // V >= 8 it runs while the next step's row of W is in flight (or once it is
-    // known that nothing flips), so that the fp64 compare stays off the chain from
-    // the trials to the row load; at V = 4, whose short row leaves no room for it
-    // there, it runs before the count (measured: the late test is slower there).
-    static constexpr bool kTestUnderRow = V >= 8;
+    // unchanged until the next flip), and after any recompute of the step.  With
+    // LATE (by default for V >= 8) it runs while the next step's row of W is in
+    // flight (or once it is known that nothing flips), so that the fp64 compare
+    // stays off the chain from the trials to the row load; otherwise before the
+    // count.  Measured: the late test is slower at V = 4, whose short row leaves no
+    // room for it, and for replicas at fixed temperatures (parallel tempering),
+    // whose low-temperature steps mostly flip nothing.
+    static constexpr bool kTestUnderRow = LATE;
     __device__ __forceinline__ void flush_best()
     {
         if (chk) {

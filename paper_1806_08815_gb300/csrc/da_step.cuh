@@ -321,12 +321,14 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
     }
 }
 
-// G = 1: one warp per replica, the body of WarpReplica.
-template <typename Tw, int V, bool FULL, bool TRACE>
+// G = 1: one warp per replica, the body of WarpReplica.  PT: the launch anneals
+// replicas at fixed per-replica temperatures (p.betas), where the best-state test
+// stays before the count.
+template <typename Tw, int V, bool FULL, bool TRACE, bool PT = false>
 __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_blocks)
     step_kernel_g1(const __grid_constant__ StepParams p)
 {
-    using R_ = WarpReplica<Tw, V, false, true>;
+    using R_ = WarpReplica<Tw, V, false, true, !PT && V >= 8>;
     using H = typename R_::H;
     if (launch_stopped(p)) return;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -519,11 +521,14 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
             }
             return cudaGetLastError();
         }
+        const bool pt = p.betas != nullptr;
         if (full) {
             if (trace) launch_shared<step_kernel_g1<Tw, V, true, true>>(blocks, threads, 0, st, p);
+            else if (pt) launch_shared<step_kernel_g1<Tw, V, true, false, true>>(blocks, threads, 0, st, p);
             else launch_shared<step_kernel_g1<Tw, V, true, false>>(blocks, threads, 0, st, p);
         } else {
             if (trace) launch_shared<step_kernel_g1<Tw, V, false, true>>(blocks, threads, 0, st, p);
+            else if (pt) launch_shared<step_kernel_g1<Tw, V, false, false, true>>(blocks, threads, 0, st, p);
             else launch_shared<step_kernel_g1<Tw, V, false, false>>(blocks, threads, 0, st, p);
         }
         return cudaGetLastError();
