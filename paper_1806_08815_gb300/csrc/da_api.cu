@@ -55,6 +55,7 @@ struct da_ctx {
     int device = 0;
     void* W = nullptr;
     void* Wf = nullptr;  // DA_INT8: the couplings as exact fp32, for the step kernel
+    void* Wc[6] = {};    // the step couplings in the G = 1 row order, by log2 V (step_uses_coal)
     void* diag = nullptr;
     da::TcOperand tc;  // digit planes of W for the tensor-core recompute
     void* ws = nullptr;
@@ -206,10 +207,35 @@ struct RunBuffers {
     long long* eex() const { return reinterpret_cast<long long*>(base + L.eex); }
 };
 
+int log2_of(int v) { return 31 - __builtin_clz((unsigned)v); }
+
+// The copy of the step couplings in the G = 1 row order for shape s, built on the
+// context's stream (and waited for) the first time a launch of that width needs it.
+da_status ensure_coal(da_ctx* c, const StepShape& s)
+{
+    if (!da::step_uses_coal(step_wtype(c), s) || c->Wc[log2_of(s.V)]) return DA_OK;
+    void* p = nullptr;
+    cudaError_t e = da::dev_malloc(&p, da::coal_W_bytes(c->N, s.V));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DA_ENOMEM, std::string("row-ordered couplings: ") + cudaGetErrorString(e));
+    }
+    e = da::launch_coalesce_W(static_cast<const float*>(step_W(c)), c->N, c->ldw, s.V, static_cast<float*>(p),
+                              c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        da::dev_free(p);
+        return fail(DA_ECUDA, std::string("row-ordered couplings: ") + cudaGetErrorString(e));
+    }
+    c->Wc[log2_of(s.V)] = p;
+    return DA_OK;
+}
+
 StepParams base_params(const da_ctx* c, const RunBuffers& b)
 {
     StepParams p;
     p.W = step_W(c);
+    p.Wc = da::step_uses_coal(step_wtype(c), b.s) ? c->Wc[log2_of(b.s.V)] : nullptr;
     p.diag = c->diag;
     p.N = c->N;
     p.ldw = c->ldw;
@@ -277,6 +303,7 @@ da_status prof_pair(da_ctx* c, cudaEvent_t* a, cudaEvent_t* b)
 da_status run_anneal(da_ctx* c, const RunBuffers& b, const float* beta_dev, long long t_begin, long long T, float inc,
                      uint64_t seed, long long recompute_every, int* trace_dev, cudaStream_t st)
 {
+    if (da_status e = ensure_coal(c, b.s)) return e;
     StepParams p = base_params(c, b);
     p.beta = beta_dev;
     p.inc = inc;
@@ -480,6 +507,10 @@ da_status da_create(const void* Q, int64_t N, da_dtype dtype, da_ctx** out)
         return bail(e == cudaErrorMemoryAllocation ? DA_ENOMEM : DA_ECUDA,
                     std::string("tensor-core operand: ") + cudaGetErrorString(e));
     }
+    // the row-ordered couplings of the default one-warp shape, so that an anneal in that
+    // shape waits for nothing
+    if (n <= 1024)
+        if (da_status st = ensure_coal(c, auto_shape(n, 1024))) return bail(st, std::string(g_err));
     *out = c;
     return DA_OK;
 }
@@ -516,6 +547,8 @@ void da_destroy(da_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->W) da::dev_free(c->W);
     if (c->Wf) da::dev_free(c->Wf);
+    for (void* w : c->Wc)
+        if (w) da::dev_free(w);
     if (c->diag) da::dev_free(c->diag);
     da::tc_operand_free(&c->tc);
     if (c->ws) da::dev_free(c->ws);
@@ -704,6 +737,7 @@ static da_status pt_common(da_ctx* c, const float* betas, float* betas_final, in
     if (n_sw) DA_CU(cudaMemsetAsync(swaps, 0, n_sw * 8, st));
     DA_CU(cudaMemsetAsync(seen, 0, (size_t)K * 8, st));
     if (da_status e = reset_state(c, b, st)) return e;
+    if (da_status e = ensure_coal(c, b.s)) return e;
     StepParams p = base_params(c, b);
     p.betas = betas_dev;
     p.temp_of = temp_of;
@@ -970,6 +1004,7 @@ extern "C" da_status da_tune_shape(da_ctx* c, int32_t R, int64_t probe_steps, in
         float ms = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {   // the first run also loads and configures the kernel
             if (da_status e = reset_state(c, b, st)) return e;
+            if (da_status e = ensure_coal(c, b.s)) return e;
             StepParams p = base_params(c, b);
             p.beta = beta_dev;
             da::set_seed(p, 0x5eed);

@@ -271,8 +271,40 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// One thread per entry m of the reordered rows: m = 128 q + 4 l + e holds
+// variable i = l V + 4 q + e (see step_uses_coal in da_internal.h).
+__global__ void __launch_bounds__(256) coalesce_kernel(const float* __restrict__ W, int N, int ldw, int V,
+                                                       float* __restrict__ Wc)
+{
+    const int P = 32 * V;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * P) return;
+    const int k = (int)(idx / P), m = (int)(idx - (long long)k * P);
+    const int q = m >> 7, l = (m & 127) >> 2, e = m & 3;
+    const int i = l * V + 4 * q + e;
+    Wc[idx] = i < N ? W[(size_t)k * ldw + i] : 0.f;
+}
+
+bool step_uses_coal(int wtype, const StepShape& s)
+{
+    return (wtype == kWFp32 || wtype == kWInt8AsF32) && s.G == 1 && !s.ws && s.V >= 8;
+}
+
+size_t coal_W_bytes(int N, int V) { return (size_t)N * 32 * V * sizeof(float); }
+
+cudaError_t launch_coalesce_W(const float* W, int N, int ldw, int V, float* Wc, cudaStream_t st)
+{
+    const long long n = (long long)N * 32 * V;
+    if (n == 0) return cudaSuccess;
+    if (V < 8 || V > 32 || (V & (V - 1)) || 32 * V < N) return cudaErrorInvalidValue;
+    prefer_shared<coalesce_kernel>();
+    coalesce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, N, ldw, V, Wc);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_field_kernels()
 {
+    prefer_shared<coalesce_kernel>();
     prefer_shared<zero_kernel>();
     prefer_shared<expand_kernel<int32_t, int8_t>>();
     prefer_shared<expand_kernel<int32_t, int16_t>>();

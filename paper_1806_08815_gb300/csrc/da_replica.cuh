@@ -23,7 +23,9 @@ namespace step_detail {
 // (prep_draws) and the draws of every step start from it (draw_pre); four more
 // words per block live in registers, for kernels that have them to spare.
 // LATE: the best-state test is made under the row load (see flush_best).
-template <typename Tw, int V, bool SW = false, bool PRE = false, bool LATE = (V >= 8)>
+// COAL: W points at the couplings in the G = 1 row order (row pitch ldw = 32 V;
+// step_uses_coal in da_internal.h) and rows are read with RowCoal.
+template <typename Tw, int V, bool SW = false, bool PRE = false, bool LATE = (V >= 8), bool COAL = false>
 struct WarpReplica {
     using A = Arith<Tw>;
     using H = typename A::H;
@@ -42,6 +44,7 @@ struct WarpReplica {
     E Ecur, Ebest;
     long long flips;
     int lane, base, N, ldw;
+    int rowoff;       // this lane's first entry in a row of W: base, or 4 lane in the G = 1 order
     uint32_t rep;
     const Tw* __restrict__ W;
     uint32_t* bestg;  // best-state words of this replica
@@ -54,6 +57,7 @@ struct WarpReplica {
     {
         lane = threadIdx.x & 31;
         base = lane * V;
+        rowoff = COAL ? 4 * lane : base;
         N = N_;
         ldw = ldw_;
         rep = rep_;
@@ -90,7 +94,9 @@ struct WarpReplica {
 
     static __device__ __forceinline__ void load_row(const Tw* p, Tw (&c)[V])
     {
+        static_assert(!(SW && COAL), "a staged W is in the plain order");
         if constexpr (SW) RowShared<Tw, V>::load(p, c);
+        else if constexpr (COAL) RowCoal<Tw, V>::load(p, c);
         else Row<Tw, V>::load(p, c);
     }
 
@@ -358,7 +364,7 @@ struct WarpReplica {
         const H dEk = __shfl_sync(0xffffffffu, A::signed_field(gk, xold), own);
         const int k = own * V + vk;
         Tw cv[V];
-        if (FULL || base < N) load_row(W + (size_t)k * ldw + base, cv);
+        if (FULL || base < N) load_row(W + (size_t)k * ldw + rowoff, cv);
         if constexpr (kTestUnderRow) flush_best();   // x is still the state after the previous step
         slots.rest_flip();
         if (FULL || base < N) {
@@ -413,7 +419,7 @@ struct WarpReplica {
                 const int j = wi * 32 + b;
                 if (base < N) {
                     Tw cv[V];
-                    load_row(W + (size_t)j * ldw + base, cv);
+                    load_row(W + (size_t)j * ldw + rowoff, cv);
 #pragma unroll
                     for (int v = 0; v < V; ++v) acc[v] += to_fixed<SHIFT>(cv[v], S);
                 }

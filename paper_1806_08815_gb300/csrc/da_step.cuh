@@ -323,18 +323,21 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
 
 // G = 1: one warp per replica, the body of WarpReplica.  PT: the launch anneals
 // replicas at fixed per-replica temperatures (p.betas), where the best-state test
-// stays before the count.
+// stays before the count.  The fp32 forms at V >= 8 read their rows from p.Wc
+// (the G = 1 row order, pitch 32 V).
 template <typename Tw, int V, bool FULL, bool TRACE, bool PT = false>
 __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_blocks)
     step_kernel_g1(const __grid_constant__ StepParams p)
 {
-    using R_ = WarpReplica<Tw, V, false, true, !PT && V >= 8>;
+    constexpr bool kCoal = sizeof(Tw) == 4 && V >= 8;   // float and f32e
+    using R_ = WarpReplica<Tw, V, false, true, !PT && V >= 8, kCoal>;
     using H = typename R_::H;
     if (launch_stopped(p)) return;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= p.R) return;
     R_ rp;
-    rp.init(static_cast<const Tw*>(p.W), p.N, p.ldw, p.rep_base + (uint32_t)r, p.bestx + (size_t)r * p.nw);
+    rp.init(static_cast<const Tw*>(kCoal ? p.Wc : p.W), p.N, kCoal ? 32 * V : p.ldw, p.rep_base + (uint32_t)r,
+            p.bestx + (size_t)r * p.nw);
     H* hg = static_cast<H*>(p.h) + (size_t)r * p.npad + rp.base;
     uint32_t* xg = p.x + (size_t)r * p.nw;
 #pragma unroll
@@ -522,6 +525,7 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
             return cudaGetLastError();
         }
         const bool pt = p.betas != nullptr;
+        if (blocks > 0 && sizeof(Tw) == 4 && V >= 8 && p.Wc == nullptr) return cudaErrorInvalidValue;
         if (full) {
             if (trace) launch_shared<step_kernel_g1<Tw, V, true, true>>(blocks, threads, 0, st, p);
             else if (pt) launch_shared<step_kernel_g1<Tw, V, true, false, true>>(blocks, threads, 0, st, p);

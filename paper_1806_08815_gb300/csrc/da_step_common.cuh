@@ -158,6 +158,34 @@ template <int V> struct Row<f32e, V> {
     }
 };
 
+// Row k of W in the G = 1 row order (step_uses_coal in da_internal.h): p points at
+// entry 4 l of the row (lane l); float4 number q, at p + 128 q, holds the lane's
+// slots 4 q .. 4 q + 3.  Every load instruction of the warp reads 512 contiguous bytes.
+template <typename Tw, int V> struct RowCoal;
+template <int V> struct RowCoal<float, V> {
+    static __device__ __forceinline__ void load(const float* p, float (&c)[V])
+    {
+        static_assert(V % 4 == 0, "V");
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) {
+            const float4 f = ldx(reinterpret_cast<const float4*>(p + 128 * q));
+            c[4 * q] = f.x; c[4 * q + 1] = f.y; c[4 * q + 2] = f.z; c[4 * q + 3] = f.w;
+        }
+    }
+};
+template <int V> struct RowCoal<f32e, V> {
+    static __device__ __forceinline__ void load(const f32e* p, f32e (&c)[V])
+    {
+        static_assert(V % 4 == 0, "V");
+        const float* pf = reinterpret_cast<const float*>(p);
+#pragma unroll
+        for (int q = 0; q < V / 4; ++q) {
+            const float4 f = ldx(reinterpret_cast<const float4*>(pf + 128 * q));
+            c[4 * q].f = f.x; c[4 * q + 1].f = f.y; c[4 * q + 2].f = f.z; c[4 * q + 3].f = f.w;
+        }
+    }
+};
+
 // 16-byte loads from shared memory (p points into the block's staged copy).
 template <typename Tw, int V> struct RowShared {
     static __device__ __forceinline__ void load(const Tw* p, Tw (&c)[V])
