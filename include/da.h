@@ -293,8 +293,12 @@ da_status da_batch_describe(char* buf, int64_t len);
 /* Override the tuner of da_batch_anneal for the calls that follow, process
  * wide (for tests and measurements): staging -1 = the tuner's choice, 0 = rows
  * of W from L2, 1 = W staged in shared memory where the class allows it (else
- * L2); warps_per_block 0 = the tuner's choice, else 1, 2 or 4 (2, 4, 8 or 16
- * when staged).  da_batch_force(-1, 0) restores the tuner.  Errors: DA_EINVAL. */
+ * L2), 2 = rows of W from L2 in the one-warp row order (a copy of the fp32
+ * couplings whose rows are permuted so that every 16-byte load of a warp reads
+ * 512 contiguous bytes) where the class allows it (fp32 and int8 instances of
+ * more than 128 variables; else plain L2); warps_per_block 0 = the tuner's
+ * choice, else 1, 2 or 4 (2, 4, 8 or 16 when staged).  da_batch_force(-1, 0)
+ * restores the tuner.  Errors: DA_EINVAL. */
 da_status da_batch_force(int32_t staging, int32_t warps_per_block);
 
 /* ---- Request loop (continuous batching) ------------------------------------

@@ -432,6 +432,16 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 const TcOperand& ctx_tc_operand(const da_ctx* c) { return c->tc; }
 bool ctx_exact_shift(const da_ctx* c) { return c->exact_shift; }
 
+const void* ctx_coal_W(da_ctx* c, int V)
+{
+    StepShape s;
+    s.V = V;
+    s.G = 1;
+    s.rpb = 1;
+    if (!step_uses_coal(step_wtype(c), s) || ensure_coal(c, s) != DA_OK) return nullptr;
+    return c->Wc[log2_of(V)];
+}
+
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S, const void** Wstep)
 {
     *W = c->W;

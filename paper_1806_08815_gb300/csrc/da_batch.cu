@@ -50,13 +50,13 @@ using step_detail::WarpReplica;
 // One work unit: replica r of item it, all of its steps, by the calling warp;
 // W points at the item's couplings (global memory, row pitch ldw) or at a
 // copy staged in shared memory (SW, row pitch ldw = 32 V).
-template <typename Tw, int V, bool SW>
+template <typename Tw, int V, bool SW, bool COAL = false>
 __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw* W, int ldw, long long t_limit)
 {
     // the precomputed draws (PRE) for V <= 16; the V = 32 kernel has no registers left for
     // them (measured slower)
     constexpr bool kPre = V <= 16;
-    using R_ = WarpReplica<Tw, V, SW, kPre>;
+    using R_ = WarpReplica<Tw, V, SW, kPre, (V >= 8), COAL>;
     using A = step_detail::Arith<Tw>;
     using H = typename R_::H;
     constexpr int nw = V;   // state words per replica (the padded width 32V / 32)
@@ -119,7 +119,8 @@ __device__ __forceinline__ void run_unit(const BatchItemDev& it, int r, const Tw
     }
 }
 
-template <typename Tw, int V>
+// COAL: rows of W from the items' copies in the one-warp row order (it.Wc).
+template <typename Tw, int V, bool COAL = false>
 __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ BatchClassParams bp)
 {
     const int lane = threadIdx.x & 31;
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(128) batch_kernel(const __grid_constant__ Batc
         }
         const BatchItemDev it = bp.items[lo];
         const int r = (int)(unit - (unsigned long long)it.unit0);
-        run_unit<Tw, V, false>(it, r, static_cast<const Tw*>(it.W), it.ldw, bp.t_limit);
+        if constexpr (COAL) run_unit<Tw, V, false, true>(it, r, static_cast<const Tw*>(it.Wc), 32 * V, bp.t_limit);
+        else run_unit<Tw, V, false>(it, r, static_cast<const Tw*>(it.W), it.ldw, bp.t_limit);
     }
 }
 
@@ -195,8 +197,26 @@ BatchKernel smem_kernel_for(int wk, int V)
     return nullptr;
 }
 
-BatchKernel kernel_for(int wk, int V)
+// The rows-from-L2 kernel of a class; coal: its items carry the row-ordered copies
+// (the fp32 forms at V >= 8).
+BatchKernel kernel_for(int wk, int V, bool coal)
 {
+    if (coal && wk == kWInt8AsF32) {
+        switch (V) {
+        case 8: return batch_kernel<step_detail::f32e, 8, true>;
+        case 16: return batch_kernel<step_detail::f32e, 16, true>;
+        case 32: return batch_kernel<step_detail::f32e, 32, true>;
+        }
+        return nullptr;
+    }
+    if (coal && wk == kWFp32) {
+        switch (V) {
+        case 8: return batch_kernel<float, 8, true>;
+        case 16: return batch_kernel<float, 16, true>;
+        case 32: return batch_kernel<float, 32, true>;
+        }
+        return nullptr;
+    }
     if (wk == kWInt16) {
         switch (V) {
         case 4: return batch_kernel<int16_t, 4>;
@@ -255,6 +275,7 @@ size_t al(size_t v) { return (v + 255) / 256 * 256; }
 struct BatchConfig {
     bool smem = false;
     int warps_per_block = 4;
+    bool coal = false;   // rows from L2 in the one-warp row order (BatchClass::coal)
 };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, bool, int>, BatchConfig> g_tune_cache;
@@ -296,6 +317,8 @@ struct BatchClass {
     std::string probes;          // the tuner's measurements, for da_batch_describe
     size_t staged_bytes() const { return (size_t)max_N * 32 * V * 4; }
     bool can_stage() const { return smem_kernel_for(wk, V) != nullptr && staged_bytes() <= kMaxStagedBytes; }
+    // rows from L2 may come in the one-warp row order (every item carries its copy, Host::Wc)
+    bool coal() const { return (wk == kWFp32 || wk == kWInt8AsF32) && V >= 8; }
 };
 
 // Groups of `wpb` replicas, each within one item, covering the first `units` units.
@@ -318,7 +341,7 @@ cudaError_t launch_class(const BatchClass& c, const std::vector<int>& reps, cons
 {
     BatchClassParams bp{c.items_dev, c.n_items, units, c.head, t_limit, nullptr, 0, 0};
     if (!cfg.smem) {
-        BatchKernel k = kernel_for(c.wk, c.V);
+        BatchKernel k = kernel_for(c.wk, c.V, cfg.coal && c.coal());
         k<<<blocks_for(k, cfg.warps_per_block, sms, 0), cfg.warps_per_block * 32, 0, st>>>(bp);
         return cudaGetLastError();
     }
@@ -349,6 +372,7 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
     if (fs >= 0 || fw > 0) {
         BatchConfig cfg;
         cfg.smem = fs == 1 && c.can_stage();
+        cfg.coal = fs == 2 && c.coal();
         cfg.warps_per_block = fw > 0 ? fw : (cfg.smem ? 8 : 4);
         if (!cfg.smem) cfg.warps_per_block = std::min(cfg.warps_per_block, 4);   // the L2 kernel's block limit
         if (cfg.smem) cfg.warps_per_block = std::max(cfg.warps_per_block, 2);
@@ -368,12 +392,17 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
         }
     }
     std::vector<BatchConfig> cands;
-    for (int wpb : {1, 2, 4}) cands.push_back(BatchConfig{false, wpb});
+    for (int wpb : {1, 2, 4}) cands.push_back(BatchConfig{false, wpb, false});
+    if (c.coal())
+        for (int wpb : {1, 2, 4}) cands.push_back(BatchConfig{false, wpb, true});
     if (c.can_stage())
-        for (int wpb : {2, 4, 8, 16}) cands.push_back(BatchConfig{true, wpb});
+        for (int wpb : {2, 4, 8, 16}) cands.push_back(BatchConfig{true, wpb, false});
     BatchConfig best = cands.front();
-    float best_l2 = 1e30f, best_staged = 1e30f;
-    BatchConfig cfg_l2 = cands.front(), cfg_staged = cands.front();
+    float best_l2 = 1e30f, best_staged = 1e30f, best_coal = 1e30f;
+    BatchConfig cfg_l2 = cands.front(), cfg_staged = cands.front(), cfg_coal = cands.front();
+    auto label = [](const BatchConfig& cfg) {
+        return std::string(cfg.smem ? "smem" : cfg.coal ? "l2r" : "l2") + "x" + std::to_string(cfg.warps_per_block);
+    };
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -388,15 +417,17 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
         if (le == cudaSuccess) le = cudaStreamSynchronize(st);
         if (le != cudaSuccess) {
             cudaGetLastError();
-            log += std::string(log.empty() ? "" : ", ") + (cfg.smem ? "smem" : "l2") + "x" +
-                   std::to_string(cfg.warps_per_block) + " failed: " + cudaGetErrorString(le);
+            log += std::string(log.empty() ? "" : ", ") + label(cfg) + " failed: " + cudaGetErrorString(le);
             continue;
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        log += std::string(log.empty() ? "" : ", ") + (cfg.smem ? "smem" : "l2") + "x" +
-               std::to_string(cfg.warps_per_block) + " " + std::to_string(ms).substr(0, 6) + " ms";
-        if (!cfg.smem && ms < best_l2) {
+        log += std::string(log.empty() ? "" : ", ") + label(cfg) + " " + std::to_string(ms).substr(0, 6) + " ms";
+        if (cfg.coal && ms < best_coal) {
+            best_coal = ms;
+            cfg_coal = cfg;
+        }
+        if (!cfg.smem && !cfg.coal && ms < best_l2) {
             best_l2 = ms;
             cfg_l2 = cfg;
         }
@@ -407,9 +438,14 @@ BatchConfig tune_class(BatchClass& c, const std::vector<int>& reps, int dev, int
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // staging is taken only when its probe beats the best L2 configuration by more than the
-    // run-to-run spread of these probes (3 %)
+    // the row-ordered rows are taken when their probe beats the plain order's by more than 1 %,
+    // staging only when its probe beats the best L2 configuration by more than the run-to-run
+    // spread of these probes (3 %)
     if (best_l2 < 1e30f) best = cfg_l2;
+    if (best_coal < 0.99f * best_l2) {
+        best = cfg_coal;
+        best_l2 = best_coal;
+    }
     if (best_staged < 0.97f * best_l2) best = cfg_staged;
     c.probes = "probes (" + std::to_string(units) + " replicas x " + std::to_string(kProbeSteps) + " steps): " + log;
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -442,6 +478,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
     struct Host {
         const void* W;       // couplings for the exact evaluation
         const void* Wstep;   // couplings in the step kernel's form (int8 instances: exact fp32)
+        const void* Wc;      // the step couplings in the one-warp row order (fp32 forms, V >= 8), or null
         int dtype;           // da_dtype of the instance
         const void* diag;
         int N, ldw, S;
@@ -473,6 +510,11 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         int V = 4;
         while (32 * V < h.N) V *= 2;
         h.V = V;
+        h.Wc = nullptr;
+        if ((dt == DA_FP32 || dt == DA_INT8) && V >= 8) {
+            h.Wc = da::ctx_coal_W(it.ctx, V);
+            if (!h.Wc) return bfail(DA_ENOMEM, "item " + std::to_string(i) + ": " + da_last_error());
+        }
         hi[i] = h;
     }
     // device layout: per item betas, states, scalars, traces, results; per class descriptors
@@ -557,6 +599,7 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
                 const da_batch_item& it = items[i];
                 BatchItemDev d{};
                 d.W = hi[i].Wstep;
+                d.Wc = hi[i].Wc;
                 d.diag = hi[i].diag;
                 d.beta = reinterpret_cast<const float*>(base + o_beta[i]);
                 d.xs = reinterpret_cast<uint32_t*>(base + o_xs[i]);
@@ -611,7 +654,9 @@ extern "C" da_status da_batch_anneal(const da_batch_item* items, int32_t n, doub
         desc_text += std::string(desc_text.empty() ? "" : "; ") + (c.wk == da::kWFp32 ? "fp32" : c.wk == da::kWInt16 ? "int16" : "int8") + " V=" +
                      std::to_string(c.V) + " (N <= " + std::to_string(c.max_N) + ", " + std::to_string(c.n_items) +
                      " instances, " + std::to_string(c.units) + " replicas): " +
-                     (c.cfg.smem ? "W staged in shared memory" : "rows of W from L2") + ", " +
+                     (c.cfg.smem ? "W staged in shared memory"
+                                 : c.cfg.coal ? "rows of W from L2 in the one-warp row order" : "rows of W from L2") +
+                     ", " +
                      std::to_string(c.cfg.warps_per_block) + " warps per block [" + c.probes + "]";
     }
     da::g_batch_desc = desc_text;
@@ -732,8 +777,8 @@ extern "C" da_status da_batch_force(int32_t staging, int32_t warps_per_block)
 {
     const bool wpb_ok = warps_per_block == 0 || warps_per_block == 1 || warps_per_block == 2 ||
                         warps_per_block == 4 || warps_per_block == 8 || warps_per_block == 16;
-    if (staging < -1 || staging > 1 || !wpb_ok || (staging != 1 && warps_per_block > 4)) {
-        da::set_last_error("staging in {-1, 0, 1}; warps per block in {0, 1, 2, 4} (up to 16 when staged)");
+    if (staging < -1 || staging > 2 || !wpb_ok || (staging != 1 && warps_per_block > 4)) {
+        da::set_last_error("staging in {-1, 0, 1, 2}; warps per block in {0, 1, 2, 4} (up to 16 when staged)");
         return DA_EINVAL;
     }
     if (staging == 1 && warps_per_block == 1) {
@@ -750,7 +795,7 @@ namespace da {
 cudaError_t launch_resident_anneal(int wk, int V, const BatchItemDev* item_dev, unsigned long long* head_dev, int R,
                                    cudaStream_t st)
 {
-    BatchKernel k = kernel_for(wk, V);
+    BatchKernel k = kernel_for(wk, V, false);   // a request's item carries no row-ordered copy
     if (!k) return cudaErrorInvalidValue;
     prefer_shared_fn(reinterpret_cast<const void*>(k));
     cudaError_t e = cudaMemsetAsync(head_dev, 0, sizeof(unsigned long long), st);
@@ -763,7 +808,7 @@ cudaError_t launch_resident_anneal(int wk, int V, const BatchItemDev* item_dev, 
 cudaError_t prepare_resident_kernels()
 {
     for (int wk : {kWInt8AsF32, kWFp32, kWInt16})
-        for (int V : {4, 8, 16, 32}) prefer_shared_fn(reinterpret_cast<const void*>(kernel_for(wk, V)));
+        for (int V : {4, 8, 16, 32}) prefer_shared_fn(reinterpret_cast<const void*>(kernel_for(wk, V, false)));
     return cudaGetLastError();
 }
 

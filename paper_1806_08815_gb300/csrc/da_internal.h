@@ -252,6 +252,7 @@ cudaError_t pool_free_async(void* p, cudaStream_t st);
 // request loop uses one item for a request that runs resident.
 struct BatchItemDev {
     const void* W;          // couplings in the step kernel's form
+    const void* Wc;         // the same in the one-warp row order (pitch 32 V; step_uses_coal), or null
     const void* diag;
     const float* beta;
     uint32_t* xs;           // [2R][nw]: final states, then best states
@@ -293,6 +294,9 @@ void set_last_error(const std::string& msg);
 // fp32, kWInt8AsF32; otherwise W).
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S,
                      const void** Wstep = nullptr);
+// The context's couplings in the one-warp row order for V variables per lane
+// (built on first use), or null when they cannot be made (da_last_error says why).
+const void* ctx_coal_W(da_ctx* c, int V);
 // The context's tensor-core operand of W (built by da_create).
 const TcOperand& ctx_tc_operand(const da_ctx* c);
 // Whether the context's fp32 instance reaches its fixed-point grid by shifts alone.

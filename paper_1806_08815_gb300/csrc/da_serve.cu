@@ -305,6 +305,7 @@ bool admit(da_server* s, Req& q, long long& launches)
     if (q.resident && T > 0) {
         da::BatchItemDev& d = q.item;
         d.W = p.W;
+        d.Wc = nullptr;   // the resident kernel reads W in the plain order
         d.diag = diag;
         d.beta = p.beta;
         d.xs = xs;

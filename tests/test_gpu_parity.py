@@ -485,12 +485,13 @@ def test_batched_launch_matches_single_instances(da, inst):
     assert np.array_equal(outs[1]["trace"], ref["trace"])
 
 
-@pytest.mark.parametrize("staging,wpb", [(0, 1), (0, 4), (1, 2), (1, 8), (1, 16), (-1, 0)])
+@pytest.mark.parametrize("staging,wpb", [(0, 1), (0, 4), (1, 2), (1, 8), (1, 16), (2, 1), (2, 4), (-1, 0)])
 def test_batched_configurations_match_single_instances(da, inst, staging, wpb):
     """Every configuration the batched launch's tuner can choose (rows of W from L2 at 1 or 4
-    warps per block; W staged in shared memory with groups of 2, 8 or 16 replicas; the tuner
-    itself) gives each item the results of its own da_anneal run, bit for bit.  Sizes that
-    stage (V = 4 and V = 8 classes up to N = 221) and that do not, ragged replica counts."""
+    warps per block, in the plain or the one-warp row order; W staged in shared memory with
+    groups of 2, 8 or 16 replicas; the tuner itself) gives each item the results of its own
+    da_anneal run, bit for bit.  Sizes that stage (V = 4 and V = 8 classes up to N = 221) and
+    that do not, ragged replica counts."""
     rng = np.random.default_rng(7)
     jobs, refs = [], []
     sizes = [64, 100, 128, 200, 221, 256, 40, 1024, 90, 520]
@@ -519,6 +520,8 @@ def test_batched_configurations_match_single_instances(da, inst, staging, wpb):
     assert el > 0
     if staging == 1:
         assert "shared memory" in desc, desc
+    if staging == 2:
+        assert "one-warp row order" in desc, desc
     for o, r in zip(outs, refs):
         for k in ("trace", "final_x", "best_x", "flips", "final_E", "best_E", "max_drift"):
             assert np.array_equal(o[k], r[k]), (k, desc)
