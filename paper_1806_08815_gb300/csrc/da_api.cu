@@ -55,7 +55,7 @@ struct da_ctx {
     int device = 0;
     void* W = nullptr;
     void* Wf = nullptr;  // DA_INT8: the couplings as exact fp32, for the step kernel
-    void* Wc[6] = {};    // the step couplings in the G = 1 row order, by log2 V (step_uses_coal)
+    void* Wc[6][4] = {};  // the step couplings in the warp row order, by (log2 V, log2 G) (step_uses_coal)
     void* diag = nullptr;
     da::TcOperand tc;  // digit planes of W for the tensor-core recompute
     void* ws = nullptr;
@@ -209,25 +209,27 @@ struct RunBuffers {
 
 int log2_of(int v) { return 31 - __builtin_clz((unsigned)v); }
 
-// The copy of the step couplings in the G = 1 row order for shape s, built on the
-// context's stream (and waited for) the first time a launch of that width needs it.
+// The copy of the step couplings in the warp row order for shape s, built on the
+// context's stream (and waited for) the first time a launch of that shape needs it.
+void*& coal_slot(da_ctx* c, const StepShape& s) { return c->Wc[log2_of(s.V)][log2_of(s.G)]; }
+
 da_status ensure_coal(da_ctx* c, const StepShape& s)
 {
-    if (!da::step_uses_coal(step_wtype(c), s) || c->Wc[log2_of(s.V)]) return DA_OK;
+    if (!da::step_uses_coal(step_wtype(c), s) || coal_slot(c, s)) return DA_OK;
     void* p = nullptr;
-    cudaError_t e = da::dev_malloc(&p, da::coal_W_bytes(c->N, s.V));
+    cudaError_t e = da::dev_malloc(&p, da::coal_W_bytes(c->N, s));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(DA_ENOMEM, std::string("row-ordered couplings: ") + cudaGetErrorString(e));
     }
-    e = da::launch_coalesce_W(static_cast<const float*>(step_W(c)), c->N, c->ldw, s.V, static_cast<float*>(p),
+    e = da::launch_coalesce_W(static_cast<const float*>(step_W(c)), c->N, c->ldw, s.V, s.G, static_cast<float*>(p),
                               c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         da::dev_free(p);
         return fail(DA_ECUDA, std::string("row-ordered couplings: ") + cudaGetErrorString(e));
     }
-    c->Wc[log2_of(s.V)] = p;
+    coal_slot(c, s) = p;
     return DA_OK;
 }
 
@@ -235,7 +237,7 @@ StepParams base_params(const da_ctx* c, const RunBuffers& b)
 {
     StepParams p;
     p.W = step_W(c);
-    p.Wc = da::step_uses_coal(step_wtype(c), b.s) ? c->Wc[log2_of(b.s.V)] : nullptr;
+    p.Wc = da::step_uses_coal(step_wtype(c), b.s) ? c->Wc[log2_of(b.s.V)][log2_of(b.s.G)] : nullptr;
     p.diag = c->diag;
     p.N = c->N;
     p.ldw = c->ldw;
@@ -439,7 +441,7 @@ const void* ctx_coal_W(da_ctx* c, int V)
     s.G = 1;
     s.rpb = 1;
     if (!step_uses_coal(step_wtype(c), s) || ensure_coal(c, s) != DA_OK) return nullptr;
-    return c->Wc[log2_of(V)];
+    return coal_slot(c, s);
 }
 
 void ctx_device_view(const da_ctx* c, const void** W, const void** diag, int32_t* ldw, int32_t* S, const void** Wstep)
@@ -557,8 +559,9 @@ void da_destroy(da_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->W) da::dev_free(c->W);
     if (c->Wf) da::dev_free(c->Wf);
-    for (void* w : c->Wc)
-        if (w) da::dev_free(w);
+    for (auto& row : c->Wc)
+        for (void* w : row)
+            if (w) da::dev_free(w);
     if (c->diag) da::dev_free(c->diag);
     da::tc_operand_free(&c->tc);
     if (c->ws) da::dev_free(c->ws);

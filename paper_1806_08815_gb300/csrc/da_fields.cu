@@ -271,34 +271,36 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// One thread per entry m of the reordered rows: m = 128 q + 4 l + e holds
-// variable i = l V + 4 q + e (see step_uses_coal in da_internal.h).
-__global__ void __launch_bounds__(256) coalesce_kernel(const float* __restrict__ W, int N, int ldw, int V,
+// One thread per entry m of the reordered rows (pitch 32 V G): in warp slice
+// s = m / 32 V, entry m' = 128 q + 4 l + e holds variable i = s 32 V + l V + 4 q + e
+// (see step_uses_coal in da_internal.h).
+__global__ void __launch_bounds__(256) coalesce_kernel(const float* __restrict__ W, int N, int ldw, int V, int P,
                                                        float* __restrict__ Wc)
 {
-    const int P = 32 * V;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)N * P) return;
     const int k = (int)(idx / P), m = (int)(idx - (long long)k * P);
-    const int q = m >> 7, l = (m & 127) >> 2, e = m & 3;
-    const int i = l * V + 4 * q + e;
+    const int slice = m / (32 * V), mm = m - slice * 32 * V;
+    const int q = mm >> 7, l = (mm & 127) >> 2, e = mm & 3;
+    const int i = slice * 32 * V + l * V + 4 * q + e;
     Wc[idx] = i < N ? W[(size_t)k * ldw + i] : 0.f;
 }
 
 bool step_uses_coal(int wtype, const StepShape& s)
 {
-    return (wtype == kWFp32 || wtype == kWInt8AsF32) && s.G == 1 && !s.ws && s.V >= 8;
+    return (wtype == kWFp32 || wtype == kWInt8AsF32) && !s.ws && s.V >= 8;
 }
 
-size_t coal_W_bytes(int N, int V) { return (size_t)N * 32 * V * sizeof(float); }
+size_t coal_W_bytes(int N, const StepShape& s) { return (size_t)N * s.npad() * sizeof(float); }
 
-cudaError_t launch_coalesce_W(const float* W, int N, int ldw, int V, float* Wc, cudaStream_t st)
+cudaError_t launch_coalesce_W(const float* W, int N, int ldw, int V, int G, float* Wc, cudaStream_t st)
 {
-    const long long n = (long long)N * 32 * V;
+    const int P = 32 * V * G;
+    const long long n = (long long)N * P;
     if (n == 0) return cudaSuccess;
-    if (V < 8 || V > 32 || (V & (V - 1)) || 32 * V < N) return cudaErrorInvalidValue;
+    if (V < 8 || V > 32 || (V & (V - 1)) || G < 1 || G > 8 || (G & (G - 1)) || P < N) return cudaErrorInvalidValue;
     prefer_shared<coalesce_kernel>();
-    coalesce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, N, ldw, V, Wc);
+    coalesce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, N, ldw, V, P, Wc);
     return cudaGetLastError();
 }
 

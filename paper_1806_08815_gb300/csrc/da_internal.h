@@ -39,8 +39,8 @@ struct StepShape {
 
 struct StepParams {
     const void* W = nullptr;      // [N][ldw] symmetric, zero diagonal (int8 or fp32)
-    const void* Wc = nullptr;     // the same couplings in the G = 1 row order (coal_W_bytes);
-                                  // required where step_uses_coal, unused otherwise
+    const void* Wc = nullptr;     // the same couplings in the warp row order, row pitch npad
+                                  // (coal_W_bytes); required where step_uses_coal, unused otherwise
     const void* diag = nullptr;   // [N] int32 or fp32
     int N = 0;
     int ldw = 0;
@@ -94,18 +94,19 @@ cudaError_t launch_best_fixup(int R, ReplicaScalars* sc, bool is_int8, const uin
 // wtype: the da_dtype of W (DA_INT8, DA_FP32, DA_INT16).
 cudaError_t launch_step(int wtype, const StepShape& s, const StepParams& p, bool trace, cudaStream_t st);
 
-// The one-warp step (G = 1, no producer warp) of the fp32 coupling forms (fp32, and
-// int8 held as exact fp32) at V >= 8 variables per lane reads its rows of W from a
-// copy in another order: row k holds W[k][i] for the 32 V padded variables
-// i = l V + v (lane l, slot v) at entry 128 (v / 4) + 4 l + v % 4, so that float4
-// number q of lane l (entries 128 q + 4 l .. + 3) holds the lane's slots 4 q .. 4 q + 3
-// and each 16-byte load instruction of the warp reads 512 contiguous bytes (in the
-// plain order every lane's 16 bytes fall in a different 128-byte line).  Entries of
-// padding variables (i >= N) are 0.  The copy is [N][32 V] floats, 16-byte aligned
-// (da_fields.cu).
+// The step kernel (no producer warp) of the fp32 coupling forms (fp32, and int8
+// held as exact fp32) at V >= 8 variables per lane reads its rows of W from a copy
+// in another order, "the warp row order": in the 32 V entries of warp w's slice of
+// a row, variable i = w 32 V + l V + v (lane l, slot v) sits at entry
+// w 32 V + 128 (v / 4) + 4 l + v % 4, so that float4 number q of lane l (entries
+// w 32 V + 128 q + 4 l .. + 3) holds the lane's slots 4 q .. 4 q + 3 and each
+// 16-byte load instruction of the warp reads 512 contiguous bytes (in the plain
+// order every lane's 16 bytes fall in a different 128-byte line).  Entries of
+// padding variables (i >= N) are 0.  The copy is [N][32 V G] floats (the shape's
+// padded width), 16-byte aligned (da_fields.cu).
 bool step_uses_coal(int wtype, const StepShape& s);
-size_t coal_W_bytes(int N, int V);
-cudaError_t launch_coalesce_W(const float* W, int N, int ldw, int V, float* Wc, cudaStream_t st);
+size_t coal_W_bytes(int N, const StepShape& s);
+cudaError_t launch_coalesce_W(const float* W, int N, int ldw, int V, int G, float* Wc, cudaStream_t st);
 bool step_shape_supported(const StepShape& s);
 
 // Field recompute and energies (da_fields.cu).
@@ -252,7 +253,7 @@ cudaError_t pool_free_async(void* p, cudaStream_t st);
 // request loop uses one item for a request that runs resident.
 struct BatchItemDev {
     const void* W;          // couplings in the step kernel's form
-    const void* Wc;         // the same in the one-warp row order (pitch 32 V; step_uses_coal), or null
+    const void* Wc;         // the same in the warp row order (pitch 32 V; step_uses_coal), or null
     const void* diag;
     const float* beta;
     uint32_t* xs;           // [2R][nw]: final states, then best states

@@ -23,7 +23,7 @@ namespace step_detail {
 // (prep_draws) and the draws of every step start from it (draw_pre); four more
 // words per block live in registers, for kernels that have them to spare.
 // LATE: the best-state test is made under the row load (see flush_best).
-// COAL: W points at the couplings in the G = 1 row order (row pitch ldw = 32 V;
+// COAL: W points at the couplings in the warp row order (row pitch ldw = 32 V;
 // step_uses_coal in da_internal.h) and rows are read with RowCoal.
 template <typename Tw, int V, bool SW = false, bool PRE = false, bool LATE = (V >= 8), bool COAL = false>
 struct WarpReplica {

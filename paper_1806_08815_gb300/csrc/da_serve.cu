@@ -90,7 +90,7 @@ struct Req {
     std::string msg;
     char* dmem = nullptr;
     // offsets into dmem
-    size_t o_Wc = 0;                  // the step couplings in the G = 1 row order (0: not used)
+    size_t o_Wc = 0;                  // the step couplings in the warp row order (0: not used)
     size_t o_W = 0, o_Wf = 0, o_diag = 0, o_beta = 0, o_h = 0, o_xs = 0, o_sc = 0, o_part = 0, o_eex = 0, o_E = 0,
            o_flips = 0, o_tc = 0, o_item = 0;
     bool resident = false;            // the whole anneal in one launch, replica state in registers
@@ -175,7 +175,7 @@ void plan_request(Req& q)
     q.o_diag = take((size_t)q.N * 4);
     q.o_Wc = 0;
     if (da::step_uses_coal(q.dtype == DA_INT8 ? da::kWInt8AsF32 : q.dtype, sh) && !q.resident)
-        q.o_Wc = take(da::coal_W_bytes(q.N, sh.V));
+        q.o_Wc = take(da::coal_W_bytes(q.N, sh));
     q.o_beta = take((size_t)q.job.steps * 4);
     q.xs_stride = sh.nwords();
     q.o_h = take((size_t)R * sh.npad() * 4);
@@ -260,7 +260,7 @@ bool admit(da_server* s, Req& q, long long& launches)
     void* Wc = q.o_Wc ? q.dmem + q.o_Wc : nullptr;
     if (Wc) {
         if (!cu_ok(da::launch_coalesce_W(static_cast<const float*>(q.dtype == DA_INT8 ? Wf : W), q.N, q.inst.ldw,
-                                         q.shape.V, static_cast<float*>(Wc), st),
+                                         q.shape.V, q.shape.G, static_cast<float*>(Wc), st),
                    q, "row-ordered couplings"))
             return false;
         launches += 1;

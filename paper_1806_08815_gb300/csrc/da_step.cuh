@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
     H* pub = reinterpret_cast<H*>(gs + 4 * 32 * G); // [2] Delta E of the flipped variable
 
     const Tw* __restrict__ Wm = static_cast<const Tw*>(p.W);
+    constexpr bool kCoal = sizeof(Tw) == 4 && V >= 8;   // fp32 forms: rows from p.Wc (step_uses_coal)
     const int base = w * 32 * V + lane * V;         // first variable of this lane
     H* hg = static_cast<H*>(p.h) + (size_t)r * p.npad + base;
     uint32_t* xg = p.x + (size_t)r * p.nw;
@@ -276,7 +277,13 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
                 if (w == own_warp && lane == own_lane) pub[t & 1] = A::signed_field(gk, xold);
             }
             Tw cv[V];
-            if (FULL || base < p.N) Row<Tw, V>::load(Wm + (size_t)k * p.ldw + base, cv);
+            if (FULL || base < p.N) {
+                if constexpr (kCoal)   // this warp's slice of the row in the warp row order (pitch npad)
+                    RowCoal<Tw, V>::load(static_cast<const Tw*>(p.Wc) + (size_t)k * p.npad + w * 32 * V + 4 * lane,
+                                         cv);
+                else
+                    Row<Tw, V>::load(Wm + (size_t)k * p.ldw + base, cv);
+            }
             // the next step's draws do not depend on row k: compute them while
             // its loads are in flight
             if (t + 1 < p.t1) draw_step(lg, (uint32_t)(t + 1));
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(32 * G * OccupancyGV<G, V>::rpb, OccupancyGV<G
 // G = 1: one warp per replica, the body of WarpReplica.  PT: the launch anneals
 // replicas at fixed per-replica temperatures (p.betas), where the best-state test
 // stays before the count.  The fp32 forms at V >= 8 read their rows from p.Wc
-// (the G = 1 row order, pitch 32 V).
+// (the warp row order, pitch 32 V).
 template <typename Tw, int V, bool FULL, bool TRACE, bool PT = false>
 __global__ void __launch_bounds__(32 * Occupancy<1>::rpb, Occupancy<1>::min_blocks)
     step_kernel_g1(const __grid_constant__ StepParams p)
@@ -537,6 +544,7 @@ cudaError_t launch_vg(const StepShape& s, const StepParams& p, bool trace, cudaS
         }
         return cudaGetLastError();
     }
+    if (blocks > 0 && sizeof(Tw) == 4 && V >= 8 && p.Wc == nullptr) return cudaErrorInvalidValue;
     if (full) {
         if (trace) launch_shared<step_kernel<Tw, V, G, true, true>>(blocks, threads, shm, st, p);
         else launch_shared<step_kernel<Tw, V, G, true, false>>(blocks, threads, shm, st, p);

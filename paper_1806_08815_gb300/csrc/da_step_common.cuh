@@ -158,9 +158,10 @@ template <int V> struct Row<f32e, V> {
     }
 };
 
-// Row k of W in the G = 1 row order (step_uses_coal in da_internal.h): p points at
-// entry 4 l of the row (lane l); float4 number q, at p + 128 q, holds the lane's
-// slots 4 q .. 4 q + 3.  Every load instruction of the warp reads 512 contiguous bytes.
+// Row k of W in the warp row order (step_uses_coal in da_internal.h): p points at
+// entry 4 l of the warp's 32 V-entry slice of the row (lane l); float4 number q, at
+// p + 128 q, holds the lane's slots 4 q .. 4 q + 3.  Every load instruction of the
+// warp reads 512 contiguous bytes.
 template <typename Tw, int V> struct RowCoal;
 template <int V> struct RowCoal<float, V> {
     static __device__ __forceinline__ void load(const float* p, float (&c)[V])
