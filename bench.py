@@ -42,7 +42,7 @@ C3 = dict(N=1024, replicas=1024, steps=200_000, recompute_every=1024, beta0=0.1,
 # Warp instructions per replica-step of the step kernel (smsp__inst_executed.sum / (R x steps))
 # from the same capture: the issue-slot roofline of a kernel bound by instruction issue.
 STEP_INST_PER_REPLICA_STEP = 716.0
-STEP_TRAFFIC = {"source_sha256_16": "71ad029d5444097d", "bytes_per_launch": 8.5962e6}
+STEP_TRAFFIC = {"source_sha256_16": "80c60f7704049e9c", "bytes_per_launch": 8.5962e6}
 
 
 def step_source_sha():

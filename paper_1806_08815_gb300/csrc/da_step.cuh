@@ -17,9 +17,11 @@
 //   (c) each lane's acceptance bits are already in index order, so a warp
 //       prefix sum of their popcounts locates the j-th accepted variable,
 //       j = floor(u * count); the chosen x_k flips while every lane adds
-//       +-W[k][i] (16-byte loads of row k, which equals column k, from L2) to
-//       its fields.  The next step's Philox words are computed while that row
-//       is in flight.  E_off returns to 0 on a flip and grows by inc otherwise.
+//       +-W[k][i] (16-byte loads of row k, which equals column k, from L2; the
+//       fp32 forms read a copy of W in the warp row order, where each load of a
+//       warp covers 512 contiguous bytes) to its fields.  The next step's
+//       Philox words are computed while that row is in flight.  E_off returns
+//       to 0 on a flip and grows by inc otherwise.
 // A G = 1 group needs no shared memory or barrier.  A G > 1 group publishes
 // its lanes' acceptance and state masks in shared memory behind one named
 // barrier per step; the energy of step t is booked after the barrier of step
