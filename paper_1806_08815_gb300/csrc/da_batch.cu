@@ -9,11 +9,12 @@
 // (coupling type, V = variables per lane); each group is one persistent kernel
 // whose configuration is chosen by a small autotuner that times short probes
 // of the real work and caches the winner per device and class: warps per
-// block, and where the rows of W come from.  A class whose instances are small
-// enough can stage W in shared memory: each block then takes a group of
-// replicas of one instance (one per warp), copies that instance's W into
-// shared memory once, and runs the group's anneals reading rows from there
-// instead of from L2.
+// block, and where the rows of W come from (L2 in the plain order, L2 from the
+// contexts' copies in the warp row order, or shared memory).  A class whose
+// instances are small enough can stage W in shared memory: each block then
+// takes a group of replicas of one instance (one per warp), copies that
+// instance's W into shared memory once, and runs the group's anneals reading
+// rows from there instead of from L2.
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
