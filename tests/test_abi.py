@@ -111,3 +111,17 @@ def test_cancel_rejects_null(libda):
 def test_segment_rejects_bad_ranges_without_a_device(libda):
     """da_anneal_segment validates its arguments before touching a device."""
     assert libda.da_anneal_segment(None, None, 0, 0, 0, ctypes.c_float(0), 1, 0, 0, None, None, None) == 1
+
+
+def test_batch_force_arguments(libda):
+    """The batched launch's configuration override is host-only: every documented value is
+    accepted (staging -1 tuner, 0 L2, 1 shared memory, 2 L2 in the warp row order), the rest
+    is refused, and (-1, 0) restores the tuner."""
+    libda.da_batch_force.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    try:
+        for staging, wpb in ((-1, 0), (0, 1), (0, 4), (1, 16), (2, 0), (2, 2), (2, 4)):
+            assert libda.da_batch_force(staging, wpb) == 0, (staging, wpb)
+        for staging, wpb in ((3, 0), (-2, 0), (2, 8), (0, 16), (1, 1), (0, 3)):
+            assert libda.da_batch_force(staging, wpb) == 1, (staging, wpb)
+    finally:
+        assert libda.da_batch_force(-1, 0) == 0
